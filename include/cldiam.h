@@ -1,0 +1,207 @@
+/*
+ * cldiam.h — C ABI of the GB300 (sm_103a) CL-DIAM library.
+ *
+ * CL-DIAM estimates the weighted diameter of a large undirected graph
+ * (Ceccarello, Pietracaprina, Pucci, Upfal, arXiv 1506.03265):
+ *   1. CLUSTER(tau) grows clusters from batches of randomly drawn centers by
+ *      Delta-bounded relaxation rounds, doubling Delta until half of the
+ *      uncovered nodes are reached (Section 3, Algorithm 1);
+ *   2. the clustering is contracted into the weighted quotient graph G_C
+ *      (Section 4): one node per cluster, edge weight w(u,v) + d_u + d_v,
+ *      minimum per cluster pair;
+ *   3. Phi_approx = Phi(G_C) + 2 R, R the largest center distance (Section 4).
+ * A Delta-stepping SSSP (Meyer and Sanders) gives the competitor's
+ * 2-approximation 2 * ecc(s) (Section 5).
+ *
+ * Conventions for every entry point:
+ *  - Status: 0 = CLDIAM_OK, negative = error (below).  No C++ exception ever
+ *    crosses this boundary.  cldiam_last_error() describes the last failure of
+ *    the calling thread.
+ *  - Pointers: arrays passed in or out may live in host memory (pageable or
+ *    pinned) or in device memory of the current device; the library copies
+ *    with unified addressing and never keeps a borrowed pointer after the
+ *    call returns.
+ *  - Ownership: every handle (cldiam_graph, cldiam_clustering,
+ *    cldiam_quotient, ...) is created and owned by the library and released by
+ *    its matching *_free function, which accepts NULL.  A clustering or
+ *    quotient refers to (does not copy) the graph it came from; free it first.
+ *  - Streams: `stream` is a cudaStream_t or NULL (the library's own stream).
+ *    All work for a graph runs on the stream it was built with.  Calls return
+ *    after their results are complete (they synchronise that stream), except
+ *    where noted.
+ *  - Integers: node ids and weights are uint32; weights must be >= 1 (the
+ *    paper's positive integral weights, Section 2).  Distances inside the
+ *    library are exact uint32; a distance or quotient weight that would
+ *    reach 2^32 - 1 yields CLDIAM_ERR_OVERFLOW instead of a wrong answer.
+ *  - Threads: one handle must not be used by two threads at once.
+ */
+#ifndef CLDIAM_H
+#define CLDIAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cldiam_status;
+
+#define CLDIAM_OK 0
+#define CLDIAM_ERR_INVALID_ARG (-1) /* a size, pointer, id or weight is out of range */
+#define CLDIAM_ERR_OOM (-2)         /* device (or host) allocation failed            */
+#define CLDIAM_ERR_OVERFLOW (-3)    /* an exact distance would not fit in uint32     */
+#define CLDIAM_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired            */
+#define CLDIAM_ERR_CUDA (-5)        /* a CUDA runtime call failed                    */
+#define CLDIAM_ERR_BUSY (-6)        /* result not ready yet (serving poll)           */
+#define CLDIAM_ERR_CANCELLED (-7)   /* request cancelled or server stopped           */
+#define CLDIAM_ERR_DIVERGED (-8)    /* CLUSTER exceeded its stage limit              */
+#define CLDIAM_ERR_UNSUPPORTED (-9) /* valid request this build does not handle      */
+
+/* cldiam_build_csr flags */
+#define CLDIAM_CSR_LCC 1u /* keep only the largest connected component */
+
+/* cldiam_opts.delta0_mode: initial Delta of CLUSTER */
+#define CLDIAM_DELTA0_AVG 0      /* floor(mean edge weight), the choice of Section 5 (default) */
+#define CLDIAM_DELTA0_MIN 1      /* minimum edge weight, as in Algorithm 1                     */
+#define CLDIAM_DELTA0_EXPLICIT 2 /* cldiam_opts.delta0                                         */
+
+typedef struct cldiam_graph cldiam_graph;           /* device-resident symmetric CSR          */
+typedef struct cldiam_clustering cldiam_clustering; /* device-resident centers, D, cluster ids */
+typedef struct cldiam_quotient cldiam_quotient;     /* device-resident quotient CSR            */
+
+/* Options of cldiam_cluster.  Zero-initialised = the defaults. */
+typedef struct {
+    int32_t delta0_mode;   /* CLDIAM_DELTA0_*                                              */
+    uint32_t delta0;       /* used with CLDIAM_DELTA0_EXPLICIT; must be >= 1                */
+    int32_t contract_mode; /* 0: contracted clusters relax from distance 0 (Procedure Contract) */
+    uint32_t step_cap;     /* must be 0 (no cap on growing steps per PartialGrowth)         */
+    uint32_t max_fw_k;     /* largest quotient solved by Floyd-Warshall; 0 = 8192           */
+    uint32_t reserved[3];  /* must be 0                                                     */
+} cldiam_opts;
+
+/* Result of the whole method plus the paper-style counters (Table 2: rounds and work). */
+typedef struct {
+    uint64_t phi_gc;      /* Phi(G_C): largest finite distance in the quotient graph      */
+    uint64_t radius;      /* R = max over nodes of D_v (upper bound on dist(c_v, v))      */
+    uint64_t phi_approx;  /* Phi(G_C) + 2 R  (>= Phi(G), Section 4)                       */
+    uint32_t k;           /* number of clusters = quotient nodes                          */
+    uint32_t stages;      /* iterations of Algorithm 1's outer loop                       */
+    uint32_t steps;       /* Delta-growing steps executed (the paper's rounds of growth)  */
+    uint32_t doublings;   /* times Delta was doubled                                      */
+    uint32_t delta_end;   /* Delta at the end                                             */
+    uint32_t guard_exits; /* stages ended at a fixed point with coverage under half      */
+    uint64_t node_updates;   /* node state decreases over all steps (the paper's work)   */
+    uint64_t edges_scanned;  /* adjacency entries read by the relaxation kernels         */
+    uint64_t quotient_edges; /* directed entries of the quotient CSR                     */
+    uint64_t centers_drawn;  /* centers drawn over all stages (singletons not included)  */
+} cldiam_result;
+
+/* ------------------------------------------------------------------------ */
+const char* cldiam_status_string(cldiam_status s);
+/* Message for the calling thread's last failure ("" if none).  Valid until the next call. */
+const char* cldiam_last_error(void);
+/* Library version (major, minor); either pointer may be NULL. */
+cldiam_status cldiam_version(int32_t* major, int32_t* minor);
+
+/*
+ * Build the device CSR of an undirected weighted graph (Section 2 graph model).
+ *  src, dst, w : m edges (host or device arrays); node ids < n, weights >= 1.
+ *  Self-loops are dropped; parallel edges merge to their minimum weight; the
+ *  result is symmetric with rows sorted by column.  With CLDIAM_CSR_LCC only
+ *  the largest connected component is kept (ties: the component holding the
+ *  smallest id) and its nodes are renumbered by increasing original id.
+ *  Errors: INVALID_ARG (n == 0, id >= n, weight 0), OOM, CUDA.
+ */
+cldiam_status cldiam_build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m,
+                               uint32_t n, uint32_t flags, void* stream, cldiam_graph** out);
+/* Node count and directed entry count (2 x undirected edges) of a built graph. */
+cldiam_status cldiam_graph_info(const cldiam_graph* g, uint32_t* n, uint64_t* nnz);
+/* Copy the CSR out: off[n+1], col[nnz], w[nnz], orig[n] (original id of each node).
+ * Any pointer may be NULL to skip that array. */
+cldiam_status cldiam_graph_copy(const cldiam_graph* g, uint64_t* off, uint32_t* col, uint32_t* w,
+                                uint32_t* orig);
+void cldiam_graph_free(cldiam_graph* g);
+
+/* Initial Delta by mode (CLDIAM_DELTA0_AVG or _MIN), Algorithm 1 / Section 5. */
+cldiam_status cldiam_delta0(const cldiam_graph* g, int32_t mode, uint32_t* out);
+
+/*
+ * CLUSTER(G, tau) of Algorithm 1, on the device.
+ *  tau  : > 0.  Stages run while |U| >= 8 tau log2 n (U = uncovered nodes);
+ *         each draws node v of U as a center iff Philox4x32-10(key = seed,
+ *         counter = (v, stage, 0, 0)) word 0 < floor(p 2^32),
+ *         p = 4 ln2 tau log2 n / |U|.
+ *  Growth: synchronous Delta-growing steps (Section 3) with the
+ *         (distance, center id) tie-break; PartialGrowth stops when no state
+ *         changes or 2 covered >= |U|; Delta doubles (capped at 2^31) while
+ *         coverage is under half and some uncovered node is still reachable.
+ *  Contract: clusters of earlier stages relax from distance 0 through every
+ *         member; D_v = d_v + R[c_v] bounds dist_G(c_v, v).
+ *  Leftover nodes become singleton clusters.  Results are a deterministic
+ *  function of (graph, tau, seed, opts).
+ *  Errors: INVALID_ARG, OVERFLOW (a D_v >= 2^32 - 1), DIVERGED, OOM, CUDA.
+ */
+cldiam_status cldiam_cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
+                             cldiam_clustering** out);
+/* Counters of the clustering (k, stages, steps, ... ; phi fields are 0). */
+cldiam_status cldiam_clustering_info(const cldiam_clustering* c, cldiam_result* out);
+/* center[n] (center node id), D[n], cid[n] (cluster id = rank of the center id); any may be NULL. */
+cldiam_status cldiam_clustering_copy(const cldiam_clustering* c, uint32_t* center, uint32_t* D, uint32_t* cid);
+void cldiam_clustering_free(cldiam_clustering* c);
+
+/*
+ * Weighted quotient graph G_C (Section 4): node i = cluster i; for every edge
+ * (u,v) with different clusters an edge of weight w(u,v) + D_u + D_v, minimum
+ * per pair, stored as a symmetric CSR sorted by (row, col).
+ * Errors: OVERFLOW (a weight >= 2^32 - 1), OOM, CUDA.
+ */
+cldiam_status cldiam_quotient_build(const cldiam_clustering* c, cldiam_quotient** out);
+cldiam_status cldiam_quotient_info(const cldiam_quotient* q, uint32_t* k, uint64_t* nnz);
+/* off[k+1], col[nnz], w[nnz]; any may be NULL. */
+cldiam_status cldiam_quotient_copy(const cldiam_quotient* q, uint64_t* off, uint32_t* col, uint32_t* w);
+void cldiam_quotient_free(cldiam_quotient* q);
+
+/*
+ * Estimate (Section 4): out->phi_gc = Phi(G_C) by exact all-pairs shortest
+ * paths on the quotient (Floyd-Warshall when k <= max_fw_k), out->radius =
+ * max D, out->phi_approx = phi_gc + 2 radius; the clustering counters are
+ * filled in too.  out is a host pointer.
+ * Errors: OVERFLOW, UNSUPPORTED (k above max_fw_k), OOM, CUDA.
+ */
+cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out);
+
+/*
+ * Largest finite shortest-path distance of a small weighted graph given as a
+ * symmetric CSR (k nodes, off[k+1], col/w[nnz]; host or device), by blocked
+ * Floyd-Warshall on the device; used for Phi(G_C).  Allocates a k x k scratch
+ * matrix.  *phi is a host pointer.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ */
+cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                              void* stream, uint64_t* phi);
+
+/* Source node of the SSSP baseline: Philox4x32-10(seed; (2^32-1, 2^32-1, 0, 0)) word 0 mod n. */
+cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t* source);
+/*
+ * Delta-stepping SSSP (Meyer and Sanders) from `source` with bucket width
+ * `delta` (>= 1; 0 = average edge weight): exact distances, so any delta gives
+ * the same result.  dist[n] (may be NULL; 0xFFFFFFFF = unreachable) and
+ * *ecc = largest finite distance (host pointer); 2 * ecc is the SSSP
+ * 2-approximation of Section 5.  *rounds (may be NULL) = light/heavy phases run.
+ * Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ */
+cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist,
+                                uint64_t* ecc, uint64_t* rounds);
+
+/*
+ * Whole method from an edge list: build CSR (with `flags`), CLUSTER, quotient,
+ * estimate.  Inputs may be host or device arrays; out is a host pointer.
+ */
+cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
+                         uint32_t flags, double tau, uint64_t seed, const cldiam_opts* opts, void* stream,
+                         cldiam_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLDIAM_H */

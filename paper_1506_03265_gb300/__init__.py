@@ -1,0 +1,309 @@
+"""Python binding of the GB300 CL-DIAM library (``include/cldiam.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libcldiam.so`` built from ``csrc/`` for sm_103a.  There is no CPU fallback;
+if the library cannot be loaded, :func:`load` raises.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); the library
+copies through unified addressing.  Names follow the C ABI:
+``build_csr``, ``cluster``, ``quotient_build``, ``estimate``, ``sssp_delta`` ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["load", "CldiamError", "Graph", "Clustering", "Quotient", "Result", "Opts", "build_csr", "cluster",
+           "quotient_build", "estimate", "apsp_max", "sssp_source", "sssp_delta", "run", "lib_path"]
+
+OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "OVERFLOW", -4: "TIMEOUT", -5: "CUDA", -6: "BUSY",
+          -7: "CANCELLED", -8: "DIVERGED", -9: "UNSUPPORTED"}
+CSR_LCC = 1
+DELTA0_AVG, DELTA0_MIN, DELTA0_EXPLICIT = 0, 1, 2
+
+
+class CldiamError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("delta0_mode", ctypes.c_int32), ("delta0", ctypes.c_uint32), ("contract_mode", ctypes.c_int32),
+                ("step_cap", ctypes.c_uint32), ("max_fw_k", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("phi_gc", ctypes.c_uint64), ("radius", ctypes.c_uint64), ("phi_approx", ctypes.c_uint64),
+                ("k", ctypes.c_uint32), ("stages", ctypes.c_uint32), ("steps", ctypes.c_uint32),
+                ("doublings", ctypes.c_uint32), ("delta_end", ctypes.c_uint32), ("guard_exits", ctypes.c_uint32),
+                ("node_updates", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64),
+                ("quotient_edges", ctypes.c_uint64), ("centers_drawn", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+_lib_file = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = True):
+    """Load libcldiam.so (building it with nvcc if needed).  Raises if it cannot be loaded."""
+    global _lib, _lib_file
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {path}")
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        st = ctypes.c_int32
+        sig = {
+            "cldiam_status_string": (ctypes.c_char_p, [st]),
+            "cldiam_last_error": (ctypes.c_char_p, []),
+            "cldiam_version": (st, [P, P]),
+            "cldiam_build_csr": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, P, PP]),
+            "cldiam_graph_info": (st, [P, P, P]),
+            "cldiam_graph_copy": (st, [P, P, P, P, P]),
+            "cldiam_graph_free": (None, [P]),
+            "cldiam_delta0": (st, [P, ctypes.c_int32, P]),
+            "cldiam_cluster": (st, [P, ctypes.c_double, ctypes.c_uint64, P, PP]),
+            "cldiam_clustering_info": (st, [P, P]),
+            "cldiam_clustering_copy": (st, [P, P, P, P]),
+            "cldiam_clustering_free": (None, [P]),
+            "cldiam_quotient_build": (st, [P, PP]),
+            "cldiam_quotient_info": (st, [P, P, P]),
+            "cldiam_quotient_copy": (st, [P, P, P, P]),
+            "cldiam_quotient_free": (None, [P]),
+            "cldiam_estimate": (st, [P, P]),
+            "cldiam_apsp_max": (st, [ctypes.c_uint32, P, P, P, P, P]),
+            "cldiam_sssp_source": (st, [P, ctypes.c_uint64, P]),
+            "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
+            "cldiam_run": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                ctypes.c_uint64, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib, _lib_file = lib, path
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        msg = (load().cldiam_last_error() or b"").decode(errors="replace")
+        raise CldiamError(status, where, msg)
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device); None passes through."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _u32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, h):
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("handle already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            getattr(load(), self._free)(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Graph(_Handle):
+    _free = "cldiam_graph_free"
+
+    @property
+    def n(self) -> int:
+        n = ctypes.c_uint32()
+        _check(load().cldiam_graph_info(self.handle, ctypes.byref(n), None), "cldiam_graph_info")
+        return n.value
+
+    @property
+    def nnz(self) -> int:
+        z = ctypes.c_uint64()
+        _check(load().cldiam_graph_info(self.handle, None, ctypes.byref(z)), "cldiam_graph_info")
+        return z.value
+
+    def copy(self):
+        """(off uint64[n+1], col uint32[nnz], w uint32[nnz], orig uint32[n]) on the host."""
+        n, z = self.n, self.nnz
+        off = np.empty(n + 1, np.uint64); col = np.empty(z, np.uint32); w = np.empty(z, np.uint32)
+        orig = np.empty(n, np.uint32)
+        _check(load().cldiam_graph_copy(self.handle, off.ctypes.data, col.ctypes.data if z else None,
+                                        w.ctypes.data if z else None, orig.ctypes.data), "cldiam_graph_copy")
+        return off, col, w, orig
+
+    def delta0(self, mode: int = DELTA0_AVG) -> int:
+        d = ctypes.c_uint32()
+        _check(load().cldiam_delta0(self.handle, mode, ctypes.byref(d)), "cldiam_delta0")
+        return d.value
+
+
+class Clustering(_Handle):
+    _free = "cldiam_clustering_free"
+
+    def __init__(self, h, graph):
+        super().__init__(h)
+        self.graph = graph  # keep the graph alive
+
+    def info(self) -> dict:
+        r = Result()
+        _check(load().cldiam_clustering_info(self.handle, ctypes.byref(r)), "cldiam_clustering_info")
+        return r.as_dict()
+
+    def copy(self):
+        """(center, D, cid) as uint32 host arrays."""
+        n = self.graph.n
+        c = np.empty(n, np.uint32); D = np.empty(n, np.uint32); cid = np.empty(n, np.uint32)
+        _check(load().cldiam_clustering_copy(self.handle, c.ctypes.data, D.ctypes.data, cid.ctypes.data),
+               "cldiam_clustering_copy")
+        return c, D, cid
+
+
+class Quotient(_Handle):
+    _free = "cldiam_quotient_free"
+
+    def __init__(self, h, clustering):
+        super().__init__(h)
+        self.clustering = clustering
+
+    def info(self):
+        k = ctypes.c_uint32(); z = ctypes.c_uint64()
+        _check(load().cldiam_quotient_info(self.handle, ctypes.byref(k), ctypes.byref(z)), "cldiam_quotient_info")
+        return k.value, z.value
+
+    def copy(self):
+        k, z = self.info()
+        off = np.empty(k + 1, np.uint64); col = np.empty(z, np.uint32); w = np.empty(z, np.uint32)
+        _check(load().cldiam_quotient_copy(self.handle, off.ctypes.data, col.ctypes.data if z else None,
+                                           w.ctypes.data if z else None), "cldiam_quotient_copy")
+        return off, col, w
+
+
+def build_csr(src, dst, w, n: int, lcc: bool = True, stream=None) -> Graph:
+    """cldiam_build_csr: device CSR of an undirected weighted graph (host or device edge arrays)."""
+    lib = load()
+    src, dst, w = _u32(src), _u32(dst), _u32(w)
+    m = int(src.shape[0])
+    h = ctypes.c_void_p()
+    st = lib.cldiam_build_csr(_ptr(src), _ptr(dst), _ptr(w), m, n, CSR_LCC if lcc else 0, _stream_ptr(stream),
+                              ctypes.byref(h))
+    _check(st, "cldiam_build_csr")
+    return Graph(h.value)
+
+
+def make_opts(delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0) -> Opts:
+    o = Opts()
+    o.delta0_mode = delta0_mode
+    o.delta0 = delta0
+    o.max_fw_k = max_fw_k
+    return o
+
+
+def cluster(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0) -> Clustering:
+    """cldiam_cluster: CLUSTER(G, tau) of Algorithm 1."""
+    o = make_opts(delta0_mode, delta0, max_fw_k)
+    h = ctypes.c_void_p()
+    _check(load().cldiam_cluster(g.handle, float(tau), seed, ctypes.byref(o), ctypes.byref(h)), "cldiam_cluster")
+    return Clustering(h.value, g)
+
+
+def quotient_build(c: Clustering) -> Quotient:
+    """cldiam_quotient_build: the weighted quotient graph of Section 4."""
+    h = ctypes.c_void_p()
+    _check(load().cldiam_quotient_build(c.handle, ctypes.byref(h)), "cldiam_quotient_build")
+    return Quotient(h.value, c)
+
+
+def estimate(q: Quotient) -> dict:
+    """cldiam_estimate: Phi(G_C), R and Phi_approx = Phi(G_C) + 2R (Section 4)."""
+    r = Result()
+    _check(load().cldiam_estimate(q.handle, ctypes.byref(r)), "cldiam_estimate")
+    return r.as_dict()
+
+
+def apsp_max(k: int, off, col, w, stream=None) -> int:
+    """cldiam_apsp_max: largest finite distance of a k-node symmetric CSR graph."""
+    phi = ctypes.c_uint64()
+    off = off if hasattr(off, "data_ptr") else np.ascontiguousarray(off, dtype=np.uint64)
+    _check(load().cldiam_apsp_max(k, _ptr(off), _ptr(_u32(col)), _ptr(_u32(w)), _stream_ptr(stream),
+                                  ctypes.byref(phi)), "cldiam_apsp_max")
+    return phi.value
+
+
+def sssp_source(g: Graph, seed: int) -> int:
+    s = ctypes.c_uint32()
+    _check(load().cldiam_sssp_source(g.handle, seed, ctypes.byref(s)), "cldiam_sssp_source")
+    return s.value
+
+
+def sssp_delta(g: Graph, source: int, delta: int = 0, want_dist: bool = True):
+    """cldiam_sssp_delta: (dist or None, ecc, rounds) of Delta-stepping from `source`."""
+    dist = np.empty(g.n, np.uint32) if want_dist else None
+    ecc = ctypes.c_uint64(); rounds = ctypes.c_uint64()
+    _check(load().cldiam_sssp_delta(g.handle, source, delta, _ptr(dist), ctypes.byref(ecc), ctypes.byref(rounds)),
+           "cldiam_sssp_delta")
+    return dist, ecc.value, rounds.value
+
+
+def run(src, dst, w, n: int, tau: float, seed: int, lcc: bool = True, delta0_mode=DELTA0_AVG, stream=None) -> dict:
+    """cldiam_run: the whole method from an edge list."""
+    src, dst, w = _u32(src), _u32(dst), _u32(w)
+    o = make_opts(delta0_mode)
+    r = Result()
+    _check(load().cldiam_run(_ptr(src), _ptr(dst), _ptr(w), int(src.shape[0]), n, CSR_LCC if lcc else 0,
+                             float(tau), seed, ctypes.byref(o), _stream_ptr(stream), ctypes.byref(r)), "cldiam_run")
+    return r.as_dict()

@@ -1,0 +1,416 @@
+// CLUSTER(G, tau) of Algorithm 1 on the GPU.
+//
+// Node state (Section 3) is one 64-bit word per node, key = d << 32 | c, so
+// the paper's tie-break (smallest distance, then smallest center index) is
+// the integer minimum and a Delta-growing step is an atomicMin per light
+// edge.  Frozen nodes (clustered in an earlier stage; Procedure Contract)
+// hold key 0, which no candidate can undercut, so the relaxation needs no
+// frozen test; they are relaxers with the virtual key (0, c_u).
+//
+// Steps are synchronous: each frontier entry carries the key its node had
+// at the start of the step, so in-place atomicMin gives exactly the
+// start-of-step (Jacobi) semantics of the paper's "in parallel" step.  The
+// next frontier is the set of nodes whose key decreased (deduplicated with a
+// per-node step stamp); nodes whose key did not change would only repeat
+// candidates that are already applied.  After a stage start or a Delta
+// doubling every relaxer is listed again.
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cld {
+
+namespace {
+
+struct Counters {
+    unsigned long long selected;       // centers drawn in this stage
+    unsigned long long newly_covered;  // nodes that got their first key this step
+    unsigned long long edges_scanned;  // adjacency entries read by relax
+    unsigned long long frozen;         // nodes frozen by finalize
+    uint32_t nnext;                    // changed nodes this step
+    uint32_t nfront;                   // entries of the next frontier
+    uint32_t growable;                 // some covered/frozen node touches an uncovered one
+    uint32_t overflow;                 // a D_v reached 2^32 - 1
+};
+
+__device__ __forceinline__ void warp_add_u64(unsigned long long* p, unsigned long long v) {
+    v = warp_sum(v);
+    if (lane_id() == 0 && v) atomicAdd(p, v);
+}
+
+// a3: draw the new centers of this stage among unfrozen nodes, reset the others.
+__global__ void k_select(uint32_t n, const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
+                         uint64_t seed, uint32_t stage, uint64_t thr, Counters* ctr) {
+    unsigned long long cnt = 0;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        uint32_t v = base + threadIdx.x;
+        if (v < n && center[v] == kNone) {
+            U4 r = philox4x32_10(seed, v, stage, 0u, 0u);
+            bool sel = (uint64_t)r.x < thr;
+            key[v] = sel ? (unsigned long long)v : kInfKey;
+            cnt += sel ? 1 : 0;
+        }
+    }
+    warp_add_u64(&ctr->selected, cnt);
+}
+
+// a4: list every relaxer with its current key: unfrozen nodes with d < Delta,
+// and frozen nodes as (0, c_u).
+__global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
+                          uint32_t delta, uint32_t* __restrict__ fv, unsigned long long* __restrict__ fkey,
+                          Counters* ctr) {
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        uint32_t v = base + threadIdx.x;
+        bool take = false;
+        unsigned long long k = 0;
+        if (v < n) {
+            uint32_t c = center[v];
+            if (c != kNone) {
+                take = true;
+                k = c;  // (0, c_u)
+            } else {
+                k = key[v];
+                take = k != kInfKey && (uint32_t)(k >> 32) < delta;
+            }
+        }
+        uint32_t slot = warp_append(&ctr->nfront, take);
+        if (take) {
+            fv[slot] = v;
+            fkey[slot] = k;
+        }
+    }
+}
+
+// a5: one synchronous Delta-growing step, one warp per frontier entry.
+__global__ void __launch_bounds__(256) k_relax(const uint32_t* __restrict__ fv, const unsigned long long* __restrict__ fkey,
+                                               uint32_t nf, const uint64_t* __restrict__ off,
+                                               const uint2* __restrict__ adj, unsigned long long* __restrict__ key,
+                                               uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
+                                               uint32_t* __restrict__ next, Counters* ctr) {
+    const uint32_t lane = lane_id();
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long newly = 0, scanned = 0;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nf; i += warps) {
+        const uint32_t u = fv[i];
+        const unsigned long long ku = fkey[i];
+        const uint64_t du = ku >> 32;
+        const unsigned long long cu = ku & 0xFFFFFFFFull;
+        const uint64_t beg = off[u], end = off[u + 1];
+        scanned += (end - beg);
+        for (uint64_t b = beg; b < end; b += 32) {
+            const uint64_t j = b + lane;
+            bool changed_first = false;
+            uint32_t v = 0;
+            if (j < end) {
+                const uint2 e = adj[j];
+                v = e.x;
+                const uint64_t cand = du + e.y;
+                if (cand <= delta) {
+                    const unsigned long long nk = (cand << 32) | cu;
+                    if (nk < key[v]) {
+                        const unsigned long long old = atomicMin(&key[v], nk);
+                        if (nk < old) {
+                            newly += (old == kInfKey) ? 1 : 0;
+                            changed_first = atomicExch(&stamp[v], stepid) != stepid;
+                        }
+                    }
+                }
+            }
+            uint32_t slot = warp_append(&ctr->nnext, changed_first);
+            if (changed_first) next[slot] = v;
+        }
+    }
+    scanned = (lane == 0) ? scanned : 0;  // every lane holds the warp's count: keep one
+    warp_add_u64(&ctr->edges_scanned, scanned);
+    warp_add_u64(&ctr->newly_covered, newly);
+}
+
+// the changed nodes become the next frontier, with their end-of-step keys
+// (read after the step kernel has finished, so they are the next step's
+// start-of-step values); nodes that reached d = Delta do not relax.
+__global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned long long* __restrict__ key, uint32_t delta,
+                           uint32_t* __restrict__ fv, unsigned long long* __restrict__ fkey, Counters* ctr) {
+    const uint32_t nn = ctr->nnext;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < nn; base += gridDim.x * blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        bool take = false;
+        uint32_t v = 0;
+        unsigned long long k = 0;
+        if (i < nn) {
+            v = next[i];
+            k = key[v];
+            take = (uint32_t)(k >> 32) < delta;
+        }
+        uint32_t slot = warp_append(&ctr->nfront, take);
+        if (take) {
+            fv[slot] = v;
+            fkey[slot] = k;
+        }
+    }
+}
+
+// guard of the doubling loop: does any covered or frozen node have an uncovered neighbour?
+__global__ void k_growable(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
+                           const unsigned long long* __restrict__ key, Counters* ctr) {
+    bool any = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (key[adj[i].x] == kInfKey && key[row[i]] != kInfKey) any = true;
+    }
+    if (__any_sync(0xffffffffu, any) && lane_id() == 0) atomicExch(&ctr->growable, 1u);
+}
+
+// a7 (part 1): D_v = d_v + R[c_v] for the nodes covered in this stage (R as before the stage).
+__global__ void k_finalize_d(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
+                             const uint32_t* __restrict__ R, uint32_t* __restrict__ D, Counters* ctr) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (center[v] != kNone) continue;
+        unsigned long long k = key[v];
+        if (k == kInfKey) continue;
+        uint64_t dv = (k >> 32) + (uint64_t)R[(uint32_t)k];
+        if (dv >= 0xFFFFFFFFull) {
+            atomicExch(&ctr->overflow, 1u);
+            dv = 0xFFFFFFFEull;
+        }
+        D[v] = (uint32_t)dv;
+    }
+}
+
+// a7 (part 2): freeze them (key 0), record the center, grow R[c].
+__global__ void k_finalize_freeze(uint32_t n, unsigned long long* __restrict__ key, uint32_t* __restrict__ center,
+                                  uint32_t* __restrict__ R, const uint32_t* __restrict__ D, Counters* ctr) {
+    unsigned long long cnt = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (center[v] != kNone) continue;
+        unsigned long long k = key[v];
+        if (k == kInfKey) continue;
+        uint32_t c = (uint32_t)k;
+        center[v] = c;
+        key[v] = 0;
+        atomicMax(&R[c], D[v]);
+        ++cnt;
+    }
+    warp_add_u64(&ctr->frozen, cnt);
+}
+
+// a8: leftover nodes become singleton clusters.
+__global__ void k_singletons(uint32_t n, uint32_t* __restrict__ center, uint32_t* __restrict__ D) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (center[v] == kNone) {
+            center[v] = v;
+            D[v] = 0;
+        }
+}
+
+// a9: cluster id = rank of the center's node id among all centers.
+__global__ void k_center_flags(uint32_t n, const uint32_t* __restrict__ center, uint32_t* __restrict__ flag) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        flag[v] = center[v] == v ? 1u : 0u;
+}
+__global__ void k_assign_cid(uint32_t n, const uint32_t* __restrict__ center, const uint32_t* __restrict__ rank,
+                             uint32_t* __restrict__ cid) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) cid[v] = rank[center[v]];
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = x;
+}
+__global__ void k_fill_u64(unsigned long long* __restrict__ a, uint32_t n, unsigned long long x) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = x;
+}
+
+struct ClusterOwner {
+    cldiam_clustering* c;
+    explicit ClusterOwner(cldiam_clustering* x) : c(x) {}
+    ~ClusterOwner() {
+        if (c) free_clustering(c);
+    }
+};
+
+}  // namespace
+
+void free_clustering(cldiam_clustering* c) {
+    if (!c) return;
+    cudaStream_t s = c->g ? c->g->stream : nullptr;
+    dfree(c->center, s);
+    dfree(c->D, s);
+    dfree(c->cid, s);
+    if (s) cudaStreamSynchronize(s);
+    delete c;
+}
+
+cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* o, cldiam_clustering** out) {
+    if (!g || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL graph or out");
+    *out = nullptr;
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be a positive number");
+    cldiam_opts opts{};
+    if (o) opts = *o;
+    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1] || opts.reserved[2])
+        return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
+    uint32_t delta = 0;
+    CLD_TRY(delta0(g, opts.delta0_mode, opts.delta0, &delta));
+
+    const cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    ClusterOwner owner(new cldiam_clustering());
+    cldiam_clustering* cl = owner.c;
+    cl->g = g;
+    cl->max_fw_k = opts.max_fw_k ? opts.max_fw_k : 8192u;
+
+    DBuf<uint32_t> center, D, cid;
+    DBuf<unsigned long long> key, fkeyA, fkeyB;
+    DBuf<uint32_t> R, stamp, fvA, fvB, next;
+    DBuf<Counters> ctr;
+    CLD_TRY(center.alloc(n, s));
+    CLD_TRY(D.alloc(n, s));
+    CLD_TRY(cid.alloc(n, s));
+    CLD_TRY(key.alloc(n, s));
+    CLD_TRY(R.alloc(n, s));
+    CLD_TRY(stamp.alloc(n, s));
+    CLD_TRY(fvA.alloc(n, s));
+    CLD_TRY(fvB.alloc(n, s));
+    CLD_TRY(fkeyA.alloc(n, s));
+    CLD_TRY(fkeyB.alloc(n, s));
+    CLD_TRY(next.alloc(n, s));
+    CLD_TRY(ctr.alloc(1, s));
+    Counters* hc = static_cast<Counters*>(g->host.h);
+    static_assert(sizeof(Counters) <= 128, "counter block must fit the pinned area");
+
+    const unsigned gb = grid_for(n, 256);
+    k_fill_u32<<<gb, 256, 0, s>>>(center.get(), n, kNone);
+    k_fill_u32<<<gb, 256, 0, s>>>(D.get(), n, 0u);
+    k_fill_u32<<<gb, 256, 0, s>>>(R.get(), n, 0u);
+    k_fill_u32<<<gb, 256, 0, s>>>(stamp.get(), n, 0u);
+    k_fill_u64<<<gb, 256, 0, s>>>(key.get(), n, kInfKey);
+    CLD_LAUNCH_CHECK();
+    CLD_CUDA(cudaMemsetAsync(ctr.get(), 0, sizeof(Counters), s));
+
+    auto sync_counters = [&]() -> cldiam_status {
+        CLD_CUDA(cudaMemcpyAsync(hc, ctr.get(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        return CLDIAM_OK;
+    };
+    // zero a counter field on the device
+    auto zero_field = [&](size_t offset, size_t bytes) -> cldiam_status {
+        CLD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(ctr.get()) + offset, 0, bytes, s));
+        return CLDIAM_OK;
+    };
+
+    cldiam_result st{};
+    const double L = std::log2((double)n);
+    uint64_t U = n;  // unfrozen nodes
+    uint32_t stage = 1, stepid = 0;
+    uint32_t* fv = fvA.get();
+    unsigned long long* fk = fkeyA.get();
+    uint32_t* fv2 = fvB.get();
+    unsigned long long* fk2 = fkeyB.get();
+    const unsigned relax_grid = (unsigned)num_sms() * 8;
+
+    for (;;) {
+        if (U == 0) break;
+        if ((double)U < 8.0 * tau * L) break;  // outer while test of Algorithm 1
+        const double p = kGamma * tau * L / (double)U;
+        const uint64_t thr = (p >= 1.0) ? 4294967296ull : (uint64_t)std::floor(p * 4294967296.0);
+        if (thr == 0) break;
+        if (stage > kMaxStages) return fail(CLDIAM_ERR_DIVERGED, "CLUSTER exceeded its stage limit");
+
+        // selection + reset, then the stage's first frontier
+        CLD_TRY(zero_field(offsetof(Counters, selected), 8));
+        k_select<<<gb, 256, 0, s>>>(n, center.get(), key.get(), seed, stage, thr, ctr.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(zero_field(offsetof(Counters, nfront), 4));
+        k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), delta, fv, fk, ctr.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(sync_counters());
+        uint64_t covered = hc->selected;
+        uint32_t nf = hc->nfront;
+        st.centers_drawn += hc->selected;
+
+        for (;;) {
+            uint32_t updated;
+            do {
+                ++stepid;
+                updated = 0;
+                if (nf > 0) {
+                    CLD_TRY(zero_field(offsetof(Counters, newly_covered), 8));
+                    CLD_TRY(zero_field(offsetof(Counters, nnext), 8));  // nnext + nfront
+                    unsigned rg = (unsigned)std::min<uint64_t>((nf + 7) / 8, relax_grid);
+                    k_relax<<<rg, 256, 0, s>>>(fv, fk, nf, g->off, g->adj, key.get(), delta, stamp.get(), stepid,
+                                               next.get(), ctr.get());
+                    CLD_LAUNCH_CHECK();
+                    k_snapshot<<<relax_grid, 256, 0, s>>>(next.get(), key.get(), delta, fv2, fk2, ctr.get());
+                    CLD_LAUNCH_CHECK();
+                    CLD_TRY(sync_counters());
+                    updated = hc->nnext;
+                    covered += hc->newly_covered;
+                    std::swap(fv, fv2);
+                    std::swap(fk, fk2);
+                    nf = hc->nfront;
+                }
+                st.steps++;
+                st.node_updates += updated;
+            } while (updated != 0 && 2 * covered < U);
+            if (2 * covered >= U) break;
+            bool growable = false;
+            if (delta < kDeltaMax && g->nnz) {
+                CLD_TRY(zero_field(offsetof(Counters, growable), 4));
+                k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, key.get(), ctr.get());
+                CLD_LAUNCH_CHECK();
+                CLD_TRY(sync_counters());
+                growable = hc->growable != 0;
+            }
+            if (!growable) {
+                st.guard_exits++;
+                break;
+            }
+            delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
+            st.doublings++;
+            CLD_TRY(zero_field(offsetof(Counters, nfront), 4));
+            k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), delta, fv, fk, ctr.get());
+            CLD_LAUNCH_CHECK();
+            CLD_TRY(sync_counters());
+            nf = hc->nfront;
+        }
+
+        // assign and contract
+        CLD_TRY(zero_field(offsetof(Counters, frozen), 8));
+        k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get());
+        k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(sync_counters());
+        if (hc->overflow) return fail(CLDIAM_ERR_OVERFLOW, "a cluster distance bound reached 2^32 - 1");
+        U -= hc->frozen;
+        st.stages++;
+        ++stage;
+    }
+    k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get());
+    CLD_LAUNCH_CHECK();
+
+    // relabel
+    DBuf<uint32_t> flag, rank, kdev;
+    CLD_TRY(flag.alloc(n, s));
+    CLD_TRY(rank.alloc(n, s));
+    CLD_TRY(kdev.alloc(1, s));
+    k_center_flags<<<gb, 256, 0, s>>>(n, center.get(), flag.get());
+    CLD_LAUNCH_CHECK();
+    CLD_TRY(scan_exclusive_u32(flag.get(), rank.get(), n, kdev.get(), s));
+    k_assign_cid<<<gb, 256, 0, s>>>(n, center.get(), rank.get(), cid.get());
+    CLD_LAUNCH_CHECK();
+    uint32_t* hk = reinterpret_cast<uint32_t*>(static_cast<char*>(g->host.h) + 128);
+    CLD_CUDA(cudaMemcpyAsync(hk, kdev.get(), 4, cudaMemcpyDeviceToHost, s));
+    CLD_TRY(sync_counters());
+    st.edges_scanned = hc->edges_scanned;
+    st.k = *hk;
+    st.delta_end = delta;
+
+    cl->center = center.detach();
+    cl->D = D.detach();
+    cl->cid = cid.detach();
+    cl->k = st.k;
+    cl->stats = st;
+    *out = cl;
+    owner.c = nullptr;
+    return CLDIAM_OK;
+}
+
+}  // namespace cld

@@ -1,0 +1,422 @@
+// CSR construction on the device (Section 2 graph model): drop self-loops,
+// merge parallel edges to their minimum weight, symmetrise, sort rows by
+// column, optionally keep the largest connected component.
+//
+// Pipeline: 2m directed keys row*n+col are radix sorted (stable, only the
+// bits n*n needs); run heads give the unique entries and an atomicMin over
+// each run gives the lightest parallel edge.  Components come from min-label
+// hooking with pointer jumping: every tree points to a smaller id of its
+// component, so roots are component minima and the labelling is
+// deterministic.
+#include "internal.cuh"
+
+namespace cld {
+
+namespace {
+
+__global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                                const uint32_t* __restrict__ w, uint64_t m, uint32_t n, uint64_t sentinel,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ bad) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = src[e], v = dst[e], ww = w[e];
+        bool ok = u < n && v < n && ww != 0;
+        if (!ok) atomicExch(bad, 1u);
+        uint64_t k0 = sentinel, k1 = sentinel;
+        if (ok && u != v) {
+            k0 = (uint64_t)u * n + v;
+            k1 = (uint64_t)v * n + u;
+        }
+        keys[2 * e] = k0;
+        keys[2 * e + 1] = k1;
+        vals[2 * e] = ww;
+        vals[2 * e + 1] = ww;
+    }
+}
+
+__global__ void k_head_flags(const uint64_t* __restrict__ keys, uint64_t cnt, uint64_t sentinel,
+                             uint32_t* __restrict__ flags) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        flags[i] = (k < sentinel && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+    }
+}
+
+__global__ void k_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                         const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, uint64_t cnt,
+                         uint64_t sentinel, uint32_t n, uint32_t* __restrict__ row, uint32_t* __restrict__ col,
+                         uint32_t* __restrict__ wmin, uint32_t* __restrict__ deg) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        if (k >= sentinel) continue;
+        uint32_t r = excl[i] + flags[i] - 1u;
+        atomicMin(&wmin[r], vals[i]);
+        if (flags[i]) {
+            uint32_t u = (uint32_t)(k / n), v = (uint32_t)(k - (uint64_t)u * n);
+            row[r] = u;
+            col[r] = v;
+            atomicAdd(&deg[u], 1u);
+        }
+    }
+}
+
+__global__ void k_widen_offsets(const uint32_t* __restrict__ excl, uint32_t n, uint32_t total, uint64_t* __restrict__ off) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+        off[i] = (i == n) ? (uint64_t)total : (uint64_t)excl[i];
+}
+
+__global__ void k_pack_adj(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w, uint64_t nnz,
+                           uint2* __restrict__ adj) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x)
+        adj[i] = make_uint2(col[i], w[i]);
+}
+
+__global__ void k_iota(uint32_t* __restrict__ a, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+// one hooking sweep over undirected edges (u < v entries)
+__global__ void k_cc_hook(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
+                          uint32_t* __restrict__ parent, uint32_t* __restrict__ changed) {
+    bool any = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = row[i], v = adj[i].x;
+        if (u >= v) continue;
+        uint32_t ru = parent[u], rv = parent[v];
+        if (ru != rv) {
+            uint32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+            atomicMin(&parent[hi], lo);
+            any = true;
+        }
+    }
+    if (__any_sync(0xffffffffu, any) && lane_id() == 0) atomicExch(changed, 1u);
+}
+
+// pointer jumping to the root (parents only ever decrease within a component)
+__global__ void k_cc_compress(uint32_t* __restrict__ parent, uint32_t n) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t p = parent[v];
+        uint32_t pp = parent[p];
+        while (p != pp) {
+            p = pp;
+            pp = parent[p];
+        }
+        parent[v] = p;
+    }
+}
+
+__global__ void k_cc_count(const uint32_t* __restrict__ parent, uint32_t n, uint32_t* __restrict__ size) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        atomicAdd(&size[parent[v]], 1u);
+}
+
+// best component: largest size, then smallest root id
+__global__ void k_cc_best(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ size, uint32_t n,
+                          unsigned long long* __restrict__ best) {
+    unsigned long long b = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (parent[v] == v) {
+            unsigned long long key = ((unsigned long long)size[v] << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+            b = key > b ? key : b;
+        }
+    b = block_reduce(b, [](unsigned long long x, unsigned long long y) { return x > y ? x : y; }, 0ull);
+    if (threadIdx.x == 0) atomicMax(best, b);
+}
+
+__global__ void k_cc_keep(const uint32_t* __restrict__ parent, uint32_t n, const unsigned long long* __restrict__ best,
+                          uint32_t* __restrict__ keep) {
+    uint32_t root = 0xFFFFFFFFu - (uint32_t)(*best & 0xFFFFFFFFull);
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        keep[v] = parent[v] == root ? 1u : 0u;
+}
+
+__global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid,
+                              const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ ndeg,
+                              uint32_t* __restrict__ orig) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (keep[v]) {
+            ndeg[newid[v]] = (uint32_t)(off[v + 1] - off[v]);
+            orig[newid[v]] = v;
+        }
+}
+
+__global__ void k_lcc_copy(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid,
+                           const uint64_t* __restrict__ off, const uint32_t* __restrict__ row,
+                           const uint2* __restrict__ adj, uint64_t nnz, const uint64_t* __restrict__ noff,
+                           uint32_t* __restrict__ nrow, uint2* __restrict__ nadj) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = row[i];
+        if (!keep[u]) continue;
+        uint32_t nu = newid[u];
+        uint64_t pos = noff[nu] + (i - off[u]);
+        uint2 e = adj[i];
+        nadj[pos] = make_uint2(newid[e.x], e.y);
+        nrow[pos] = nu;
+    }
+}
+
+__global__ void k_graph_stats(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
+                              unsigned long long* __restrict__ wsum, uint32_t* __restrict__ wmin) {
+    unsigned long long s = 0;
+    uint32_t mn = 0xFFFFFFFFu;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint2 e = adj[i];
+        if (row[i] < e.x) s += e.y;
+        mn = e.y < mn ? e.y : mn;
+    }
+    s = block_reduce(s, [](unsigned long long a, unsigned long long b) { return a + b; }, 0ull);
+    if (threadIdx.x == 0 && s) atomicAdd(wsum, s);
+    mn = block_reduce(mn, [](uint32_t a, uint32_t b) { return a < b ? a : b; }, 0xFFFFFFFFu);
+    if (threadIdx.x == 0) atomicMin(wmin, mn);
+}
+
+__global__ void k_degree_max(const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ out) {
+    uint32_t m = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        m = max(m, (uint32_t)(off[v + 1] - off[v]));
+    m = block_reduce(m, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u);
+    if (threadIdx.x == 0) atomicMax(out, m);
+}
+
+struct GraphOwner {
+    cldiam_graph* g;
+    explicit GraphOwner(cldiam_graph* x) : g(x) {}
+    ~GraphOwner() {
+        if (g) free_graph(g);
+    }
+    cldiam_graph* release() {
+        cldiam_graph* x = g;
+        g = nullptr;
+        return x;
+    }
+};
+
+}  // namespace
+
+void free_graph(cldiam_graph* g) {
+    if (!g) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g->device);
+    dfree(g->off, g->stream);
+    dfree(g->adj, g->stream);
+    dfree(g->row, g->stream);
+    dfree(g->orig, g->stream);
+    cudaStreamSynchronize(g->stream);
+    cudaSetDevice(cur);
+    delete g;
+}
+
+cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
+                        uint32_t flags, cudaStream_t s, cldiam_graph** out) {
+    if (!out) return fail(CLDIAM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n == 0) return fail(CLDIAM_ERR_INVALID_ARG, "n must be >= 1");
+    if (m > 0 && (!src || !dst || !w)) return fail(CLDIAM_ERR_INVALID_ARG, "edge arrays are NULL");
+    if (2 * m > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "more than 2^31 - 1 edges");
+    if (flags & ~CLDIAM_CSR_LCC) return fail(CLDIAM_ERR_INVALID_ARG, "unknown flags");
+
+    GraphOwner owner(new cldiam_graph());
+    cldiam_graph* g = owner.g;
+    CLD_CUDA(cudaGetDevice(&g->device));
+    g->stream = s;
+    CLD_TRY(g->host.alloc(256));
+    uint32_t* hbad = static_cast<uint32_t*>(g->host.h);
+
+    // inputs on the device
+    void *dsrc = nullptr, *ddst = nullptr, *dw = nullptr;
+    bool osrc = false, odst = false, ow = false;
+    struct InFree {
+        void** p; bool* o; cudaStream_t s;
+        ~InFree() { if (*o) dfree(*p, s); }
+    };
+    CLD_TRY(to_device(src, m * 4, s, &dsrc, &osrc));
+    InFree f1{&dsrc, &osrc, s};
+    CLD_TRY(to_device(dst, m * 4, s, &ddst, &odst));
+    InFree f2{&ddst, &odst, s};
+    CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
+    InFree f3{&dw, &ow, s};
+
+    const uint64_t sentinel = (uint64_t)n * (uint64_t)n;
+    const int bits = bits_for(sentinel);
+    const uint64_t cnt = 2 * m;
+    DBuf<uint64_t> keys, keys2;
+    DBuf<uint32_t> vals, vals2, flagsb, excl, scal;
+    CLD_TRY(keys.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(keys2.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(vals.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(vals2.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(scal.alloc(8, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(uint32_t), s));
+    if (m > 0) {
+        k_emit_directed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
+                                                         (const uint32_t*)dw, m, n, sentinel, keys.get(),
+                                                         vals.get(), scal.get());
+        CLD_LAUNCH_CHECK();
+    }
+    CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (*hbad) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
+
+    bool alt = false;
+    CLD_TRY(radix_sort_pairs_u64(keys.get(), vals.get(), keys2.get(), vals2.get(), cnt, bits, &alt, s));
+    uint64_t* sk = alt ? keys2.get() : keys.get();
+    uint32_t* sv = alt ? vals2.get() : vals.get();
+
+    CLD_TRY(flagsb.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(excl.alloc(cnt ? cnt : 1, s));
+    if (cnt) {
+        k_head_flags<<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, sentinel, flagsb.get());
+        CLD_LAUNCH_CHECK();
+    }
+    CLD_TRY(scan_exclusive_u32(flagsb.get(), excl.get(), cnt, scal.get() + 1, s));
+    CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nnz = hbad[1];
+
+    DBuf<uint32_t> row, col, wmin, deg, degx;
+    CLD_TRY(row.alloc(nnz ? nnz : 1, s));
+    CLD_TRY(col.alloc(nnz ? nnz : 1, s));
+    CLD_TRY(wmin.alloc(nnz ? nnz : 1, s));
+    CLD_TRY(deg.alloc((size_t)n + 1, s));
+    CLD_TRY(degx.alloc((size_t)n + 1, s));
+    CLD_CUDA(cudaMemsetAsync(wmin.get(), 0xFF, (size_t)(nnz ? nnz : 1) * 4, s));
+    CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
+    if (cnt) {
+        k_unique<<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flagsb.get(), excl.get(), cnt, sentinel, n, row.get(),
+                                                    col.get(), wmin.get(), deg.get());
+        CLD_LAUNCH_CHECK();
+    }
+    keys.release(); keys2.release(); vals.release(); vals2.release(); flagsb.release(); excl.release();
+
+    DBuf<uint64_t> off;
+    DBuf<uint2> adj;
+    CLD_TRY(off.alloc((size_t)n + 1, s));
+    CLD_TRY(adj.alloc(nnz ? nnz : 1, s));
+    CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n, scal.get() + 2, s));
+    k_widen_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, nnz, off.get());
+    CLD_LAUNCH_CHECK();
+    if (nnz) {
+        k_pack_adj<<<grid_for(nnz, 256), 256, 0, s>>>(col.get(), wmin.get(), nnz, adj.get());
+        CLD_LAUNCH_CHECK();
+    }
+    col.release(); wmin.release();
+
+    uint32_t n_out = n;
+    uint64_t nnz_out = nnz;
+    DBuf<uint32_t> orig;
+    if (flags & CLDIAM_CSR_LCC) {
+        DBuf<uint32_t> parent, size, keep, newid;
+        DBuf<unsigned long long> best;
+        CLD_TRY(parent.alloc(n, s));
+        CLD_TRY(best.alloc(1, s));
+        k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n);
+        CLD_LAUNCH_CHECK();
+        for (int it = 0; nnz > 0; ++it) {
+            CLD_CUDA(cudaMemsetAsync(scal.get() + 3, 0, 4, s));
+            k_cc_hook<<<grid_for(nnz, 256), 256, 0, s>>>(row.get(), adj.get(), nnz, parent.get(), scal.get() + 3);
+            CLD_LAUNCH_CHECK();
+            k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n);
+            CLD_LAUNCH_CHECK();
+            CLD_CUDA(cudaMemcpyAsync(hbad + 3, scal.get() + 3, 4, cudaMemcpyDeviceToHost, s));
+            CLD_CUDA(cudaStreamSynchronize(s));
+            if (!hbad[3]) break;
+            if (it > 10000) return fail(CLDIAM_ERR_CUDA, "connected components did not converge");
+        }
+        CLD_TRY(size.alloc(n, s));
+        CLD_CUDA(cudaMemsetAsync(size.get(), 0, (size_t)n * 4, s));
+        CLD_CUDA(cudaMemsetAsync(best.get(), 0, 8, s));
+        k_cc_count<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, size.get());
+        CLD_LAUNCH_CHECK();
+        k_cc_best<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), size.get(), n, best.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(keep.alloc(n, s));
+        CLD_TRY(newid.alloc(n, s));
+        k_cc_keep<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, best.get(), keep.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(scan_exclusive_u32(keep.get(), newid.get(), n, scal.get() + 4, s));
+        CLD_CUDA(cudaMemcpyAsync(hbad + 4, scal.get() + 4, 4, cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        n_out = hbad[4];
+        CLD_TRY(orig.alloc(n_out, s));
+        CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
+        k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), n, deg.get(), orig.get());
+        CLD_LAUNCH_CHECK();
+        CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n_out, scal.get() + 5, s));
+        CLD_CUDA(cudaMemcpyAsync(hbad + 5, scal.get() + 5, 4, cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        nnz_out = hbad[5];
+        DBuf<uint64_t> noff;
+        DBuf<uint2> nadj;
+        DBuf<uint32_t> nrow;
+        CLD_TRY(noff.alloc((size_t)n_out + 1, s));
+        CLD_TRY(nadj.alloc(nnz_out ? nnz_out : 1, s));
+        CLD_TRY(nrow.alloc(nnz_out ? nnz_out : 1, s));
+        k_widen_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
+                                                                          noff.get());
+        CLD_LAUNCH_CHECK();
+        if (nnz) {
+            k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), row.get(), adj.get(),
+                                                          nnz, noff.get(), nrow.get(), nadj.get());
+            CLD_LAUNCH_CHECK();
+        }
+        g->off = noff.detach();
+        g->adj = nadj.detach();
+        g->row = nrow.detach();
+    } else {
+        CLD_TRY(orig.alloc(n, s));
+        k_iota<<<grid_for(n, 256), 256, 0, s>>>(orig.get(), n);
+        CLD_LAUNCH_CHECK();
+        g->off = off.detach();
+        g->adj = adj.detach();
+        g->row = row.detach();
+    }
+    g->orig = orig.detach();
+    g->n = n_out;
+    g->nnz = nnz_out;
+
+    // weight statistics for the initial Delta (Algorithm 1 / Section 5)
+    DBuf<unsigned long long> wsum;
+    CLD_TRY(wsum.alloc(1, s));
+    CLD_CUDA(cudaMemsetAsync(wsum.get(), 0, 8, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
+    if (g->nnz) {
+        k_graph_stats<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, wsum.get(), scal.get() + 6);
+        CLD_LAUNCH_CHECK();
+    }
+    k_degree_max<<<grid_for(g->n, 256), 256, 0, s>>>(g->off, g->n, scal.get() + 7);
+    CLD_LAUNCH_CHECK();
+    uint64_t* hsum = reinterpret_cast<uint64_t*>(static_cast<char*>(g->host.h) + 64);
+    CLD_CUDA(cudaMemcpyAsync(hsum, wsum.get(), 8, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaMemcpyAsync(hbad + 6, scal.get() + 6, 8, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    g->wsum_upper = *hsum;
+    g->wmin = hbad[6];
+    g->max_deg = hbad[7];
+    *out = owner.release();
+    return CLDIAM_OK;
+}
+
+cldiam_status delta0(const cldiam_graph* g, int mode, uint32_t explicit_value, uint32_t* out) {
+    if (mode == CLDIAM_DELTA0_EXPLICIT) {
+        if (explicit_value == 0) return fail(CLDIAM_ERR_INVALID_ARG, "explicit delta0 must be >= 1");
+        *out = explicit_value > kDeltaMax ? kDeltaMax : explicit_value;
+        return CLDIAM_OK;
+    }
+    if (g->nnz == 0) {
+        *out = 1;
+        return CLDIAM_OK;
+    }
+    if (mode == CLDIAM_DELTA0_MIN) {
+        *out = g->wmin;
+        return CLDIAM_OK;
+    }
+    if (mode != CLDIAM_DELTA0_AVG) return fail(CLDIAM_ERR_INVALID_ARG, "unknown delta0 mode");
+    uint64_t avg = g->wsum_upper / (g->nnz / 2);
+    if (avg < 1) avg = 1;
+    if (avg > kDeltaMax) avg = kDeltaMax;
+    *out = (uint32_t)avg;
+    return CLDIAM_OK;
+}
+
+}  // namespace cld

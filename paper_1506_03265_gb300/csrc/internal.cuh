@@ -1,0 +1,69 @@
+// Library handles and cross-file entry points of the CL-DIAM CUDA library.
+#pragma once
+
+#include "common.cuh"
+
+// Device-resident symmetric CSR (Section 2 graph model).
+struct cldiam_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t n = 0;
+    uint64_t nnz = 0;            // directed entries = 2 x undirected edges
+    uint64_t* off = nullptr;     // [n+1]
+    uint2* adj = nullptr;        // [nnz] (col, w), rows sorted by col
+    uint32_t* row = nullptr;     // [nnz] row of each entry (COO view for edge-parallel passes)
+    uint32_t* orig = nullptr;    // [n] original id
+    uint64_t wsum_upper = 0;     // sum of weights over u < v entries
+    uint32_t wmin = 0;
+    uint32_t max_deg = 0;
+    cld::Pinned host;            // small pinned block for counter read-back
+};
+
+struct cldiam_clustering {
+    cldiam_graph* g = nullptr;
+    uint32_t* center = nullptr;  // [n] center node id
+    uint32_t* D = nullptr;       // [n] upper bound on dist_G(center, v)
+    uint32_t* cid = nullptr;     // [n] cluster id (rank of the center id)
+    uint32_t k = 0;
+    uint32_t max_fw_k = 8192;
+    cldiam_result stats{};
+};
+
+struct cldiam_quotient {
+    const cldiam_clustering* c = nullptr;
+    cudaStream_t stream = nullptr;
+    uint32_t k = 0;
+    uint64_t nnz = 0;
+    uint64_t* off = nullptr;  // [k+1]
+    uint32_t* col = nullptr;  // [nnz]
+    uint32_t* w = nullptr;    // [nnz]
+    uint32_t max_fw_k = 8192;
+};
+
+namespace cld {
+
+cudaStream_t resolve_stream(void* user_stream);
+// Copy `bytes` from a host-or-device pointer into a fresh device buffer unless
+// it already is device memory (then *dev = src, *owned = false).
+cldiam_status to_device(const void* src, size_t bytes, cudaStream_t s, void** dev, bool* owned);
+bool is_device_ptr(const void* p);
+
+cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
+                        uint32_t flags, cudaStream_t s, cldiam_graph** out);
+void free_graph(cldiam_graph* g);
+
+cldiam_status delta0(const cldiam_graph* g, int mode, uint32_t explicit_value, uint32_t* out);
+cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* o, cldiam_clustering** out);
+void free_clustering(cldiam_clustering* c);
+
+cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out);
+void free_quotient(cldiam_quotient* q);
+
+// Largest finite APSP distance of a k-node CSR already on the device.
+cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                              uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate);
+
+cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
+                         uint64_t* rounds);
+
+}  // namespace cld

@@ -1,0 +1,218 @@
+"""GPU path vs the CPU oracle, element by element (integers: bit-exact).
+
+Every call goes through the C ABI (libcldiam.so via the Python binding).
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cd():
+    import paper_1506_03265_gb300 as m
+    m.load()
+    return m
+
+
+def rand_edges(seed, n=None, m=None, wmax=50, loops=True):
+    rng = np.random.default_rng(seed)
+    n = n or int(rng.integers(2, 400))
+    m = m if m is not None else int(rng.integers(n // 2, 4 * n))
+    src = rng.integers(0, n, m).astype(np.uint32)
+    dst = rng.integers(0, n, m).astype(np.uint32)
+    if not loops:
+        dst = np.where(src == dst, (dst + 1) % n, dst).astype(np.uint32)
+    w = rng.integers(1, wmax + 1, m).astype(np.uint32)
+    return n, src, dst, w
+
+
+def check_csr(cd, n, src, dst, w, lcc):
+    g = cd.build_csr(src, dst, w, n, lcc=lcc)
+    og = oracle.build_csr(n, src, dst, w, lcc=lcc)
+    off, col, ww, orig = g.copy()
+    assert g.n == og.n and g.nnz == og.nnz
+    assert np.array_equal(off, og.off)
+    assert np.array_equal(col, og.col)
+    assert np.array_equal(ww, og.wt)
+    assert np.array_equal(orig, og.orig)
+    return g, og
+
+
+def check_cluster(cd, g, og, tau, seed, mode=0):
+    c = cd.cluster(g, tau, seed, delta0_mode=mode)
+    d0 = oracle.delta0(og, mode)
+    assert g.delta0(mode) == d0
+    ocl = oracle.cluster(og, tau, seed, d0)
+    center, D, cid = c.copy()
+    assert np.array_equal(center, ocl.center)
+    assert np.array_equal(D.astype(np.uint64), ocl.D)
+    info = c.info()
+    for f in ("stages", "steps", "doublings", "delta_end", "guard_exits", "node_updates", "centers_drawn"):
+        assert info[f] == ocl.stats[f], f
+    q = cd.quotient_build(c)
+    oq = oracle.quotient(og, ocl)
+    assert np.array_equal(cid, oq.cid)
+    qoff, qcol, qw = q.copy()
+    assert q.info()[0] == oq.k
+    assert np.array_equal(qoff, oq.off)
+    assert np.array_equal(qcol, oq.col)
+    assert np.array_equal(qw.astype(np.uint64), oq.w)
+    r = cd.estimate(q)
+    ores = oracle.estimate(oq, ocl)
+    assert (r["k"], r["phi_gc"], r["radius"], r["phi_approx"]) == (ores.k, ores.phi_gc, ores.radius, ores.phi_approx)
+    return r
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("lcc", [True, False])
+def test_csr_random(cd, seed, lcc):
+    check_csr(cd, *rand_edges(seed), lcc)
+
+
+def test_csr_degenerate(cd):
+    z = np.zeros(0, np.uint32)
+    g = cd.build_csr(z, z, z, 1)
+    assert g.n == 1 and g.nnz == 0
+    s = np.array([0, 1, 2], np.uint32)
+    g = cd.build_csr(s, s, np.ones(3, np.uint32), 3)
+    assert g.n == 1 and g.nnz == 0
+    with pytest.raises(cd.CldiamError):
+        cd.build_csr(np.array([0], np.uint32), np.array([5], np.uint32), np.array([1], np.uint32), 3)
+    with pytest.raises(cd.CldiamError):
+        cd.build_csr(np.array([0], np.uint32), np.array([1], np.uint32), np.array([0], np.uint32), 3)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_cluster_random_connected(cd, seed):
+    n, s, d, w = rand_edges(100 + seed)
+    g, og = check_csr(cd, n, s, d, w, True)
+    for tau in (0.05, 0.3):
+        check_cluster(cd, g, og, tau, seed)
+    check_cluster(cd, g, og, 0.1, seed, mode=1)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cluster_disconnected_guard(cd, seed):
+    # no LCC: some components start without a center, which exercises the fixed-point guard
+    n, s, d, w = rand_edges(200 + seed, n=300, m=200)
+    g, og = check_csr(cd, n, s, d, w, False)
+    check_cluster(cd, g, og, 0.2, seed)
+
+
+def test_cluster_all_singletons(cd):
+    n, s, d, w = rand_edges(7, n=50, m=120)
+    g, og = check_csr(cd, n, s, d, w, True)
+    r = check_cluster(cd, g, og, 1e6, 3)
+    assert r["k"] == g.n and r["stages"] == 0
+
+
+def test_single_node(cd):
+    z = np.zeros(0, np.uint32)
+    g = cd.build_csr(z, z, z, 1)
+    c = cd.cluster(g, 1.0, 1)
+    r = cd.estimate(cd.quotient_build(c))
+    assert r["k"] == 1 and r["phi_approx"] == 0
+
+
+@pytest.mark.parametrize("side,W", [(16, 10), (33, 100), (64, 100)])
+def test_meshes(cd, side, W):
+    e = inputs.grid(side, W, side)
+    g, og = check_csr(cd, e.n, e.src, e.dst, e.w, True)
+    for tau in (0.1, 0.3, 1.0):
+        check_cluster(cd, g, og, tau, side)
+
+
+@pytest.mark.parametrize("scale", [8, 11, 14])
+def test_rmat(cd, scale):
+    e = inputs.rmat(scale, 8, 1000, scale)
+    g, og = check_csr(cd, e.n, e.src, e.dst, e.w, True)
+    for tau in (0.5, 2.0):
+        check_cluster(cd, g, og, tau, scale)
+
+
+def test_road_mesh(cd):
+    e = inputs.road_mesh(128, 1000, 3)
+    g, og = check_csr(cd, e.n, e.src, e.dst, e.w, True)
+    check_cluster(cd, g, og, 0.5, 3)
+
+
+def test_grid64_workload(cd):
+    from inputs.workloads import WORKLOADS
+    wl = WORKLOADS["grid64"]
+    e = wl.make()
+    g, og = check_csr(cd, e.n, e.src, e.dst, e.w, True)
+    r = check_cluster(cd, g, og, wl.tau, wl.seed)
+    assert r["phi_approx"] >= 3164  # >= the farthest-node lower bound of this mesh (oracle, 4 sweeps)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sssp_delta(cd, seed):
+    n, s, d, w = rand_edges(300 + seed, wmax=1000)
+    g, og = check_csr(cd, n, s, d, w, False)
+    src = cd.sssp_source(g, seed)
+    assert src == oracle.sssp_source(seed, g.n)
+    ref = oracle.dijkstra(og, src)
+    for delta in (0, 1, 37, 5000):
+        dist, ecc, rounds = cd.sssp_delta(g, src, delta)
+        ref32 = np.where(ref == oracle.UNREACHABLE, 0xFFFFFFFF, ref).astype(np.uint64)
+        assert np.array_equal(dist.astype(np.uint64), ref32)
+        assert ecc == int(ref[ref != oracle.UNREACHABLE].max())
+
+
+def test_sssp_workload_shapes(cd):
+    for e in (inputs.grid(64, 100, 1), inputs.rmat(14, 16, 1 << 20, 2), inputs.road_mesh(96, 1000, 3)):
+        g, og = check_csr(cd, e.n, e.src, e.dst, e.w, True)
+        src = cd.sssp_source(g, 5)
+        dist, ecc, _ = cd.sssp_delta(g, src)
+        assert np.array_equal(dist.astype(np.uint64), oracle.dijkstra(og, src))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_apsp_max(cd, seed):
+    rng = np.random.default_rng(seed)
+    for k in (1, 2, 31, 32, 33, 70):
+        n, s, d, w = rand_edges(seed * 100 + k, n=k, m=3 * k, wmax=1 << 20)
+        og = oracle.build_csr(n, s, d, w, lcc=False)
+        q = oracle.Quotient(og.n, np.arange(og.n, dtype=np.uint32), og.off, og.col, og.wt.astype(np.uint64))
+        assert cd.apsp_max(og.n, og.off, og.col, og.wt) == oracle.apsp_max(q)
+
+
+def test_overflow_is_reported(cd):
+    # a path whose length exceeds 2^32 - 1: the SSSP must refuse, not wrap
+    n = 4
+    s = np.array([0, 1, 2], np.uint32); d = np.array([1, 2, 3], np.uint32)
+    w = np.array([0xF0000000, 0xF0000000, 5], np.uint32)
+    g = cd.build_csr(s, d, w, n)
+    with pytest.raises(cd.CldiamError) as ei:
+        cd.sssp_delta(g, 0)
+    assert ei.value.status == -3
+
+
+def test_determinism(cd):
+    e = inputs.rmat(12, 8, 1000, 9)
+    g = cd.build_csr(e.src, e.dst, e.w, e.n)
+    a = cd.cluster(g, 1.0, 4).copy()
+    b = cd.cluster(g, 1.0, 4).copy()
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_run_entry_point(cd):
+    e = inputs.grid(40, 100, 2)
+    r = cd.run(e.src, e.dst, e.w, e.n, 0.3, 2)
+    og = oracle.build_csr(e.n, e.src, e.dst, e.w)
+    ores, _, _ = oracle.cldiam(og, 0.3, 2)
+    assert (r["k"], r["phi_approx"]) == (ores.k, ores.phi_approx)
+
+
+def test_device_inputs(cd):
+    torch = pytest.importorskip("torch")
+    e = inputs.grid(32, 100, 3)
+    t = [torch.from_numpy(a.astype(np.int32)).cuda() for a in (e.src, e.dst, e.w)]
+    g = cd.build_csr(t[0], t[1], t[2], e.n)
+    og = oracle.build_csr(e.n, e.src, e.dst, e.w)
+    off, col, w, _ = g.copy()
+    assert np.array_equal(off, og.off) and np.array_equal(col, og.col)
