@@ -200,6 +200,23 @@ cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_
                          uint32_t flags, double tau, uint64_t seed, const cldiam_opts* opts, void* stream,
                          cldiam_result* out);
 
+/* ------------------------------------------------------------------------
+ * Instrumentation.  No counterpart in the method itself; it exposes what the
+ * paper measures (rounds and work, Table 2) plus per-kernel device time.
+ * Kernel classes: 0 relax, 1 snapshot, 2 rebuild, 3 select, 4 finalize,
+ * 5 growable, 6 radix_hist, 7 radix_scatter, 8 scan, 9 csr, 10 components,
+ * 11 quotient, 12 floyd_warshall, 13 delta_stepping, 14 reduce, 15 misc.
+ * Process-wide; not meant for concurrent use from several threads.
+ */
+/* Bit i set: bracket every launch of class i with CUDA events on its stream. 0 = off (default). */
+cldiam_status cldiam_profile_set_timing(uint32_t class_mask);
+/* Zero all counters (waits for pending timing events). */
+cldiam_status cldiam_profile_reset(void);
+uint32_t cldiam_profile_num_classes(void);
+/* Launch count, summed event time (ms, timed classes only) and algorithmic bytes of one class since
+ * the last reset; *name is a static string.  Any output pointer may be NULL. */
+cldiam_status cldiam_profile_get(uint32_t cls, const char** name, uint64_t* launches, double* ms, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

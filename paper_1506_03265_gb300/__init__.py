@@ -98,6 +98,10 @@ def load(build_if_missing: bool = True):
             "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
             "cldiam_run": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                 ctypes.c_uint64, P, P, P]),
+            "cldiam_profile_set_timing": (st, [ctypes.c_uint32]),
+            "cldiam_profile_reset": (st, []),
+            "cldiam_profile_num_classes": (ctypes.c_uint32, []),
+            "cldiam_profile_get": (st, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p), P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -297,6 +301,34 @@ def sssp_delta(g: Graph, source: int, delta: int = 0, want_dist: bool = True):
     _check(load().cldiam_sssp_delta(g.handle, source, delta, _ptr(dist), ctypes.byref(ecc), ctypes.byref(rounds)),
            "cldiam_sssp_delta")
     return dist, ecc.value, rounds.value
+
+
+KERNEL_CLASSES = ["relax", "snapshot", "rebuild", "select", "finalize", "growable", "radix_hist", "radix_scatter",
+                  "scan", "csr", "components", "quotient", "floyd_warshall", "delta_stepping", "reduce", "misc"]
+
+
+def profile_set_timing(classes) -> None:
+    """Time every launch of the named kernel classes with CUDA events (empty = off)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KERNEL_CLASSES.index(c)
+    _check(load().cldiam_profile_set_timing(mask), "cldiam_profile_set_timing")
+
+
+def profile_reset() -> None:
+    _check(load().cldiam_profile_reset(), "cldiam_profile_reset")
+
+
+def profile_get() -> dict:
+    """{class: {"launches", "ms", "bytes"}} since the last reset."""
+    lib = load()
+    out = {}
+    for i in range(lib.cldiam_profile_num_classes()):
+        name = ctypes.c_char_p(); L = ctypes.c_uint64(); ms = ctypes.c_double(); b = ctypes.c_double()
+        _check(lib.cldiam_profile_get(i, ctypes.byref(name), ctypes.byref(L), ctypes.byref(ms), ctypes.byref(b)),
+               "cldiam_profile_get")
+        out[name.value.decode()] = {"launches": L.value, "ms": ms.value, "bytes": b.value}
+    return out
 
 
 def run(src, dst, w, n: int, tau: float, seed: int, lcc: bool = True, delta0_mode=DELTA0_AVG, stream=None) -> dict:

@@ -10,6 +10,7 @@
 // of two finite entries that reaches 2^32 - 1 raises the overflow flag
 // instead of wrapping.
 #include "internal.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -153,7 +154,7 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     CLD_TRY(scal.alloc(3, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 12, s));
     if (validate) {
-        k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, scal.get() + 2);
+        CLD_K(K_FW, s, k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, scal.get() + 2));
         CLD_LAUNCH_CHECK();
         uint32_t bad = 0;
         CLD_CUDA(cudaMemcpyAsync(&bad, scal.get() + 2, 4, cudaMemcpyDeviceToHost, s));
@@ -161,18 +162,18 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
         if (bad) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
     }
     CLD_TRY(M.alloc((size_t)kp * kp, s));
-    k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M.get(), kp, k);
-    k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M.get());
+    CLD_K(K_FW, s, k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M.get(), kp, k));
+    CLD_K(K_FW, s, k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M.get()));
     CLD_LAUNCH_CHECK();
     for (uint32_t r = 0; r < nt; ++r) {
-        k_fw_phase1<<<1, T * T, 0, s>>>(M.get(), kp, r, scal.get());
+        CLD_K(K_FW, s, k_fw_phase1<<<1, T * T, 0, s>>>(M.get(), kp, r, scal.get()));
         if (nt > 1) {
-            k_fw_phase2<<<2 * (nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get());
-            k_fw_phase3<<<dim3(nt - 1, nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get());
+            CLD_K(K_FW, s, k_fw_phase2<<<2 * (nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get()));
+            CLD_K(K_FW, s, k_fw_phase3<<<dim3(nt - 1, nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get()));
         }
         CLD_LAUNCH_CHECK();
     }
-    k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M.get(), kp, k, scal.get() + 1);
+    CLD_K(K_FW, s, k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M.get(), kp, k, scal.get() + 1));
     CLD_LAUNCH_CHECK();
     uint32_t h[2];
     CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 8, cudaMemcpyDeviceToHost, s));

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -28,15 +29,38 @@ struct Counters {
     unsigned long long newly_covered;  // nodes that got their first key this step
     unsigned long long edges_scanned;  // adjacency entries read by relax
     unsigned long long frozen;         // nodes frozen by finalize
+    unsigned long long frozen_deg;     // their degree sum
+    unsigned long long front;          // next frontier: (entries << 32) | adjacency entries
     uint32_t nnext;                    // changed nodes this step
-    uint32_t nfront;                   // entries of the next frontier
     uint32_t growable;                 // some covered/frozen node touches an uncovered one
     uint32_t overflow;                 // a D_v reached 2^32 - 1
+    uint32_t pad;
 };
+
+constexpr unsigned long long kPull = kInfKey;  // frontier key marking a pull entry
 
 __device__ __forceinline__ void warp_add_u64(unsigned long long* p, unsigned long long v) {
     v = warp_sum(v);
     if (lane_id() == 0 && v) atomicAdd(p, v);
+}
+
+// Append to the frontier: one packed atomicAdd per warp hands out both the
+// entry slot (high word) and the entry's first position in the flattened
+// edge list (low word), so positions increase with slots and the frontier's
+// degree prefix needs no separate scan.  All lanes must call it.
+__device__ __forceinline__ void front_append(unsigned long long* ctr, bool pred, uint32_t deg, uint32_t& slot,
+                                             uint32_t& pre) {
+    unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (mask == 0) return;
+    uint32_t d = pred ? deg : 0u;
+    uint32_t incl = warp_incl_scan(d);
+    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane_id() == leader) base = atomicAdd(ctr, ((unsigned long long)__popc(mask) << 32) | total);
+    base = __shfl_sync(0xffffffffu, base, leader);
+    slot = (uint32_t)(base >> 32) + (uint32_t)__popc(mask & lanemask_lt());
+    pre = (uint32_t)base + (incl - d);
 }
 
 // a3: draw the new centers of this stage among unfrozen nodes, reset the others.
@@ -55,97 +79,166 @@ __global__ void k_select(uint32_t n, const uint32_t* __restrict__ center, unsign
     warp_add_u64(&ctr->selected, cnt);
 }
 
-// a4: list every relaxer with its current key: unfrozen nodes with d < Delta,
-// and frozen nodes as (0, c_u).
+// a4: list every relaxer with its current key: unfrozen nodes with d < Delta
+// push their key; the contracted clusters either push (0, c_u) from every
+// frozen u, or (pull mode) every unfrozen node lists itself to pull
+// (w, c_u) from its frozen neighbours -- the same candidates, read from the
+// side with fewer adjacency entries.
 __global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
-                          uint32_t delta, uint32_t* __restrict__ fv, unsigned long long* __restrict__ fkey,
-                          Counters* ctr) {
+                          const uint64_t* __restrict__ off, uint32_t delta, bool pull, uint32_t* __restrict__ fv,
+                          unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         uint32_t v = base + threadIdx.x;
-        bool take = false;
+        bool push = false, pl = false;
         unsigned long long k = 0;
+        uint32_t deg = 0;
         if (v < n) {
+            deg = (uint32_t)(off[v + 1] - off[v]);
             uint32_t c = center[v];
-            if (c != kNone) {
-                take = true;
-                k = c;  // (0, c_u)
-            } else {
-                k = key[v];
-                take = k != kInfKey && (uint32_t)(k >> 32) < delta;
+            if (deg > 0) {
+                if (c != kNone) {
+                    push = !pull;
+                    k = c;  // (0, c_u)
+                } else {
+                    k = key[v];
+                    push = k != kInfKey && (uint32_t)(k >> 32) < delta;
+                    pl = pull;
+                }
             }
         }
-        uint32_t slot = warp_append(&ctr->nfront, take);
-        if (take) {
+        uint32_t slot = 0, pre = 0;
+        front_append(&ctr->front, push, deg, slot, pre);
+        if (push) {
             fv[slot] = v;
             fkey[slot] = k;
+            fpre[slot] = pre;
+        }
+        front_append(&ctr->front, pl, deg, slot, pre);
+        if (pl) {
+            fv[slot] = v;
+            fkey[slot] = kPull;
+            fpre[slot] = pre;
         }
     }
 }
 
-// a5: one synchronous Delta-growing step, one warp per frontier entry.
-__global__ void __launch_bounds__(256) k_relax(const uint32_t* __restrict__ fv, const unsigned long long* __restrict__ fkey,
-                                               uint32_t nf, const uint64_t* __restrict__ off,
-                                               const uint2* __restrict__ adj, unsigned long long* __restrict__ key,
-                                               uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
-                                               uint32_t* __restrict__ next, Counters* ctr) {
-    const uint32_t lane = lane_id();
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long newly = 0, scanned = 0;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nf; i += warps) {
-        const uint32_t u = fv[i];
-        const unsigned long long ku = fkey[i];
-        const uint64_t du = ku >> 32;
-        const unsigned long long cu = ku & 0xFFFFFFFFull;
-        const uint64_t beg = off[u], end = off[u + 1];
-        scanned += (end - beg);
-        for (uint64_t b = beg; b < end; b += 32) {
-            const uint64_t j = b + lane;
+constexpr int RT = 256;   // relax threads per CTA
+constexpr int RC = 1024;  // adjacency entries per chunk
+
+// a5: one synchronous Delta-growing step over the frontier, edge-balanced:
+// the frontier's adjacency lists are viewed as one flattened range of E
+// entries cut into chunks of RC; each CTA takes chunks, loads the frontier
+// entries the chunk spans into shared memory and maps every entry position to
+// its frontier entry by binary search, so hubs spread over many CTAs.
+__global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, const unsigned long long* __restrict__ fkey,
+                                              const uint32_t* __restrict__ fpre, uint32_t nf, uint32_t E,
+                                              const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
+                                              const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
+                                              uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
+                                              uint32_t* __restrict__ next, Counters* ctr) {
+    __shared__ uint32_t s_pre[RC];
+    __shared__ uint32_t s_beg[RC];
+    __shared__ uint32_t s_v[RC];
+    __shared__ unsigned long long s_key[RC];
+    __shared__ uint32_t s_i0, s_cnt;
+    const uint32_t tid = threadIdx.x;
+    unsigned long long newly = 0;
+    for (uint32_t chunk = blockIdx.x; (uint64_t)chunk * RC < E; chunk += gridDim.x) {
+        const uint32_t e0 = chunk * RC;
+        const uint32_t e1 = min(E, e0 + RC);
+        if (tid == 0) {
+            uint32_t lo = 0, hi = nf - 1;  // last entry starting at or before e0
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (fpre[mid] <= e0) lo = mid; else hi = mid - 1;
+            }
+            uint32_t i0 = lo;
+            hi = nf - 1;                    // last entry starting at or before e1 - 1
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (fpre[mid] <= e1 - 1) lo = mid; else hi = mid - 1;
+            }
+            s_i0 = i0;
+            s_cnt = lo - i0 + 1;
+        }
+        __syncthreads();
+        const uint32_t i0 = s_i0, cnt = s_cnt;  // cnt <= RC: every entry has >= 1 adjacency entry
+        for (uint32_t j = tid; j < cnt; j += RT) {
+            uint32_t v = fv[i0 + j];
+            s_pre[j] = fpre[i0 + j];
+            s_v[j] = v;
+            s_key[j] = fkey[i0 + j];
+            s_beg[j] = (uint32_t)off[v];
+        }
+        __syncthreads();
+        uint32_t jlo = 0;
+        for (uint32_t base = e0; base < e1; base += RT) {
+            const uint32_t e = base + tid;
             bool changed_first = false;
-            uint32_t v = 0;
-            if (j < end) {
-                const uint2 e = adj[j];
-                v = e.x;
-                const uint64_t cand = du + e.y;
-                if (cand <= delta) {
-                    const unsigned long long nk = (cand << 32) | cu;
-                    if (nk < key[v]) {
-                        const unsigned long long old = atomicMin(&key[v], nk);
-                        if (nk < old) {
-                            newly += (old == kInfKey) ? 1 : 0;
-                            changed_first = atomicExch(&stamp[v], stepid) != stepid;
-                        }
+            uint32_t target = 0;
+            if (e < e1) {
+                uint32_t lo = jlo, hi = cnt - 1;
+                while (lo < hi) {
+                    uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                jlo = lo;
+                const uint2 ed = adj[s_beg[lo] + (e - s_pre[lo])];
+                const unsigned long long ku = s_key[lo];
+                unsigned long long nk = kInfKey;
+                if (ku != kPull) {
+                    const uint64_t cand = (ku >> 32) + ed.y;
+                    if (cand <= delta) {
+                        target = ed.x;
+                        nk = (cand << 32) | (ku & 0xFFFFFFFFull);
+                    }
+                } else if (ed.y <= delta) {
+                    const uint32_t cu = center[ed.x];
+                    if (cu != kNone) {
+                        target = s_v[lo];
+                        nk = ((unsigned long long)ed.y << 32) | cu;
+                    }
+                }
+                if (nk != kInfKey && nk < key[target]) {
+                    const unsigned long long old = atomicMin(&key[target], nk);
+                    if (nk < old) {
+                        newly += (old == kInfKey) ? 1 : 0;
+                        changed_first = atomicExch(&stamp[target], stepid) != stepid;
                     }
                 }
             }
             uint32_t slot = warp_append(&ctr->nnext, changed_first);
-            if (changed_first) next[slot] = v;
+            if (changed_first) next[slot] = target;
         }
+        __syncthreads();  // the next chunk reuses the shared arrays
     }
-    scanned = (lane == 0) ? scanned : 0;  // every lane holds the warp's count: keep one
-    warp_add_u64(&ctr->edges_scanned, scanned);
     warp_add_u64(&ctr->newly_covered, newly);
 }
 
 // the changed nodes become the next frontier, with their end-of-step keys
 // (read after the step kernel has finished, so they are the next step's
 // start-of-step values); nodes that reached d = Delta do not relax.
-__global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned long long* __restrict__ key, uint32_t delta,
-                           uint32_t* __restrict__ fv, unsigned long long* __restrict__ fkey, Counters* ctr) {
+__global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned long long* __restrict__ key,
+                           const uint64_t* __restrict__ off, uint32_t delta, uint32_t* __restrict__ fv,
+                           unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
     const uint32_t nn = ctr->nnext;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nn; base += gridDim.x * blockDim.x) {
         uint32_t i = base + threadIdx.x;
         bool take = false;
-        uint32_t v = 0;
+        uint32_t v = 0, deg = 0;
         unsigned long long k = 0;
         if (i < nn) {
             v = next[i];
             k = key[v];
-            take = (uint32_t)(k >> 32) < delta;
+            deg = (uint32_t)(off[v + 1] - off[v]);
+            take = (uint32_t)(k >> 32) < delta && deg > 0;
         }
-        uint32_t slot = warp_append(&ctr->nfront, take);
+        uint32_t slot = 0, pre = 0;
+        front_append(&ctr->front, take, deg, slot, pre);
         if (take) {
             fv[slot] = v;
             fkey[slot] = k;
+            fpre[slot] = pre;
         }
     }
 }
@@ -178,8 +271,9 @@ __global__ void k_finalize_d(uint32_t n, const unsigned long long* __restrict__ 
 
 // a7 (part 2): freeze them (key 0), record the center, grow R[c].
 __global__ void k_finalize_freeze(uint32_t n, unsigned long long* __restrict__ key, uint32_t* __restrict__ center,
-                                  uint32_t* __restrict__ R, const uint32_t* __restrict__ D, Counters* ctr) {
-    unsigned long long cnt = 0;
+                                  uint32_t* __restrict__ R, const uint32_t* __restrict__ D, const uint64_t* __restrict__ off,
+                                  Counters* ctr) {
+    unsigned long long cnt = 0, degs = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (center[v] != kNone) continue;
         unsigned long long k = key[v];
@@ -189,8 +283,10 @@ __global__ void k_finalize_freeze(uint32_t n, unsigned long long* __restrict__ k
         key[v] = 0;
         atomicMax(&R[c], D[v]);
         ++cnt;
+        degs += off[v + 1] - off[v];
     }
     warp_add_u64(&ctr->frozen, cnt);
+    warp_add_u64(&ctr->frozen_deg, degs);
 }
 
 // a8: leftover nodes become singleton clusters.
@@ -257,9 +353,11 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     cl->g = g;
     cl->max_fw_k = opts.max_fw_k ? opts.max_fw_k : 8192u;
 
+    // a frontier lists each node at most twice (push + pull entry)
+    const size_t fcap = 2 * (size_t)n;
     DBuf<uint32_t> center, D, cid;
     DBuf<unsigned long long> key, fkeyA, fkeyB;
-    DBuf<uint32_t> R, stamp, fvA, fvB, next;
+    DBuf<uint32_t> R, stamp, fvA, fvB, fpA, fpB, next;
     DBuf<Counters> ctr;
     CLD_TRY(center.alloc(n, s));
     CLD_TRY(D.alloc(n, s));
@@ -267,30 +365,32 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     CLD_TRY(key.alloc(n, s));
     CLD_TRY(R.alloc(n, s));
     CLD_TRY(stamp.alloc(n, s));
-    CLD_TRY(fvA.alloc(n, s));
-    CLD_TRY(fvB.alloc(n, s));
-    CLD_TRY(fkeyA.alloc(n, s));
-    CLD_TRY(fkeyB.alloc(n, s));
+    CLD_TRY(fvA.alloc(fcap, s));
+    CLD_TRY(fvB.alloc(fcap, s));
+    CLD_TRY(fpA.alloc(fcap, s));
+    CLD_TRY(fpB.alloc(fcap, s));
+    CLD_TRY(fkeyA.alloc(fcap, s));
+    CLD_TRY(fkeyB.alloc(fcap, s));
     CLD_TRY(next.alloc(n, s));
     CLD_TRY(ctr.alloc(1, s));
     Counters* hc = static_cast<Counters*>(g->host.h);
     static_assert(sizeof(Counters) <= 128, "counter block must fit the pinned area");
 
     const unsigned gb = grid_for(n, 256);
-    k_fill_u32<<<gb, 256, 0, s>>>(center.get(), n, kNone);
-    k_fill_u32<<<gb, 256, 0, s>>>(D.get(), n, 0u);
-    k_fill_u32<<<gb, 256, 0, s>>>(R.get(), n, 0u);
-    k_fill_u32<<<gb, 256, 0, s>>>(stamp.get(), n, 0u);
-    k_fill_u64<<<gb, 256, 0, s>>>(key.get(), n, kInfKey);
+    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(center.get(), n, kNone));
+    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(D.get(), n, 0u));
+    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(R.get(), n, 0u));
+    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(stamp.get(), n, 0u));
+    CLD_K(K_MISC, s, k_fill_u64<<<gb, 256, 0, s>>>(key.get(), n, kInfKey));
     CLD_LAUNCH_CHECK();
     CLD_CUDA(cudaMemsetAsync(ctr.get(), 0, sizeof(Counters), s));
 
     auto sync_counters = [&]() -> cldiam_status {
         CLD_CUDA(cudaMemcpyAsync(hc, ctr.get(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
         CLD_CUDA(cudaStreamSynchronize(s));
+        prof_flush();
         return CLDIAM_OK;
     };
-    // zero a counter field on the device
     auto zero_field = [&](size_t offset, size_t bytes) -> cldiam_status {
         CLD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(ctr.get()) + offset, 0, bytes, s));
         return CLDIAM_OK;
@@ -298,13 +398,28 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
 
     cldiam_result st{};
     const double L = std::log2((double)n);
-    uint64_t U = n;  // unfrozen nodes
+    uint64_t U = n;               // unfrozen nodes
+    uint64_t frozen_deg = 0;      // adjacency entries of frozen nodes
+    const bool pull_ok = g->nnz < 0x80000000ull;  // push + pull entries must index below 2^32
     uint32_t stage = 1, stepid = 0;
     uint32_t* fv = fvA.get();
+    uint32_t* fp = fpA.get();
     unsigned long long* fk = fkeyA.get();
     uint32_t* fv2 = fvB.get();
+    uint32_t* fp2 = fpB.get();
     unsigned long long* fk2 = fkeyB.get();
-    const unsigned relax_grid = (unsigned)num_sms() * 8;
+    const unsigned max_relax_grid = (unsigned)num_sms() * 8;
+    uint32_t nf = 0, E = 0;
+
+    // list every relaxer (stage start, or after Delta doubled)
+    auto rebuild = [&]() -> cldiam_status {
+        const bool pull = pull_ok && (g->nnz - frozen_deg) < frozen_deg;
+        CLD_TRY(zero_field(offsetof(Counters, front), 8));
+        CLD_K(K_REBUILD, s, k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), g->off, delta, pull, fv, fk, fp,
+                                                          ctr.get()));
+        CLD_LAUNCH_CHECK();
+        return CLDIAM_OK;
+    };
 
     for (;;) {
         if (U == 0) break;
@@ -316,14 +431,13 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
 
         // selection + reset, then the stage's first frontier
         CLD_TRY(zero_field(offsetof(Counters, selected), 8));
-        k_select<<<gb, 256, 0, s>>>(n, center.get(), key.get(), seed, stage, thr, ctr.get());
+        CLD_K(K_SELECT, s, k_select<<<gb, 256, 0, s>>>(n, center.get(), key.get(), seed, stage, thr, ctr.get()));
         CLD_LAUNCH_CHECK();
-        CLD_TRY(zero_field(offsetof(Counters, nfront), 4));
-        k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), delta, fv, fk, ctr.get());
-        CLD_LAUNCH_CHECK();
+        CLD_TRY(rebuild());
         CLD_TRY(sync_counters());
         uint64_t covered = hc->selected;
-        uint32_t nf = hc->nfront;
+        nf = (uint32_t)(hc->front >> 32);
+        E = (uint32_t)hc->front;
         st.centers_drawn += hc->selected;
 
         for (;;) {
@@ -333,19 +447,30 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                 updated = 0;
                 if (nf > 0) {
                     CLD_TRY(zero_field(offsetof(Counters, newly_covered), 8));
-                    CLD_TRY(zero_field(offsetof(Counters, nnext), 8));  // nnext + nfront
-                    unsigned rg = (unsigned)std::min<uint64_t>((nf + 7) / 8, relax_grid);
-                    k_relax<<<rg, 256, 0, s>>>(fv, fk, nf, g->off, g->adj, key.get(), delta, stamp.get(), stepid,
-                                               next.get(), ctr.get());
+                    CLD_TRY(zero_field(offsetof(Counters, front), 8));
+                    CLD_TRY(zero_field(offsetof(Counters, nnext), 4));
+                    const unsigned rg = (unsigned)std::min<uint64_t>((E + RC - 1) / RC, max_relax_grid);
+                    CLD_K(K_RELAX, s, k_relax<<<rg, RT, 0, s>>>(fv, fk, fp, nf, E, g->off, g->adj, center.get(),
+                                                                 key.get(), delta, stamp.get(), stepid, next.get(),
+                                                                 ctr.get()));
                     CLD_LAUNCH_CHECK();
-                    k_snapshot<<<relax_grid, 256, 0, s>>>(next.get(), key.get(), delta, fv2, fk2, ctr.get());
+                    CLD_K(K_SNAPSHOT, s, k_snapshot<<<max_relax_grid, 256, 0, s>>>(next.get(), key.get(), g->off, delta,
+                                                                                 fv2, fk2, fp2, ctr.get()));
                     CLD_LAUNCH_CHECK();
                     CLD_TRY(sync_counters());
                     updated = hc->nnext;
                     covered += hc->newly_covered;
+                    st.edges_scanned += E;
+                    // algorithmic bytes of this relax launch: per frontier entry its slot (4 + 8 + 4 B)
+                    // and row start (8 B); per adjacency entry the (col, w) pair (8 B) and the target's
+                    // key (8 B); per changed node its key, stamp and list slot (16 B)
+                    prof_add_bytes(K_RELAX, 24.0 * nf + 16.0 * (double)E + 16.0 * updated);
+                    prof_add_bytes(K_SNAPSHOT, 4.0 * updated + 8.0 * updated + 16.0 * updated + 16.0 * (hc->front >> 32));
                     std::swap(fv, fv2);
+                    std::swap(fp, fp2);
                     std::swap(fk, fk2);
-                    nf = hc->nfront;
+                    nf = (uint32_t)(hc->front >> 32);
+                    E = (uint32_t)hc->front;
                 }
                 st.steps++;
                 st.node_updates += updated;
@@ -354,7 +479,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
             bool growable = false;
             if (delta < kDeltaMax && g->nnz) {
                 CLD_TRY(zero_field(offsetof(Counters, growable), 4));
-                k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, key.get(), ctr.get());
+                CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz,
+                                                                                         key.get(), ctr.get()));
                 CLD_LAUNCH_CHECK();
                 CLD_TRY(sync_counters());
                 growable = hc->growable != 0;
@@ -365,25 +491,26 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
             }
             delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
             st.doublings++;
-            CLD_TRY(zero_field(offsetof(Counters, nfront), 4));
-            k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), delta, fv, fk, ctr.get());
-            CLD_LAUNCH_CHECK();
+            CLD_TRY(rebuild());
             CLD_TRY(sync_counters());
-            nf = hc->nfront;
+            nf = (uint32_t)(hc->front >> 32);
+            E = (uint32_t)hc->front;
         }
 
         // assign and contract
-        CLD_TRY(zero_field(offsetof(Counters, frozen), 8));
-        k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get());
-        k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get());
+        CLD_TRY(zero_field(offsetof(Counters, frozen), 16));  // frozen + frozen_deg
+        CLD_K(K_FINALIZE, s, k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get()));
+        CLD_K(K_FINALIZE, s, k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), g->off,
+                                                                  ctr.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(sync_counters());
         if (hc->overflow) return fail(CLDIAM_ERR_OVERFLOW, "a cluster distance bound reached 2^32 - 1");
         U -= hc->frozen;
+        frozen_deg += hc->frozen_deg;
         st.stages++;
         ++stage;
     }
-    k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get());
+    CLD_K(K_FINALIZE, s, k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get()));
     CLD_LAUNCH_CHECK();
 
     // relabel
@@ -391,15 +518,14 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     CLD_TRY(flag.alloc(n, s));
     CLD_TRY(rank.alloc(n, s));
     CLD_TRY(kdev.alloc(1, s));
-    k_center_flags<<<gb, 256, 0, s>>>(n, center.get(), flag.get());
+    CLD_K(K_MISC, s, k_center_flags<<<gb, 256, 0, s>>>(n, center.get(), flag.get()));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive_u32(flag.get(), rank.get(), n, kdev.get(), s));
-    k_assign_cid<<<gb, 256, 0, s>>>(n, center.get(), rank.get(), cid.get());
+    CLD_K(K_MISC, s, k_assign_cid<<<gb, 256, 0, s>>>(n, center.get(), rank.get(), cid.get()));
     CLD_LAUNCH_CHECK();
     uint32_t* hk = reinterpret_cast<uint32_t*>(static_cast<char*>(g->host.h) + 128);
     CLD_CUDA(cudaMemcpyAsync(hk, kdev.get(), 4, cudaMemcpyDeviceToHost, s));
     CLD_TRY(sync_counters());
-    st.edges_scanned = hc->edges_scanned;
     st.k = *hk;
     st.delta_end = delta;
 

@@ -9,6 +9,7 @@
 // component, so roots are component minima and the labelling is
 // deterministic.
 #include "internal.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -45,15 +46,20 @@ __global__ void k_unique(const uint64_t* __restrict__ keys, const uint32_t* __re
                          const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, uint64_t cnt,
                          uint64_t sentinel, uint32_t n, uint32_t* __restrict__ row, uint32_t* __restrict__ col,
                          uint32_t* __restrict__ wmin, uint32_t* __restrict__ deg) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        if (k >= sentinel) continue;
-        uint32_t r = excl[i] + flags[i] - 1u;
-        atomicMin(&wmin[r], vals[i]);
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < cnt; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        const uint64_t k = i < cnt ? keys[i] : sentinel;
+        const bool valid = k < sentinel;
+        // parallel edges form runs of equal keys: reduce each warp's part of a run first
+        const uint32_t v = warp_seg_min(k, valid, valid ? vals[i] : 0xFFFFFFFFu);
+        const bool tail = warp_run_tail(k, valid);  // all lanes take part in the shuffles
+        if (!valid) continue;
+        const uint32_t r = excl[i] + flags[i] - 1u;
+        if (tail) atomicMin(&wmin[r], v);
         if (flags[i]) {
-            uint32_t u = (uint32_t)(k / n), v = (uint32_t)(k - (uint64_t)u * n);
+            uint32_t u = (uint32_t)(k / n), c = (uint32_t)(k - (uint64_t)u * n);
             row[r] = u;
-            col[r] = v;
+            col[r] = c;
             atomicAdd(&deg[u], 1u);
         }
     }
@@ -105,8 +111,13 @@ __global__ void k_cc_compress(uint32_t* __restrict__ parent, uint32_t n) {
 }
 
 __global__ void k_cc_count(const uint32_t* __restrict__ parent, uint32_t n, uint32_t* __restrict__ size) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        atomicAdd(&size[parent[v]], 1u);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        const uint32_t r = v < n ? parent[v] : 0xFFFFFFFFu;
+        // most nodes share one root: one atomic per distinct root per warp
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        if (v < n && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&size[r], (uint32_t)__popc(peers));
+    }
 }
 
 // best component: largest size, then smallest root id
@@ -236,7 +247,8 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
     InFree f3{&dw, &ow, s};
 
-    const uint64_t sentinel = (uint64_t)n * (uint64_t)n;
+    // valid keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
+    const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
     const int bits = bits_for(sentinel);
     const uint64_t cnt = 2 * m;
     DBuf<uint64_t> keys, keys2;
@@ -248,9 +260,9 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(scal.alloc(8, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(uint32_t), s));
     if (m > 0) {
-        k_emit_directed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
+        CLD_K(K_CSR, s, k_emit_directed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
                                                          (const uint32_t*)dw, m, n, sentinel, keys.get(),
-                                                         vals.get(), scal.get());
+                                                         vals.get(), scal.get()));
         CLD_LAUNCH_CHECK();
     }
     CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -265,7 +277,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(flagsb.alloc(cnt ? cnt : 1, s));
     CLD_TRY(excl.alloc(cnt ? cnt : 1, s));
     if (cnt) {
-        k_head_flags<<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, sentinel, flagsb.get());
+        CLD_K(K_CSR, s, k_head_flags<<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, sentinel, flagsb.get()));
         CLD_LAUNCH_CHECK();
     }
     CLD_TRY(scan_exclusive_u32(flagsb.get(), excl.get(), cnt, scal.get() + 1, s));
@@ -282,8 +294,8 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_CUDA(cudaMemsetAsync(wmin.get(), 0xFF, (size_t)(nnz ? nnz : 1) * 4, s));
     CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
     if (cnt) {
-        k_unique<<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flagsb.get(), excl.get(), cnt, sentinel, n, row.get(),
-                                                    col.get(), wmin.get(), deg.get());
+        CLD_K(K_CSR, s, k_unique<<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flagsb.get(), excl.get(), cnt, sentinel, n, row.get(),
+                                                    col.get(), wmin.get(), deg.get()));
         CLD_LAUNCH_CHECK();
     }
     keys.release(); keys2.release(); vals.release(); vals2.release(); flagsb.release(); excl.release();
@@ -293,10 +305,10 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(off.alloc((size_t)n + 1, s));
     CLD_TRY(adj.alloc(nnz ? nnz : 1, s));
     CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n, scal.get() + 2, s));
-    k_widen_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, nnz, off.get());
+    CLD_K(K_CSR, s, k_widen_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, nnz, off.get()));
     CLD_LAUNCH_CHECK();
     if (nnz) {
-        k_pack_adj<<<grid_for(nnz, 256), 256, 0, s>>>(col.get(), wmin.get(), nnz, adj.get());
+        CLD_K(K_CSR, s, k_pack_adj<<<grid_for(nnz, 256), 256, 0, s>>>(col.get(), wmin.get(), nnz, adj.get()));
         CLD_LAUNCH_CHECK();
     }
     col.release(); wmin.release();
@@ -309,13 +321,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         DBuf<unsigned long long> best;
         CLD_TRY(parent.alloc(n, s));
         CLD_TRY(best.alloc(1, s));
-        k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n);
+        CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
         CLD_LAUNCH_CHECK();
         for (int it = 0; nnz > 0; ++it) {
             CLD_CUDA(cudaMemsetAsync(scal.get() + 3, 0, 4, s));
-            k_cc_hook<<<grid_for(nnz, 256), 256, 0, s>>>(row.get(), adj.get(), nnz, parent.get(), scal.get() + 3);
+            CLD_K(K_CC, s, k_cc_hook<<<grid_for(nnz, 256), 256, 0, s>>>(row.get(), adj.get(), nnz, parent.get(), scal.get() + 3));
             CLD_LAUNCH_CHECK();
-            k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n);
+            CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
             CLD_LAUNCH_CHECK();
             CLD_CUDA(cudaMemcpyAsync(hbad + 3, scal.get() + 3, 4, cudaMemcpyDeviceToHost, s));
             CLD_CUDA(cudaStreamSynchronize(s));
@@ -325,13 +337,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(size.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(size.get(), 0, (size_t)n * 4, s));
         CLD_CUDA(cudaMemsetAsync(best.get(), 0, 8, s));
-        k_cc_count<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, size.get());
+        CLD_K(K_CC, s, k_cc_count<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, size.get()));
         CLD_LAUNCH_CHECK();
-        k_cc_best<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), size.get(), n, best.get());
+        CLD_K(K_CC, s, k_cc_best<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), size.get(), n, best.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(keep.alloc(n, s));
         CLD_TRY(newid.alloc(n, s));
-        k_cc_keep<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, best.get(), keep.get());
+        CLD_K(K_CC, s, k_cc_keep<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, best.get(), keep.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(scan_exclusive_u32(keep.get(), newid.get(), n, scal.get() + 4, s));
         CLD_CUDA(cudaMemcpyAsync(hbad + 4, scal.get() + 4, 4, cudaMemcpyDeviceToHost, s));
@@ -339,7 +351,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         n_out = hbad[4];
         CLD_TRY(orig.alloc(n_out, s));
         CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
-        k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), n, deg.get(), orig.get());
+        CLD_K(K_CSR, s, k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), n, deg.get(), orig.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n_out, scal.get() + 5, s));
         CLD_CUDA(cudaMemcpyAsync(hbad + 5, scal.get() + 5, 4, cudaMemcpyDeviceToHost, s));
@@ -351,12 +363,12 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(noff.alloc((size_t)n_out + 1, s));
         CLD_TRY(nadj.alloc(nnz_out ? nnz_out : 1, s));
         CLD_TRY(nrow.alloc(nnz_out ? nnz_out : 1, s));
-        k_widen_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
-                                                                          noff.get());
+        CLD_K(K_CSR, s, k_widen_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
+                                                                          noff.get()));
         CLD_LAUNCH_CHECK();
         if (nnz) {
-            k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), row.get(), adj.get(),
-                                                          nnz, noff.get(), nrow.get(), nadj.get());
+            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), row.get(), adj.get(),
+                                                          nnz, noff.get(), nrow.get(), nadj.get()));
             CLD_LAUNCH_CHECK();
         }
         g->off = noff.detach();
@@ -364,7 +376,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         g->row = nrow.detach();
     } else {
         CLD_TRY(orig.alloc(n, s));
-        k_iota<<<grid_for(n, 256), 256, 0, s>>>(orig.get(), n);
+        CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(orig.get(), n));
         CLD_LAUNCH_CHECK();
         g->off = off.detach();
         g->adj = adj.detach();
@@ -381,10 +393,10 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
     if (g->nnz) {
-        k_graph_stats<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, wsum.get(), scal.get() + 6);
+        CLD_K(K_CSR, s, k_graph_stats<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, wsum.get(), scal.get() + 6));
         CLD_LAUNCH_CHECK();
     }
-    k_degree_max<<<grid_for(g->n, 256), 256, 0, s>>>(g->off, g->n, scal.get() + 7);
+    CLD_K(K_CSR, s, k_degree_max<<<grid_for(g->n, 256), 256, 0, s>>>(g->off, g->n, scal.get() + 7));
     CLD_LAUNCH_CHECK();
     uint64_t* hsum = reinterpret_cast<uint64_t*>(static_cast<char*>(g->host.h) + 64);
     CLD_CUDA(cudaMemcpyAsync(hsum, wsum.get(), 8, cudaMemcpyDeviceToHost, s));

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -145,17 +146,17 @@ static cldiam_status scan_exclusive(const T* in, T* out, size_t n, T* total, cud
     }
     size_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        k_tile_scan<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, total);
+        CLD_K(K_SCAN, s, k_tile_scan<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, total));
         CLD_LAUNCH_CHECK();
         return CLDIAM_OK;
     }
     DBuf<T> part, part_scan;
     CLD_TRY(part.alloc(nb, s));
     CLD_TRY(part_scan.alloc(nb, s));
-    k_tile_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, part.get());
+    CLD_K(K_SCAN, s, k_tile_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, part.get()));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive<T>(part.get(), part_scan.get(), nb, nullptr, s));
-    k_tile_scan<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, part_scan.get(), total);
+    CLD_K(K_SCAN, s, k_tile_scan<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, part_scan.get(), total));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
@@ -193,21 +194,21 @@ __global__ void k_reduce_sum_u32(const uint32_t* __restrict__ in, size_t n, unsi
 cldiam_status reduce_max_u32(const uint32_t* in, size_t n, uint32_t* out, cudaStream_t s) {
     CLD_CUDA(cudaMemsetAsync(out, 0, sizeof(uint32_t), s));
     if (n == 0) return CLDIAM_OK;
-    k_reduce_max_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, out);
+    CLD_K(K_REDUCE, s, k_reduce_max_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, out));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
 cldiam_status reduce_min_u32(const uint32_t* in, size_t n, uint32_t* out, cudaStream_t s) {
     CLD_CUDA(cudaMemsetAsync(out, 0xFF, sizeof(uint32_t), s));
     if (n == 0) return CLDIAM_OK;
-    k_reduce_min_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, out);
+    CLD_K(K_REDUCE, s, k_reduce_min_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, out));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
 cldiam_status reduce_sum_u32_to_u64(const uint32_t* in, size_t n, uint64_t* out, cudaStream_t s) {
     CLD_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
     if (n == 0) return CLDIAM_OK;
-    k_reduce_sum_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, reinterpret_cast<unsigned long long*>(out));
+    CLD_K(K_REDUCE, s, k_reduce_sum_u32<<<grid_for(n, 256, 4), 256, 0, s>>>(in, n, reinterpret_cast<unsigned long long*>(out)));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
@@ -316,11 +317,14 @@ static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint
     uint32_t* vo = vals_alt;
     bool alt = false;
     for (int shift = 0; shift < bits; shift += 8) {
-        k_radix_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ki, n, shift, hist.get(), ntiles);
+        CLD_K(K_RADIX_HIST, s, k_radix_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ki, n, shift, hist.get(), ntiles));
         CLD_LAUNCH_CHECK();
         CLD_TRY(scan_exclusive_u32(hist.get(), hist.get(), (size_t)RS_RADIX * ntiles, nullptr, s));
-        k_radix_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist.get(), ntiles);
+        CLD_K(K_RADIX_SCATTER, s, k_radix_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist.get(), ntiles));
         CLD_LAUNCH_CHECK();
+        // algorithmic bytes: histogram reads every key; scatter reads and writes every (key, value)
+        prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
+        prof_add_bytes(K_RADIX_SCATTER, 2.0 * (double)n * (sizeof(K) + sizeof(uint32_t)));
         K* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
         alt = !alt;

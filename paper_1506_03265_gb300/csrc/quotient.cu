@@ -8,6 +8,7 @@
 // minimum.  Because the CSR is symmetric the result is symmetric, sorted by
 // (row, col).
 #include "internal.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -56,11 +57,18 @@ template <class K>
 __global__ void k_q_unique(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                            const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, uint32_t cnt,
                            uint32_t k, uint32_t* __restrict__ col, uint32_t* __restrict__ w, uint32_t* __restrict__ deg) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-        uint32_t r = excl[i] + flags[i] - 1u;
-        atomicMin(&w[r], vals[i]);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < cnt;
+        const K key = valid ? keys[i] : (K)0;
+        uint32_t v = valid ? vals[i] : 0xFFFFFFFFu;
+        // one atomicMin per run segment of this warp instead of one per item
+        v = warp_seg_min(key, valid, v);
+        const bool tail = warp_run_tail(key, valid);  // all lanes take part in the shuffles
+        if (!valid) continue;
+        const uint32_t r = excl[i] + flags[i] - 1u;
+        if (tail) atomicMin(&w[r], v);
         if (flags[i]) {
-            K key = keys[i];
             uint32_t a = (uint32_t)(key / k);
             col[r] = (uint32_t)(key - (K)a * k);
             atomicAdd(&deg[a], 1u);
@@ -87,8 +95,8 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     CLD_TRY(scal.alloc(4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 16, s));
     if (g->nnz) {
-        k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, c->cid, c->D, k, keys.get(),
-                                                          vals.get(), scal.get(), scal.get() + 1);
+        CLD_K(K_QUOTIENT, s, k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, c->cid, c->D, k, keys.get(),
+                                                          vals.get(), scal.get(), scal.get() + 1));
         CLD_LAUNCH_CHECK();
     }
     CLD_CUDA(cudaMemcpyAsync(hh, scal.get(), 8, cudaMemcpyDeviceToHost, s));
@@ -113,7 +121,7 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     CLD_TRY(flags.alloc(cnt ? cnt : 1, s));
     CLD_TRY(excl.alloc(cnt ? cnt : 1, s));
     if (cnt) {
-        k_q_heads<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, flags.get());
+        CLD_K(K_QUOTIENT, s, k_q_heads<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, flags.get()));
         CLD_LAUNCH_CHECK();
     }
     CLD_TRY(scan_exclusive_u32(flags.get(), excl.get(), cnt, scal.get() + 2, s));
@@ -131,12 +139,12 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     CLD_CUDA(cudaMemsetAsync(w.get(), 0xFF, (size_t)(nq ? nq : 1) * 4, s));
     CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)k + 1) * 4, s));
     if (cnt) {
-        k_q_unique<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flags.get(), excl.get(), cnt, k, col.get(), w.get(),
-                                                         deg.get());
+        CLD_K(K_QUOTIENT, s, k_q_unique<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flags.get(), excl.get(), cnt, k, col.get(), w.get(),
+                                                         deg.get()));
         CLD_LAUNCH_CHECK();
     }
     CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), k, nullptr, s));
-    k_q_offsets<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(degx.get(), k, nq, off.get());
+    CLD_K(K_QUOTIENT, s, k_q_offsets<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(degx.get(), k, nq, off.get()));
     CLD_LAUNCH_CHECK();
     CLD_CUDA(cudaStreamSynchronize(s));
     q->k = k;

@@ -11,6 +11,7 @@
 // once per bucket epoch (epoch stamps); stale far entries are dropped when
 // the next bucket is chosen.
 #include "internal.cuh"
+#include "prof.cuh"
 
 namespace cld {
 
@@ -153,7 +154,7 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
     SCounters* hc = reinterpret_cast<SCounters*>(static_cast<char*>(g->host.h) + 192);
     static_assert(sizeof(SCounters) <= 64, "counter block must fit the pinned area");
     const unsigned gb = grid_for(n, 256);
-    k_ds_init<<<gb, 256, 0, s>>>(dist.get(), rstamp.get(), sstamp.get(), fstamp.get(), n, source);
+    CLD_K(K_SSSP, s, k_ds_init<<<gb, 256, 0, s>>>(dist.get(), rstamp.get(), sstamp.get(), fstamp.get(), n, source));
     CLD_LAUNCH_CHECK();
     CLD_CUDA(cudaMemcpyAsync(cur.get(), &source, 4, cudaMemcpyHostToDevice, s));
     CLD_CUDA(cudaMemsetAsync(ctr.get(), 0, sizeof(SCounters), s));
@@ -179,9 +180,9 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
             CLD_CUDA(cudaMemsetAsync(&ctr.get()->nnext, 0, 4, s));
             CLD_CUDA(cudaMemcpyAsync(&ctr.get()->nfar, &nfar, 4, cudaMemcpyHostToDevice, s));
             unsigned rg = (unsigned)std::min<uint64_t>((ncur + 7) / 8, relax_grid);
-            k_ds_relax<<<rg, 256, 0, s>>>(pcur, ncur, false, g->off, g->adj, dist.get(), delta, hi, rstamp.get(),
+            CLD_K(K_SSSP, s, k_ds_relax<<<rg, 256, 0, s>>>(pcur, ncur, false, g->off, g->adj, dist.get(), delta, hi, rstamp.get(),
                                           round_id, sstamp.get(), fstamp.get(), epoch, pnext, settled.get(), pfar,
-                                          ctr.get());
+                                          ctr.get()));
             CLD_LAUNCH_CHECK();
             CLD_TRY(sync());
             ++rounds;
@@ -194,9 +195,9 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
         if (ns > 0) {
             CLD_CUDA(cudaMemcpyAsync(&ctr.get()->nfar, &nfar, 4, cudaMemcpyHostToDevice, s));
             unsigned rg = (unsigned)std::min<uint64_t>((ns + 7) / 8, relax_grid);
-            k_ds_relax<<<rg, 256, 0, s>>>(settled.get(), ns, true, g->off, g->adj, dist.get(), delta, hi, rstamp.get(),
+            CLD_K(K_SSSP, s, k_ds_relax<<<rg, 256, 0, s>>>(settled.get(), ns, true, g->off, g->adj, dist.get(), delta, hi, rstamp.get(),
                                           round_id, sstamp.get(), fstamp.get(), epoch, pnext, settled.get(), pfar,
-                                          ctr.get());
+                                          ctr.get()));
             CLD_LAUNCH_CHECK();
             CLD_TRY(sync());
             ++rounds;
@@ -205,7 +206,7 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
         if (nfar == 0) break;
         // next bucket
         CLD_CUDA(cudaMemsetAsync(&ctr.get()->minbucket, 0xFF, 4, s));
-        k_ds_minbucket<<<grid_for(nfar, 256), 256, 0, s>>>(pfar, nfar, dist.get(), hi, delta, ctr.get());
+        CLD_K(K_SSSP, s, k_ds_minbucket<<<grid_for(nfar, 256), 256, 0, s>>>(pfar, nfar, dist.get(), hi, delta, ctr.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(sync());
         if (hc->minbucket == 0xFFFFFFFFu) break;
@@ -215,8 +216,8 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
         ++epoch;
         CLD_CUDA(cudaMemsetAsync(&ctr.get()->nnext, 0, 4, s));
         CLD_CUDA(cudaMemsetAsync(&ctr.get()->nfar2, 0, 4, s));
-        k_ds_split<<<grid_for(nfar, 256), 256, 0, s>>>(pfar, nfar, dist.get(), old_hi, hi, fstamp.get(), epoch, pcur,
-                                                      pfar2, ctr.get());
+        CLD_K(K_SSSP, s, k_ds_split<<<grid_for(nfar, 256), 256, 0, s>>>(pfar, nfar, dist.get(), old_hi, hi, fstamp.get(), epoch, pcur,
+                                                      pfar2, ctr.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(sync());
         ncur = hc->nnext;
@@ -224,7 +225,7 @@ cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint3
         std::swap(pfar, pfar2);
     }
     CLD_CUDA(cudaMemsetAsync(ecc_d.get(), 0, 4, s));
-    k_ds_ecc<<<gb, 256, 0, s>>>(dist.get(), n, ecc_d.get());
+    CLD_K(K_SSSP, s, k_ds_ecc<<<gb, 256, 0, s>>>(dist.get(), n, ecc_d.get()));
     CLD_LAUNCH_CHECK();
     uint32_t* he = reinterpret_cast<uint32_t*>(static_cast<char*>(g->host.h) + 240);
     CLD_CUDA(cudaMemcpyAsync(he, ecc_d.get(), 4, cudaMemcpyDeviceToHost, s));
