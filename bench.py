@@ -44,12 +44,14 @@ SAMPLE_SCALE = 17  # CPU oracle sample: R-MAT scale 17 with the rmat20 recipe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="run one pipeline pass on the workload and exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -128,7 +130,7 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(gpu_index)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -334,6 +336,7 @@ def run_gpu(args):
         "e2e": e2e,
         "roofline": roofline,
         "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
+        "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
         "clocks": clocks,
         "gpu_launches": launches,
         "sssp_baseline": {"what": "Delta-stepping SSSP from the Philox source, 2*ecc = upper bound",
@@ -349,9 +352,25 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
 
 
+def profile_pass(args):
+    """One CL-DIAM pass (CSR build .. estimate) on the workload, nothing else: the ncu capture target."""
+    import torch
+
+    import paper_1506_03265_gb300 as cd
+    from inputs.workloads import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    e = wl.make()
+    ts = [torch.from_numpy(a.view(np.int32)).cuda() for a in (e.src, e.dst, e.w)]
+    g = cd.build_csr(ts[0], ts[1], ts[2], e.n, lcc=True)
+    r = cd.estimate(cd.quotient_build(cd.cluster(g, wl.tau, wl.seed)))
+    print(json.dumps({"workload": args.workload, "k": r["k"], "phi_approx": r["phi_approx"]}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_pass:
+        profile_pass(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -75,7 +75,7 @@ typedef struct {
     uint32_t delta0;       /* used with CLDIAM_DELTA0_EXPLICIT; must be >= 1                */
     int32_t contract_mode; /* 0: contracted clusters relax from distance 0 (Procedure Contract) */
     uint32_t step_cap;     /* must be 0 (no cap on growing steps per PartialGrowth)         */
-    uint32_t max_fw_k;     /* largest quotient solved by Floyd-Warshall; 0 = 8192           */
+    uint32_t max_fw_k;     /* largest dense quotient solved by Floyd-Warshall; 0 = 8192     */
     uint32_t reserved[3];  /* must be 0                                                     */
 } cldiam_opts;
 
@@ -163,18 +163,21 @@ void cldiam_quotient_free(cldiam_quotient* q);
 
 /*
  * Estimate (Section 4): out->phi_gc = Phi(G_C) by exact all-pairs shortest
- * paths on the quotient (Floyd-Warshall when k <= max_fw_k), out->radius =
- * max D, out->phi_approx = phi_gc + 2 radius; the clustering counters are
- * filled in too.  out is a host pointer.
- * Errors: OVERFLOW, UNSUPPORTED (k above max_fw_k), OOM, CUDA.
+ * paths on the quotient -- batched SSSP (multi-source Bellman-Ford, k <= 51,200)
+ * when it has fewer than k^2/8 entries, else blocked Floyd-Warshall (k <=
+ * max_fw_k) -- out->radius = max D, out->phi_approx = phi_gc + 2 radius; the
+ * clustering counters are filled in too.  out is a host pointer.
+ * Errors: OVERFLOW, UNSUPPORTED (no path applies to this k), OOM, CUDA.
  */
 cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out);
 
 /*
  * Largest finite shortest-path distance of a small weighted graph given as a
- * symmetric CSR (k nodes, off[k+1], col/w[nnz]; host or device), by blocked
- * Floyd-Warshall on the device; used for Phi(G_C).  Allocates a k x k scratch
- * matrix.  *phi is a host pointer.  Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
+ * symmetric CSR (k nodes, off[k+1], col/w[nnz]; host or device), exact, on the
+ * device: batched SSSP for sparse graphs, blocked Floyd-Warshall (k <= 8192,
+ * with a k x k scratch matrix) for dense ones; used for Phi(G_C).  The CSR is
+ * validated on the device first.  *phi is a host pointer.
+ * Errors: INVALID_ARG (malformed CSR), OVERFLOW, UNSUPPORTED, OOM, CUDA.
  */
 cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
                               void* stream, uint64_t* phi);

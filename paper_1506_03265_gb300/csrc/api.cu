@@ -192,10 +192,9 @@ cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out) {
     if (!q || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL quotient or out");
     return guarded([&]() -> cldiam_status {
         const cldiam_clustering* c = q->c;
-        if (q->k > q->max_fw_k) return fail(CLDIAM_ERR_UNSUPPORTED, "quotient larger than max_fw_k");
         cldiam_result r = c->stats;
         uint64_t phi = 0;
-        CLD_TRY(apsp_max_device(q->k, q->off, q->col, q->w, q->nnz, q->stream, &phi, false));
+        CLD_TRY(apsp_max_device(q->k, q->off, q->col, q->w, q->nnz, q->stream, &phi, false, q->max_fw_k));
         DBuf<uint32_t> rmax;
         CLD_TRY(rmax.alloc(1, q->stream));
         CLD_TRY(reduce_max_u32(c->D, c->g->n, rmax.get(), q->stream));
@@ -232,7 +231,8 @@ cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* c
             if (st == CLDIAM_OK) st = to_device(w, nnz * 4, s, &dw, &o3);
         }
         if (st == CLDIAM_OK)
-            st = apsp_max_device(k, (const uint64_t*)doff, (const uint32_t*)dcol, (const uint32_t*)dw, nnz, s, phi, true);
+            st = apsp_max_device(k, (const uint64_t*)doff, (const uint32_t*)dcol, (const uint32_t*)dw, nnz, s, phi, true,
+                                 8192u);
         if (o1) dfree(doff, s);
         if (o2) dfree(dcol, s);
         if (o3) dfree(dw, s);

@@ -3,12 +3,14 @@
 // distance matrix in (min, +) arithmetic on the integer ALUs (min-plus is not
 // a tensor-core contraction).
 //
-// Blocked FW with 32 x 32 tiles (Venkataraman, Sahni, Mukhopadhyaya): for
+// Blocked FW with 64 x 64 tiles (Venkataraman, Sahni, Mukhopadhyaya): for
 // each pivot tile r, (1) close the diagonal tile, (2) update the tiles of
 // row r and column r through it, (3) update every other tile from its row-r
 // and column-r tiles.  Entries are uint32 with 0xFFFFFFFF = no path; a sum
 // of two finite entries that reaches 2^32 - 1 raises the overflow flag
 // instead of wrapping.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "prof.cuh"
 
@@ -16,7 +18,6 @@ namespace cld {
 
 namespace {
 
-constexpr int T = 32;
 constexpr uint32_t INF = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t relax_min(uint32_t c, uint32_t a, uint32_t b, bool& ovf) {
@@ -60,73 +61,130 @@ __global__ void k_fw_scatter(const uint64_t* __restrict__ off, const uint32_t* _
         }
 }
 
+// Tiles are T x T = 64 x 64; a CTA of 256 threads gives each thread a 4 x 4
+// block (rows 4*ty.., cols 4*tx..).  Within the pivot tile and the pivot
+// row / column tiles, iteration p reads row p and column p, which iteration p
+// itself cannot change (D[p][p] = 0), so one barrier per p suffices.
+constexpr int FT = 64;
+constexpr int FQ = 4;       // 4 x 4 entries per thread
+constexpr int FTH = 256;    // 16 x 16 threads
+constexpr int FP = FT + 1;  // padded shared row
+
+__device__ __forceinline__ void fw_load_tile(uint32_t (*t)[FP], const uint32_t* M, uint32_t kp, uint32_t ti,
+                                             uint32_t tj) {
+    for (int i = threadIdx.x; i < FT * FT; i += FTH) {
+        int y = i / FT, x = i % FT;
+        t[y][x] = M[((size_t)ti * FT + y) * kp + (size_t)tj * FT + x];
+    }
+}
+__device__ __forceinline__ void fw_store_tile(uint32_t (*t)[FP], uint32_t* M, uint32_t kp, uint32_t ti, uint32_t tj) {
+    for (int i = threadIdx.x; i < FT * FT; i += FTH) {
+        int y = i / FT, x = i % FT;
+        M[((size_t)ti * FT + y) * kp + (size_t)tj * FT + x] = t[y][x];
+    }
+}
+
 // phase 1: the pivot tile against itself
-__global__ void __launch_bounds__(T* T) k_fw_phase1(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
-                                                    uint32_t* __restrict__ ovf_flag) {
-    __shared__ uint32_t t[T][T + 1];
-    const int y = threadIdx.x / T, x = threadIdx.x % T;
-    size_t base = (size_t)r * T * kp + (size_t)r * T;
-    t[y][x] = M[base + (size_t)y * kp + x];
+__global__ void __launch_bounds__(FTH) k_fw_phase1(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
+                                                   uint32_t* __restrict__ ovf_flag) {
+    __shared__ uint32_t t[FT][FP];
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    fw_load_tile(t, M, kp, r, r);
     __syncthreads();
     bool ovf = false;
-    for (int p = 0; p < T; ++p) {
-        uint32_t v = relax_min(t[y][x], t[y][p], t[p][x], ovf);
-        __syncthreads();
-        t[y][x] = v;
+    for (int p = 0; p < FT; ++p) {
+        uint32_t a[FQ], b[FQ];
+#pragma unroll
+        for (int q = 0; q < FQ; ++q) {
+            a[q] = t[ty * FQ + q][p];
+            b[q] = t[p][tx * FQ + q];
+        }
+#pragma unroll
+        for (int i = 0; i < FQ; ++i)
+#pragma unroll
+            for (int j = 0; j < FQ; ++j) {
+                uint32_t& c = t[ty * FQ + i][tx * FQ + j];
+                c = relax_min(c, a[i], b[j], ovf);
+            }
         __syncthreads();
     }
-    M[base + (size_t)y * kp + x] = t[y][x];
+    fw_store_tile(t, M, kp, r, r);
     if (ovf) atomicExch(ovf_flag, 1u);
 }
 
-// phase 2: tiles in pivot row r and pivot column r
-__global__ void __launch_bounds__(T* T) k_fw_phase2(uint32_t* __restrict__ M, uint32_t kp, uint32_t r, uint32_t nt,
-                                                    uint32_t* __restrict__ ovf_flag) {
-    __shared__ uint32_t piv[T][T + 1];
-    __shared__ uint32_t t[T][T + 1];
-    const int y = threadIdx.x / T, x = threadIdx.x % T;
-    uint32_t idx = blockIdx.x;  // 0..nt-2 row tiles, nt-1..2nt-3 column tiles
-    bool is_row = idx < nt - 1;
-    uint32_t o = is_row ? idx : idx - (nt - 1);
+// phase 2: tiles in pivot row r (blockIdx.y == 0) and pivot column r (blockIdx.y == 1)
+__global__ void __launch_bounds__(FTH) k_fw_phase2(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
+                                                   uint32_t* __restrict__ ovf_flag) {
+    __shared__ uint32_t piv[FT][FP];
+    __shared__ uint32_t t[FT][FP];
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    const bool is_row = blockIdx.y == 0;
+    uint32_t o = blockIdx.x;
     if (o >= r) ++o;
-    uint32_t ti = is_row ? r : o, tj = is_row ? o : r;
-    size_t pb = (size_t)r * T * kp + (size_t)r * T;
-    size_t tb = (size_t)ti * T * kp + (size_t)tj * T;
-    piv[y][x] = M[pb + (size_t)y * kp + x];
-    t[y][x] = M[tb + (size_t)y * kp + x];
+    const uint32_t ti = is_row ? r : o, tj = is_row ? o : r;
+    fw_load_tile(piv, M, kp, r, r);
+    fw_load_tile(t, M, kp, ti, tj);
     __syncthreads();
     bool ovf = false;
-    for (int p = 0; p < T; ++p) {
-        // row tile: t[y][x] = min(t, piv[y][p] + t[p][x]); column tile: min(t, t[y][p] + piv[p][x])
-        uint32_t a = is_row ? piv[y][p] : t[y][p];
-        uint32_t b = is_row ? t[p][x] : piv[p][x];
-        uint32_t v = relax_min(t[y][x], a, b, ovf);
-        __syncthreads();
-        t[y][x] = v;
+    for (int p = 0; p < FT; ++p) {
+        uint32_t a[FQ], b[FQ];
+#pragma unroll
+        for (int q = 0; q < FQ; ++q) {
+            // row tile: min(t, piv[y][p] + t[p][x]); column tile: min(t, t[y][p] + piv[p][x])
+            a[q] = is_row ? piv[ty * FQ + q][p] : t[ty * FQ + q][p];
+            b[q] = is_row ? t[p][tx * FQ + q] : piv[p][tx * FQ + q];
+        }
+#pragma unroll
+        for (int i = 0; i < FQ; ++i)
+#pragma unroll
+            for (int j = 0; j < FQ; ++j) {
+                uint32_t& c = t[ty * FQ + i][tx * FQ + j];
+                c = relax_min(c, a[i], b[j], ovf);
+            }
         __syncthreads();
     }
-    M[tb + (size_t)y * kp + x] = t[y][x];
+    fw_store_tile(t, M, kp, ti, tj);
     if (ovf) atomicExch(ovf_flag, 1u);
 }
 
-// phase 3: every other tile from its pivot-column and pivot-row tiles
-__global__ void __launch_bounds__(T* T) k_fw_phase3(uint32_t* __restrict__ M, uint32_t kp, uint32_t r, uint32_t nt,
-                                                    uint32_t* __restrict__ ovf_flag) {
-    __shared__ uint32_t A[T][T + 1];
-    __shared__ uint32_t B[T][T + 1];
-    const int y = threadIdx.x / T, x = threadIdx.x % T;
+// phase 3: every other tile from its pivot-column and pivot-row tiles; no barrier inside the p loop
+__global__ void __launch_bounds__(FTH) k_fw_phase3(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
+                                                   uint32_t* __restrict__ ovf_flag) {
+    __shared__ uint32_t A[FT][FP];
+    __shared__ __align__(16) uint32_t B[FT][FT];
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     uint32_t ti = blockIdx.y, tj = blockIdx.x;
     if (ti >= r) ++ti;
     if (tj >= r) ++tj;
-    A[y][x] = M[((size_t)ti * T + y) * kp + (size_t)r * T + x];
-    B[y][x] = M[((size_t)r * T + y) * kp + (size_t)tj * T + x];
-    size_t ci = ((size_t)ti * T + y) * kp + (size_t)tj * T + x;
-    uint32_t c = M[ci];
+    fw_load_tile(A, M, kp, ti, r);
+    for (int i = threadIdx.x; i < FT * FT; i += FTH) {
+        int y = i / FT, x = i % FT;
+        B[y][x] = M[((size_t)r * FT + y) * kp + (size_t)tj * FT + x];
+    }
+    uint32_t c[FQ][FQ];
+#pragma unroll
+    for (int i = 0; i < FQ; ++i) {
+        const uint4 v = *reinterpret_cast<const uint4*>(&M[((size_t)ti * FT + ty * FQ + i) * kp + (size_t)tj * FT + tx * FQ]);
+        c[i][0] = v.x; c[i][1] = v.y; c[i][2] = v.z; c[i][3] = v.w;
+    }
     __syncthreads();
     bool ovf = false;
-#pragma unroll 8
-    for (int p = 0; p < T; ++p) c = relax_min(c, A[y][p], B[p][x], ovf);
-    M[ci] = c;
+#pragma unroll 4
+    for (int p = 0; p < FT; ++p) {
+        uint32_t a[FQ];
+#pragma unroll
+        for (int q = 0; q < FQ; ++q) a[q] = A[ty * FQ + q][p];
+        const uint4 bv = *reinterpret_cast<const uint4*>(&B[p][tx * FQ]);
+        const uint32_t b[FQ] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int i = 0; i < FQ; ++i)
+#pragma unroll
+            for (int j = 0; j < FQ; ++j) c[i][j] = relax_min(c[i][j], a[i], b[j], ovf);
+    }
+#pragma unroll
+    for (int i = 0; i < FQ; ++i)
+        *reinterpret_cast<uint4*>(&M[((size_t)ti * FT + ty * FQ + i) * kp + (size_t)tj * FT + tx * FQ]) =
+            make_uint4(c[i][0], c[i][1], c[i][2], c[i][3]);
     if (ovf) atomicExch(ovf_flag, 1u);
 }
 
@@ -142,14 +200,112 @@ __global__ void k_fw_max_finite(const uint32_t* __restrict__ M, uint32_t kp, uin
     if (threadIdx.x == 0) atomicMax(out, m);
 }
 
+// Batched exact SSSP on the quotient CSR (multi-source Bellman-Ford): a CTA
+// owns S consecutive sources and keeps dist[v][s] for all k nodes in shared
+// memory; in each round one warp per node v pulls min(dist[u][s] + w(u,v))
+// over its neighbours u for all S sources at once (lane = (neighbour slot,
+// source)), and only v's warp writes row v.  Rounds repeat until no distance
+// changes.  Exact, so the eccentricities and their maximum equal
+// Floyd-Warshall's, with about rounds x entries x k work instead of k^3,
+// which wins on sparse quotients.
+template <int S, bool kCsrInSmem>
+__global__ void __launch_bounds__(1024) k_apsp_msbf(const uint64_t* __restrict__ goff, const uint32_t* __restrict__ gcol,
+                                                    const uint32_t* __restrict__ gw, uint32_t k, uint32_t nnz,
+                                                    uint32_t* __restrict__ out_max, uint32_t* __restrict__ ovf_flag) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t* dist = sm;  // k x S
+    // when it fits, the quotient CSR itself is staged in shared memory too (32-bit offsets)
+    uint32_t* soff = sm + (size_t)k * S;
+    uint32_t* scol = soff + (k + 1);
+    uint32_t* sw = scol + nnz;
+    __shared__ uint32_t s_changed;
+    const uint32_t s0 = blockIdx.x * S;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id(), nwarps = blockDim.x >> 5;
+    const uint32_t my_s = lane % S, slot = lane / S;
+    constexpr uint32_t kSlots = 32 / S;
+    for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x) {
+        const uint32_t v = i / S, s = i % S;
+        dist[i] = (s0 + s == v) ? 0u : INF;
+    }
+    if (kCsrInSmem) {
+        for (uint32_t i = threadIdx.x; i <= k; i += blockDim.x) soff[i] = (uint32_t)goff[i];
+        for (uint32_t i = threadIdx.x; i < nnz; i += blockDim.x) {
+            scol[i] = gcol[i];
+            sw[i] = gw[i];
+        }
+    }
+    bool ovf = false;
+    __syncthreads();
+    for (uint32_t round = 0; round < k; ++round) {
+        if (threadIdx.x == 0) s_changed = 0;
+        __syncthreads();
+        bool changed = false;
+        for (uint32_t v = warp; v < k; v += nwarps) {
+            const uint32_t beg = kCsrInSmem ? soff[v] : (uint32_t)goff[v];
+            const uint32_t end = kCsrInSmem ? soff[v + 1] : (uint32_t)goff[v + 1];
+            uint32_t best = INF;
+            for (uint32_t j = beg + slot; j < end; j += kSlots) {
+                const uint32_t u = kCsrInSmem ? scol[j] : gcol[j];
+                const uint32_t wj = kCsrInSmem ? sw[j] : gw[j];
+                const uint32_t du = dist[u * S + my_s];
+                if (du != INF) {
+                    const uint64_t nd = (uint64_t)du + wj;
+                    if (nd >= INF) ovf = true;
+                    else best = min(best, (uint32_t)nd);
+                }
+            }
+#pragma unroll
+            for (uint32_t o = S; o < 32; o <<= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (lane < S && best < dist[v * S + lane]) {
+                dist[v * S + lane] = best;
+                changed = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, changed) && lane == 0) s_changed = 1;
+        __syncthreads();
+        if (!s_changed) break;
+    }
+    uint32_t best = 0;
+    for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x)
+        if (s0 + i % S < k && dist[i] != INF && dist[i] > best) best = dist[i];
+    best = block_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u);
+    if (threadIdx.x == 0) atomicMax(out_max, best);
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicExch(ovf_flag, 1u);
+}
+
+template <int S>
+cldiam_status launch_msbf(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
+                          cudaStream_t s, uint32_t* out_max, uint32_t* ovf) {
+    constexpr int kMax = 220 * 1024;
+    static bool attr[64];
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k_apsp_msbf<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax));
+        CLD_CUDA(cudaFuncSetAttribute(k_apsp_msbf<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    const size_t dist_bytes = (size_t)k * S * 4;
+    const size_t csr_bytes = ((size_t)k + 1 + 2 * nnz) * 4;
+    const unsigned grid = (k + S - 1) / S;
+    if (dist_bytes + csr_bytes <= (size_t)kMax) {
+        CLD_K(K_FW, s, k_apsp_msbf<S, true><<<grid, 1024, dist_bytes + csr_bytes, s>>>(off, col, w, k, (uint32_t)nnz,
+                                                                                     out_max, ovf));
+    } else {
+        CLD_K(K_FW, s, k_apsp_msbf<S, false><<<grid, 1024, dist_bytes, s>>>(off, col, w, k, (uint32_t)nnz, out_max, ovf));
+    }
+    CLD_LAUNCH_CHECK();
+    return CLDIAM_OK;
+}
+
 }  // namespace
 
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
-                              cudaStream_t s, uint64_t* phi, bool validate) {
+                              cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k) {
     *phi = 0;
     if (k <= 1) return CLDIAM_OK;
-    const uint32_t nt = (k + T - 1) / T;
-    const uint32_t kp = nt * T;
+    const uint32_t nt = (k + FT - 1) / FT;
+    const uint32_t kp = nt * FT;
     DBuf<uint32_t> M, scal;
     CLD_TRY(scal.alloc(3, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 12, s));
@@ -161,20 +317,33 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
         CLD_CUDA(cudaStreamSynchronize(s));
         if (bad) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
     }
-    CLD_TRY(M.alloc((size_t)kp * kp, s));
-    CLD_K(K_FW, s, k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M.get(), kp, k));
-    CLD_K(K_FW, s, k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M.get()));
-    CLD_LAUNCH_CHECK();
-    for (uint32_t r = 0; r < nt; ++r) {
-        CLD_K(K_FW, s, k_fw_phase1<<<1, T * T, 0, s>>>(M.get(), kp, r, scal.get()));
-        if (nt > 1) {
-            CLD_K(K_FW, s, k_fw_phase2<<<2 * (nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get()));
-            CLD_K(K_FW, s, k_fw_phase3<<<dim3(nt - 1, nt - 1), T * T, 0, s>>>(M.get(), kp, r, nt, scal.get()));
+    // sparse quotient (fewer than k^2 / 8 entries): batched SSSP, S sources per CTA with
+    // k x S distances in shared memory (S = 8 while it fits in 200 KB)
+    constexpr size_t kSmem = 220 * 1024;
+    const bool sparse = (double)nnz * 8.0 < (double)k * k;
+    if (sparse && (size_t)k * 8 * 4 <= kSmem) {
+        CLD_TRY(launch_msbf<8>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
+    } else if (sparse && (size_t)k * 4 * 4 <= kSmem) {
+        CLD_TRY(launch_msbf<4>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
+    } else if (sparse && (size_t)k * 4 <= kSmem) {
+        CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
+    } else {
+        if (k > max_fw_k) return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient larger than max_fw_k");
+        CLD_TRY(M.alloc((size_t)kp * kp, s));
+        CLD_K(K_FW, s, k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M.get(), kp, k));
+        CLD_K(K_FW, s, k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M.get()));
+        CLD_LAUNCH_CHECK();
+        for (uint32_t r = 0; r < nt; ++r) {
+            CLD_K(K_FW, s, k_fw_phase1<<<1, FTH, 0, s>>>(M.get(), kp, r, scal.get()));
+            if (nt > 1) {
+                CLD_K(K_FW, s, k_fw_phase2<<<dim3(nt - 1, 2), FTH, 0, s>>>(M.get(), kp, r, scal.get()));
+                CLD_K(K_FW, s, k_fw_phase3<<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M.get(), kp, r, scal.get()));
+            }
+            CLD_LAUNCH_CHECK();
         }
+        CLD_K(K_FW, s, k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M.get(), kp, k, scal.get() + 1));
         CLD_LAUNCH_CHECK();
     }
-    CLD_K(K_FW, s, k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M.get(), kp, k, scal.get() + 1));
-    CLD_LAUNCH_CHECK();
     uint32_t h[2];
     CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 8, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));

@@ -44,23 +44,30 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* p, unsigned lon
     if (lane_id() == 0 && v) atomicAdd(p, v);
 }
 
-// Append to the frontier: one packed atomicAdd per warp hands out both the
-// entry slot (high word) and the entry's first position in the flattened
+// Append to the frontier: one packed atomicAdd per CTA hands out both the
+// entry slots (high word) and the entries' first positions in the flattened
 // edge list (low word), so positions increase with slots and the frontier's
-// degree prefix needs no separate scan.  All lanes must call it.
+// degree prefix needs no separate scan.  All threads of the block must call
+// it (it synchronises the block); `scratch` holds 33 words.
 __device__ __forceinline__ void front_append(unsigned long long* ctr, bool pred, uint32_t deg, uint32_t& slot,
-                                             uint32_t& pre) {
-    unsigned mask = __ballot_sync(0xffffffffu, pred);
-    if (mask == 0) return;
-    uint32_t d = pred ? deg : 0u;
-    uint32_t incl = warp_incl_scan(d);
-    uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane_id() == leader) base = atomicAdd(ctr, ((unsigned long long)__popc(mask) << 32) | total);
-    base = __shfl_sync(0xffffffffu, base, leader);
+                                             uint32_t& pre, unsigned long long* scratch) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
+    const uint32_t d = pred ? deg : 0u;
+    const uint32_t incl = warp_incl_scan(d);
+    if (l == 31) scratch[w] = ((unsigned long long)__popc(mask) << 32) | incl;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long v = l < nw ? scratch[l] : 0ull;
+        const unsigned long long iv = warp_incl_scan(v);  // packed (count, entries): no carry, block sums < 2^32
+        if (l < nw) scratch[l] = iv - v;
+        if (l == 31) scratch[32] = iv ? atomicAdd(ctr, iv) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long base = scratch[32] + scratch[w];
     slot = (uint32_t)(base >> 32) + (uint32_t)__popc(mask & lanemask_lt());
     pre = (uint32_t)base + (incl - d);
+    __syncthreads();
 }
 
 // a3: draw the new centers of this stage among unfrozen nodes, reset the others.
@@ -87,6 +94,7 @@ __global__ void k_select(uint32_t n, const uint32_t* __restrict__ center, unsign
 __global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
                           const uint64_t* __restrict__ off, uint32_t delta, bool pull, uint32_t* __restrict__ fv,
                           unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
+    __shared__ unsigned long long scratch[33];
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         uint32_t v = base + threadIdx.x;
         bool push = false, pl = false;
@@ -107,13 +115,13 @@ __global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key
             }
         }
         uint32_t slot = 0, pre = 0;
-        front_append(&ctr->front, push, deg, slot, pre);
+        front_append(&ctr->front, push, deg, slot, pre, scratch);
         if (push) {
             fv[slot] = v;
             fkey[slot] = k;
             fpre[slot] = pre;
         }
-        front_append(&ctr->front, pl, deg, slot, pre);
+        front_append(&ctr->front, pl, deg, slot, pre, scratch);
         if (pl) {
             fv[slot] = v;
             fkey[slot] = kPull;
@@ -140,7 +148,8 @@ __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, c
     __shared__ uint32_t s_beg[RC];
     __shared__ uint32_t s_v[RC];
     __shared__ unsigned long long s_key[RC];
-    __shared__ uint32_t s_i0, s_cnt;
+    __shared__ uint32_t s_next[RC];  // nodes first changed by this chunk (at most one per entry)
+    __shared__ uint32_t s_i0, s_cnt, s_nn, s_nbase;
     const uint32_t tid = threadIdx.x;
     unsigned long long newly = 0;
     for (uint32_t chunk = blockIdx.x; (uint64_t)chunk * RC < E; chunk += gridDim.x) {
@@ -160,6 +169,7 @@ __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, c
             }
             s_i0 = i0;
             s_cnt = lo - i0 + 1;
+            s_nn = 0;
         }
         __syncthreads();
         const uint32_t i0 = s_i0, cnt = s_cnt;  // cnt <= RC: every entry has >= 1 adjacency entry
@@ -207,9 +217,12 @@ __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, c
                     }
                 }
             }
-            uint32_t slot = warp_append(&ctr->nnext, changed_first);
-            if (changed_first) next[slot] = target;
+            if (changed_first) s_next[atomicAdd(&s_nn, 1u)] = target;
         }
+        __syncthreads();
+        if (tid == 0) s_nbase = s_nn ? atomicAdd(&ctr->nnext, s_nn) : 0u;  // one global atomic per chunk
+        __syncthreads();
+        for (uint32_t j = tid; j < s_nn; j += RT) next[s_nbase + j] = s_next[j];
         __syncthreads();  // the next chunk reuses the shared arrays
     }
     warp_add_u64(&ctr->newly_covered, newly);
@@ -221,6 +234,7 @@ __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, c
 __global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned long long* __restrict__ key,
                            const uint64_t* __restrict__ off, uint32_t delta, uint32_t* __restrict__ fv,
                            unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
+    __shared__ unsigned long long scratch[33];
     const uint32_t nn = ctr->nnext;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nn; base += gridDim.x * blockDim.x) {
         uint32_t i = base + threadIdx.x;
@@ -234,7 +248,7 @@ __global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned lon
             take = (uint32_t)(k >> 32) < delta && deg > 0;
         }
         uint32_t slot = 0, pre = 0;
-        front_append(&ctr->front, take, deg, slot, pre);
+        front_append(&ctr->front, take, deg, slot, pre, scratch);
         if (take) {
             fv[slot] = v;
             fkey[slot] = k;
@@ -274,16 +288,26 @@ __global__ void k_finalize_freeze(uint32_t n, unsigned long long* __restrict__ k
                                   uint32_t* __restrict__ R, const uint32_t* __restrict__ D, const uint64_t* __restrict__ off,
                                   Counters* ctr) {
     unsigned long long cnt = 0, degs = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (center[v] != kNone) continue;
-        unsigned long long k = key[v];
-        if (k == kInfKey) continue;
-        uint32_t c = (uint32_t)k;
-        center[v] = c;
-        key[v] = 0;
-        atomicMax(&R[c], D[v]);
-        ++cnt;
-        degs += off[v + 1] - off[v];
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        bool take = false;
+        uint32_t c = kNone, dv = 0;
+        if (v < n && center[v] == kNone) {
+            const unsigned long long k = key[v];
+            if (k != kInfKey) {
+                take = true;
+                c = (uint32_t)k;
+                dv = D[v];
+                center[v] = c;
+                key[v] = 0;
+                ++cnt;
+                degs += off[v + 1] - off[v];
+            }
+        }
+        // nodes of one cluster often share a warp: one atomicMax per distinct center
+        const unsigned peers = __match_any_sync(0xffffffffu, take ? c : kNone);
+        const uint32_t m = __reduce_max_sync(peers, dv);
+        if (take && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicMax(&R[c], m);
     }
     warp_add_u64(&ctr->frozen, cnt);
     warp_add_u64(&ctr->frozen_deg, degs);
@@ -477,7 +501,10 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
             } while (updated != 0 && 2 * covered < U);
             if (2 * covered >= U) break;
             bool growable = false;
-            if (delta < kDeltaMax && g->nnz) {
+            if (delta < kDeltaMax && g->connected) {
+                // connected graph: some covered or frozen node touches an uncovered one iff any exists
+                growable = covered > 0 || U < n;
+            } else if (delta < kDeltaMax && g->nnz) {
                 CLD_TRY(zero_field(offsetof(Counters, growable), 4));
                 CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz,
                                                                                          key.get(), ctr.get()));

@@ -185,6 +185,26 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool pred) {
     return base + __popc(mask & lanemask_lt());
 }
 
+// Block-aggregated append: one global atomicAdd per CTA.  Returns this
+// thread's slot when `pred`.  Every thread of the block must call it (it
+// synchronises the block); `scratch` is caller shared memory of 33 words.
+__device__ __forceinline__ uint32_t block_append(uint32_t* counter, bool pred, uint32_t* scratch) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
+    if (l == 0) scratch[w] = (uint32_t)__popc(mask);
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = l < nw ? scratch[l] : 0u;
+        const uint32_t incl = warp_incl_scan(v);
+        if (l < nw) scratch[l] = incl - v;
+        if (l == 31) scratch[32] = incl ? atomicAdd(counter, incl) : 0u;
+    }
+    __syncthreads();
+    const uint32_t slot = scratch[32] + scratch[w] + (uint32_t)__popc(mask & lanemask_lt());
+    __syncthreads();
+    return slot;
+}
+
 // Segmented minimum over a warp's lanes holding consecutive items of a
 // sorted sequence: lanes with equal keys form one run, so comparing the key
 // `o` lanes back suffices.  Returns, in each lane, the minimum of its run's
@@ -244,6 +264,21 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
+
+// Unique keys of a sorted sequence with the minimum value of each run:
+// row_out[r] = key / div (row_out may be null), col_out[r*cs] = key % div,
+// w_out[r*cs] = run minimum (w_out must hold 0xFFFFFFFF beforehand);
+// keys >= sentinel are skipped; *total_dev = number of unique keys.
+cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, size_t cnt, uint64_t sentinel,
+                                    uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint32_t* total_dev, cudaStream_t s);
+cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
+                                    uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint32_t* total_dev, cudaStream_t s);
+
+// CSR offsets off[0..n] of entries whose (sorted) row ids are row[0..nnz):
+// off[u] = index of the first entry with row >= u.  No atomics, no scan.
+cldiam_status offsets_from_rows(const uint32_t* row, uint64_t nnz, uint32_t n, uint64_t* off, cudaStream_t s);
 
 inline int bits_for(uint64_t max_value) {  // bits needed to represent values <= max_value
     int b = 0;

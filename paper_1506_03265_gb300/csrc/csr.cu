@@ -8,6 +8,9 @@
 // hooking with pointer jumping: every tree points to a smaller id of its
 // component, so roots are component minima and the labelling is
 // deterministic.
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 #include "prof.cuh"
 
@@ -34,67 +37,60 @@ __global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t
     }
 }
 
-__global__ void k_head_flags(const uint64_t* __restrict__ keys, uint64_t cnt, uint64_t sentinel,
-                             uint32_t* __restrict__ flags) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        flags[i] = (k < sentinel && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
-    }
-}
-
-__global__ void k_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                         const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, uint64_t cnt,
-                         uint64_t sentinel, uint32_t n, uint32_t* __restrict__ row, uint32_t* __restrict__ col,
-                         uint32_t* __restrict__ wmin, uint32_t* __restrict__ deg) {
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < cnt; base += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = base + threadIdx.x;
-        const uint64_t k = i < cnt ? keys[i] : sentinel;
-        const bool valid = k < sentinel;
-        // parallel edges form runs of equal keys: reduce each warp's part of a run first
-        const uint32_t v = warp_seg_min(k, valid, valid ? vals[i] : 0xFFFFFFFFu);
-        const bool tail = warp_run_tail(k, valid);  // all lanes take part in the shuffles
-        if (!valid) continue;
-        const uint32_t r = excl[i] + flags[i] - 1u;
-        if (tail) atomicMin(&wmin[r], v);
-        if (flags[i]) {
-            uint32_t u = (uint32_t)(k / n), c = (uint32_t)(k - (uint64_t)u * n);
-            row[r] = u;
-            col[r] = c;
-            atomicAdd(&deg[u], 1u);
-        }
-    }
-}
-
 __global__ void k_widen_offsets(const uint32_t* __restrict__ excl, uint32_t n, uint32_t total, uint64_t* __restrict__ off) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
         off[i] = (i == n) ? (uint64_t)total : (uint64_t)excl[i];
-}
-
-__global__ void k_pack_adj(const uint32_t* __restrict__ col, const uint32_t* __restrict__ w, uint64_t nnz,
-                           uint2* __restrict__ adj) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x)
-        adj[i] = make_uint2(col[i], w[i]);
 }
 
 __global__ void k_iota(uint32_t* __restrict__ a, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
 
-// one hooking sweep over undirected edges (u < v entries)
-__global__ void k_cc_hook(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
-                          uint32_t* __restrict__ parent, uint32_t* __restrict__ changed) {
-    bool any = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = row[i], v = adj[i].x;
-        if (u >= v) continue;
-        uint32_t ru = parent[u], rv = parent[v];
-        if (ru != rv) {
-            uint32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
-            atomicMin(&parent[hi], lo);
-            any = true;
-        }
+// Union of the trees of u and v: the larger root is hooked under the smaller
+// one with a compare-and-swap, so every tree root stays the minimum id of its
+// tree.  Each retry strictly lowers the larger of the two candidate roots,
+// so the loop ends.
+__device__ __forceinline__ void cc_link(uint32_t u, uint32_t v, uint32_t* parent) {
+    uint32_t p1 = parent[u], p2 = parent[v];
+    while (p1 != p2) {
+        const uint32_t high = p1 > p2 ? p1 : p2, low = p1 > p2 ? p2 : p1;
+        const uint32_t ph = parent[high];
+        if (ph == low) break;
+        if (ph == high && atomicCAS(&parent[high], high, low) == high) break;
+        p1 = parent[parent[high]];
+        p2 = parent[low];
     }
-    if (__any_sync(0xffffffffu, any) && lane_id() == 0) atomicExch(changed, 1u);
+}
+
+// first pass: link every node with its r-th neighbour
+__global__ void k_cc_link_nth(const uint64_t* __restrict__ off, const uint2* __restrict__ adj, uint32_t n, uint32_t r,
+                              uint32_t* __restrict__ parent) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t b = off[v];
+        if (b + r < off[v + 1]) cc_link(v, adj[b + r].x, parent);
+    }
+}
+
+// final pass: nodes outside the dominant tree link all their remaining
+// neighbours (an edge with both ends in the dominant tree adds nothing; an
+// edge with one end outside is linked from that end)
+__global__ void k_cc_link_rest(const uint64_t* __restrict__ off, const uint2* __restrict__ adj, uint32_t n,
+                               uint32_t skip, uint32_t giant, uint32_t* __restrict__ parent) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        uint32_t r = parent[v];
+        while (parent[r] != r) r = parent[r];
+        if (r == giant) continue;
+        for (uint64_t j = off[v] + skip; j < off[v + 1]; ++j) cc_link(v, adj[j].x, parent);
+    }
+}
+
+__global__ void k_cc_sample(const uint32_t* __restrict__ parent, uint32_t n, uint32_t count, uint32_t* __restrict__ out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)(((uint64_t)i * 2654435761ull) % n);
+        uint32_t r = parent[v];
+        while (parent[r] != r) r = parent[r];
+        out[i] = r;
+    }
 }
 
 // pointer jumping to the root (parents only ever decrease within a component)
@@ -252,7 +248,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     const int bits = bits_for(sentinel);
     const uint64_t cnt = 2 * m;
     DBuf<uint64_t> keys, keys2;
-    DBuf<uint32_t> vals, vals2, flagsb, excl, scal;
+    DBuf<uint32_t> vals, vals2, scal;
     CLD_TRY(keys.alloc(cnt ? cnt : 1, s));
     CLD_TRY(keys2.alloc(cnt ? cnt : 1, s));
     CLD_TRY(vals.alloc(cnt ? cnt : 1, s));
@@ -274,44 +270,24 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     uint64_t* sk = alt ? keys2.get() : keys.get();
     uint32_t* sv = alt ? vals2.get() : vals.get();
 
-    CLD_TRY(flagsb.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(excl.alloc(cnt ? cnt : 1, s));
-    if (cnt) {
-        CLD_K(K_CSR, s, k_head_flags<<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, sentinel, flagsb.get()));
-        CLD_LAUNCH_CHECK();
-    }
-    CLD_TRY(scan_exclusive_u32(flagsb.get(), excl.get(), cnt, scal.get() + 1, s));
+    // unique (row, col) runs with their lightest weight, in one look-back pass
+    DBuf<uint32_t> row, deg, degx;
+    DBuf<uint64_t> off;
+    DBuf<uint2> adj;
+    CLD_TRY(row.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(adj.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(deg.alloc((size_t)n + 1, s));
+    CLD_TRY(degx.alloc((size_t)n + 1, s));
+    CLD_TRY(off.alloc((size_t)n + 1, s));
+    CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));
+    CLD_TRY(unique_min_sorted_u64(sk, sv, cnt, sentinel, n, row.get(), &adj.get()->x, &adj.get()->y, 2,
+                                  scal.get() + 1, s));
     CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnz = hbad[1];
-
-    DBuf<uint32_t> row, col, wmin, deg, degx;
-    CLD_TRY(row.alloc(nnz ? nnz : 1, s));
-    CLD_TRY(col.alloc(nnz ? nnz : 1, s));
-    CLD_TRY(wmin.alloc(nnz ? nnz : 1, s));
-    CLD_TRY(deg.alloc((size_t)n + 1, s));
-    CLD_TRY(degx.alloc((size_t)n + 1, s));
-    CLD_CUDA(cudaMemsetAsync(wmin.get(), 0xFF, (size_t)(nnz ? nnz : 1) * 4, s));
-    CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
-    if (cnt) {
-        CLD_K(K_CSR, s, k_unique<<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flagsb.get(), excl.get(), cnt, sentinel, n, row.get(),
-                                                    col.get(), wmin.get(), deg.get()));
-        CLD_LAUNCH_CHECK();
-    }
-    keys.release(); keys2.release(); vals.release(); vals2.release(); flagsb.release(); excl.release();
-
-    DBuf<uint64_t> off;
-    DBuf<uint2> adj;
-    CLD_TRY(off.alloc((size_t)n + 1, s));
-    CLD_TRY(adj.alloc(nnz ? nnz : 1, s));
-    CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n, scal.get() + 2, s));
-    CLD_K(K_CSR, s, k_widen_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, nnz, off.get()));
-    CLD_LAUNCH_CHECK();
-    if (nnz) {
-        CLD_K(K_CSR, s, k_pack_adj<<<grid_for(nnz, 256), 256, 0, s>>>(col.get(), wmin.get(), nnz, adj.get()));
-        CLD_LAUNCH_CHECK();
-    }
-    col.release(); wmin.release();
+    keys.release(); keys2.release(); vals.release(); vals2.release();
+    // entries are sorted by row: offsets come from the row boundaries
+    CLD_TRY(offsets_from_rows(row.get(), nnz, n, off.get(), s));
 
     uint32_t n_out = n;
     uint64_t nnz_out = nnz;
@@ -323,16 +299,35 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(best.alloc(1, s));
         CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
         CLD_LAUNCH_CHECK();
-        for (int it = 0; nnz > 0; ++it) {
-            CLD_CUDA(cudaMemsetAsync(scal.get() + 3, 0, 4, s));
-            CLD_K(K_CC, s, k_cc_hook<<<grid_for(nnz, 256), 256, 0, s>>>(row.get(), adj.get(), nnz, parent.get(), scal.get() + 3));
+        // Afforest-style: link two neighbours per node, find the dominant tree by sampling,
+        // then link the remaining edges of the nodes outside it
+        constexpr uint32_t kNeighbourRounds = 2;
+        if (nnz > 0) {
+            for (uint32_t r = 0; r < kNeighbourRounds; ++r) {
+                CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, r, parent.get()));
+                CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
+            }
             CLD_LAUNCH_CHECK();
+            constexpr uint32_t kSamples = 1024;
+            DBuf<uint32_t> samp;
+            CLD_TRY(samp.alloc(kSamples, s));
+            CLD_K(K_CC, s, k_cc_sample<<<4, 256, 0, s>>>(parent.get(), n, kSamples, samp.get()));
+            CLD_LAUNCH_CHECK();
+            std::vector<uint32_t> hs(kSamples);
+            CLD_CUDA(cudaMemcpyAsync(hs.data(), samp.get(), kSamples * 4, cudaMemcpyDeviceToHost, s));
+            CLD_CUDA(cudaStreamSynchronize(s));
+            std::sort(hs.begin(), hs.end());
+            uint32_t giant = hs[0], best_run = 0;
+            for (size_t i = 0; i < hs.size();) {
+                size_t j = i;
+                while (j < hs.size() && hs[j] == hs[i]) ++j;
+                if (j - i > best_run) { best_run = (uint32_t)(j - i); giant = hs[i]; }
+                i = j;
+            }
+            CLD_K(K_CC, s, k_cc_link_rest<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, kNeighbourRounds,
+                                                                            giant, parent.get()));
             CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
             CLD_LAUNCH_CHECK();
-            CLD_CUDA(cudaMemcpyAsync(hbad + 3, scal.get() + 3, 4, cudaMemcpyDeviceToHost, s));
-            CLD_CUDA(cudaStreamSynchronize(s));
-            if (!hbad[3]) break;
-            if (it > 10000) return fail(CLDIAM_ERR_CUDA, "connected components did not converge");
         }
         CLD_TRY(size.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(size.get(), 0, (size_t)n * 4, s));
@@ -385,6 +380,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     g->orig = orig.detach();
     g->n = n_out;
     g->nnz = nnz_out;
+    g->connected = (flags & CLDIAM_CSR_LCC) != 0;
 
     // weight statistics for the initial Delta (Algorithm 1 / Section 5)
     DBuf<unsigned long long> wsum;

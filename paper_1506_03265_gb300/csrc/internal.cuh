@@ -16,6 +16,7 @@ struct cldiam_graph {
     uint64_t wsum_upper = 0;     // sum of weights over u < v entries
     uint32_t wmin = 0;
     uint32_t max_deg = 0;
+    bool connected = false;      // built with the LCC flag: one connected component
     cld::Pinned host;            // small pinned block for counter read-back
 };
 
@@ -61,7 +62,7 @@ void free_quotient(cldiam_quotient* q);
 
 // Largest finite APSP distance of a k-node CSR already on the device.
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
-                              uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate);
+                              uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k);
 
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
                          uint64_t* rounds);

@@ -168,6 +168,25 @@ cldiam_status scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, ui
     return scan_exclusive<uint64_t>(in, out, n, total, s);
 }
 
+// ------------------------------------------------------------------ offsets from sorted rows
+__global__ void k_offsets_from_rows(const uint32_t* __restrict__ row, uint64_t nnz, uint32_t n,
+                                    uint64_t* __restrict__ off) {
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nnz; r += (uint64_t)gridDim.x * blockDim.x) {
+        // entry r opens rows row[r-1]+1 .. row[r] (all rows up to row[0] when r = 0); position nnz
+        // closes rows row[nnz-1]+1 .. n
+        if (r > 0 && r < nnz && row[r] == row[r - 1]) continue;
+        const uint64_t lo = (r == 0) ? 0 : (uint64_t)row[r - 1] + 1;
+        const uint64_t hi = (r == nnz) ? n : (uint64_t)row[r];
+        for (uint64_t x = lo; x <= hi; ++x) off[x] = r;
+    }
+}
+
+cldiam_status offsets_from_rows(const uint32_t* row, uint64_t nnz, uint32_t n, uint64_t* off, cudaStream_t s) {
+    CLD_K(K_CSR, s, k_offsets_from_rows<<<grid_for(nnz + 1, 256), 256, 0, s>>>(row, nnz, n, off));
+    CLD_LAUNCH_CHECK();
+    return CLDIAM_OK;
+}
+
 // ------------------------------------------------------------------ reductions
 __global__ void k_reduce_max_u32(const uint32_t* __restrict__ in, size_t n, uint32_t* out) {
     uint32_t m = 0;
@@ -214,91 +233,208 @@ cldiam_status reduce_sum_u32_to_u64(const uint32_t* in, size_t n, uint64_t* out,
 }
 
 // ------------------------------------------------------------------ radix sort
-constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 8;                       // items per thread
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2048 items per tile
-constexpr int RS_RADIX = 256;
-
-// item (warp w, iteration i, lane l) of a tile sits at w*256 + i*32 + l, so
-// every warp load is 32 consecutive keys.
+// Onesweep-style LSD radix sort (8-bit digits).  One read of the keys builds
+// the digit histograms of every pass; each pass is then a single kernel in
+// which tile t ranks its items (warp match-based, stable), publishes its
+// per-digit counts, and obtains the counts of all earlier tiles by decoupled
+// look-back over a per-(tile, digit) status word, so no per-pass histogram
+// read or separate scan is needed.  Items are staged in shared memory in
+// digit order and written out as contiguous runs.
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS)
-    k_radix_hist(const K* __restrict__ keys, size_t n, int shift, uint32_t* __restrict__ hist, uint32_t ntiles) {
-    __shared__ uint32_t h[RS_RADIX];
-    for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) h[i] = 0;
+struct OsCfg {  // items per thread: fewer for 64-bit keys to keep registers (and occupancy) in check
+    static constexpr int ITEMS = sizeof(K) == 8 ? 8 : 12;
+    static constexpr int TILE = OS_THREADS * ITEMS;
+};
+constexpr int OS_RADIX = 256;
+constexpr unsigned long long OS_AGG = 1ull << 32;   // status: tile's own count
+constexpr unsigned long long OS_PRE = 2ull << 32;   // status: inclusive prefix over tiles 0..t
+constexpr long long OS_WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: a look-back that waits longer gives up
+
+template <class K>
+__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass,
+                                                 uint32_t* __restrict__ hist) {
+    // one private histogram per warp and pass: shared atomics collide only within a warp
+    __shared__ uint32_t h[8][4][OS_RADIX];  // warps x passes (<= 4 per launch) x digits
+    for (int i = threadIdx.x; i < 8 * 4 * OS_RADIX; i += blockDim.x) (&h[0][0][0])[i] = 0;
     __syncthreads();
-    const uint32_t tile = blockIdx.x;
-    const unsigned w = threadIdx.x >> 5, l = lane_id();
-    size_t base = (size_t)tile * RS_TILE + (size_t)w * (RS_ITEMS * 32);
+    const unsigned w = threadIdx.x >> 5;
+    constexpr int U = 8;  // keys loaded per thread before counting, to keep loads in flight
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int p0 = 0; p0 < npass; p0 += 4) {
+        const int np = min(4, npass - p0);
+        for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += stride * U) {
+            K kk[U];
 #pragma unroll
-    for (int i = 0; i < RS_ITEMS; ++i) {
-        size_t idx = base + (size_t)i * 32 + l;
-        bool valid = idx < n;
-        uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & 0xFF) : 0x100u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && l == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+            for (int u = 0; u < U; ++u) {
+                const size_t i = base + (size_t)u * stride;
+                kk[u] = i < n ? keys[i] : (K)0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (base + (size_t)u * stride >= n) break;
+                for (int p = 0; p < np; ++p)
+                    atomicAdd(&h[w][p][(uint32_t)((kk[u] >> (8 * (p0 + p))) & 0xFF)], 1u);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < np * OS_RADIX; i += blockDim.x) {
+            const int p = i / OS_RADIX, d = i % OS_RADIX;
+            uint32_t c = 0;
+            for (int ww = 0; ww < 8; ++ww) {
+                c += h[ww][p][d];
+                h[ww][p][d] = 0;
+            }
+            if (c) atomicAdd(&hist[(p0 + p) * OS_RADIX + d], c);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) hist[(size_t)d * ntiles + tile] = h[d];
 }
 
-template <class K>
-__global__ void __launch_bounds__(RS_THREADS)
-    k_radix_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
-                    uint32_t* __restrict__ vals_out, size_t n, int shift, const uint32_t* __restrict__ offs,
-                    uint32_t ntiles) {
-    __shared__ uint32_t whist[RS_WARPS][RS_RADIX];
-    __shared__ uint32_t gbase[RS_RADIX];
-    for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&whist[0][0])[i] = 0;
-    const uint32_t tile = blockIdx.x;
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) gbase[d] = offs[(size_t)d * ntiles + tile];
+// exclusive scan of each pass's 256 digit counts (one block, 256 threads)
+__global__ void k_os_hist_scan(uint32_t* __restrict__ hist, int npass) {
+    __shared__ uint32_t wsum[OS_WARPS];
+    const unsigned d = threadIdx.x, w = d >> 5, l = lane_id();
+    for (int p = 0; p < npass; ++p) {
+        uint32_t c = hist[p * OS_RADIX + d];
+        uint32_t incl = warp_incl_scan(c);
+        if (l == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t off = 0;
+        for (unsigned ww = 0; ww < w; ++ww) off += wsum[ww];
+        hist[p * OS_RADIX + d] = off + incl - c;
+        __syncthreads();
+    }
+}
+
+template <class K, int OS_ITEMS = OsCfg<K>::ITEMS, int OS_TILE = OsCfg<K>::TILE>
+__global__ void __launch_bounds__(OS_THREADS, 4)
+    k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+              uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ goff,
+              unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    K* s_key = reinterpret_cast<K*>(os_smem);
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(os_smem + sizeof(K) * OS_TILE);
+    __shared__ uint32_t whist[OS_WARPS][OS_RADIX];
+    __shared__ uint32_t tstart[OS_RADIX];
+    __shared__ uint32_t gbase[OS_RADIX];
+    __shared__ uint32_t wsum[OS_WARPS];
+    __shared__ uint32_t s_tile;
+    const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles in start order: earlier tiles are running or done
+    for (int i = tid; i < OS_WARPS * OS_RADIX; i += OS_THREADS) (&whist[0][0])[i] = 0;
     __syncthreads();
-    const unsigned w = threadIdx.x >> 5, l = lane_id();
+    const uint32_t tile = s_tile;
+    const size_t tbase = (size_t)tile * OS_TILE;
     const unsigned ltmask = lanemask_lt();
-    size_t base = (size_t)tile * RS_TILE + (size_t)w * (RS_ITEMS * 32);
-    K key[RS_ITEMS];
-    uint32_t val[RS_ITEMS];
-    uint32_t dig[RS_ITEMS];
-    uint32_t rank[RS_ITEMS];
+
+    K key[OS_ITEMS];
+    uint32_t val[OS_ITEMS];
+    uint32_t rank_pk[(OS_ITEMS + 1) / 2];  // warp-local ranks (< 32 * OS_ITEMS) as 16-bit halves; 0xFFFF = no item
+    // issue every load of the tile before ranking, so they are in flight together
 #pragma unroll
-    for (int i = 0; i < RS_ITEMS; ++i) {
-        size_t idx = base + (size_t)i * 32 + l;
-        bool valid = idx < n;
-        key[i] = valid ? keys_in[idx] : (K)0;
-        val[i] = valid ? vals_in[idx] : 0u;
-        uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFF) : 0x100u;
-        dig[i] = d;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned leader = __ffs(peers) - 1;
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const size_t idx = tbase + (size_t)w * (OS_ITEMS * 32) + (size_t)i * 32 + l;
+        const bool valid = idx < n;
+        key[i] = valid ? kin[idx] : (K)0;
+        val[i] = valid ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const size_t idx = tbase + (size_t)w * (OS_ITEMS * 32) + (size_t)i * 32 + l;
+        const bool valid = idx < n;
+        const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFF) : 0x100u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (valid && l == leader) {
             b = whist[w][d];
             whist[w][d] = b + (uint32_t)__popc(peers);
         }
         b = __shfl_sync(0xffffffffu, b, leader);
-        rank[i] = b + (uint32_t)__popc(peers & ltmask);
+        const uint32_t rk = valid ? b + (uint32_t)__popc(peers & ltmask) : 0xFFFFu;
+        if (i % 2 == 0) rank_pk[i / 2] = rk;
+        else rank_pk[i / 2] |= rk << 16;
         __syncwarp();
     }
     __syncthreads();
-    // exclusive scan over warps, per digit
-    for (int d = threadIdx.x; d < RS_RADIX; d += RS_THREADS) {
-        uint32_t s = 0;
+
+    // per digit (thread d): warp offsets within the tile, tile count, publication, look-back
+    const unsigned d = tid;
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int ww = 0; ww < RS_WARPS; ++ww) {
-            uint32_t t = whist[ww][d];
-            whist[ww][d] = s;
-            s += t;
+    for (int ww = 0; ww < OS_WARPS; ++ww) {
+        uint32_t t = whist[ww][d];
+        whist[ww][d] = cnt;
+        cnt += t;
+    }
+    volatile unsigned long long* vst = status;
+    if (tile == 0) vst[d] = OS_PRE | cnt;
+    else vst[(size_t)tile * OS_RADIX + d] = OS_AGG | cnt;
+    // tile-local exclusive scan over digits
+    {
+        uint32_t incl = warp_incl_scan(cnt);
+        if (l == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t off = 0;
+        for (unsigned ww = 0; ww < w; ++ww) off += wsum[ww];
+        tstart[d] = off + incl - cnt;
+    }
+    uint32_t excl = 0;
+    if (tile > 0) {
+        // windowed look-back: read the statuses of LB earlier tiles at once, add their counts
+        // back to the first inclusive prefix; wait (bounded) only on a tile not yet published
+        constexpr int LB = 8;
+        const long long t0 = clock64();
+        long long t = (long long)tile - 1;
+        bool done = false, timed_out = false;
+        while (!done && !timed_out) {
+            unsigned long long sw[LB];
+#pragma unroll
+            for (int j = 0; j < LB; ++j)
+                sw[j] = (t - j >= 0) ? (unsigned long long)vst[(size_t)(t - j) * OS_RADIX + d] : (unsigned long long)OS_PRE;
+#pragma unroll
+            for (int j = 0; j < LB; ++j) {
+                if (done || timed_out) break;
+                while ((sw[j] & ~0xFFFFFFFFull) == 0) {
+                    if (clock64() - t0 > OS_WAIT_CYCLES) {
+                        atomicExch(err, 1u);
+                        timed_out = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                    sw[j] = vst[(size_t)(t - j) * OS_RADIX + d];
+                }
+                excl += (uint32_t)sw[j];
+                if ((sw[j] & ~0xFFFFFFFFull) == OS_PRE) done = true;
+            }
+            t -= LB;
+        }
+        vst[(size_t)tile * OS_RADIX + d] = OS_PRE | (excl + cnt);
+    }
+    gbase[d] = goff[d] + excl;
+    __syncthreads();
+
+    // stage in digit order
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const uint32_t rk = (rank_pk[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
+        if (rk != 0xFFFFu) {
+            const uint32_t dd = (uint32_t)((key[i] >> shift) & 0xFF);
+            const uint32_t pos = tstart[dd] + whist[w][dd] + rk;
+            s_key[pos] = key[i];
+            s_val[pos] = val[i];
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int i = 0; i < RS_ITEMS; ++i) {
-        if (dig[i] < 0x100u) {
-            uint32_t pos = gbase[dig[i]] + whist[w][dig[i]] + rank[i];
-            keys_out[pos] = key[i];
-            vals_out[pos] = val[i];
-        }
+    const uint32_t tcount = (uint32_t)min((size_t)OS_TILE, n - tbase);
+    for (uint32_t i = tid; i < tcount; i += OS_THREADS) {
+        const K k = s_key[i];
+        const uint32_t dd = (uint32_t)((k >> shift) & 0xFF);
+        const size_t pos = (size_t)gbase[dd] + (i - tstart[dd]);
+        kout[pos] = k;
+        vout[pos] = s_val[i];
     }
 }
 
@@ -308,29 +444,203 @@ static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint
     *in_alt = false;
     if (n <= 1 || bits <= 0) return CLDIAM_OK;
     if (n > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "radix sort limited to 2^32 - 1 items");
-    uint32_t ntiles = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-    DBuf<uint32_t> hist;
-    CLD_TRY(hist.alloc((size_t)RS_RADIX * ntiles, s));
+    const int npass = (bits + 7) / 8;
+    constexpr int OS_TILE = OsCfg<K>::TILE;
+    const uint32_t ntiles = (uint32_t)((n + OS_TILE - 1) / OS_TILE);
+    const size_t smem = (sizeof(K) + sizeof(uint32_t)) * OS_TILE;
+    static bool attr_set[64];
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    DBuf<uint32_t> hist, ctl;
+    DBuf<unsigned long long> status;
+    CLD_TRY(hist.alloc((size_t)npass * OS_RADIX, s));
+    CLD_TRY(ctl.alloc(2 * npass + 2, s));
+    CLD_TRY(status.alloc((size_t)ntiles * OS_RADIX, s));
+    CLD_CUDA(cudaMemsetAsync(hist.get(), 0, (size_t)npass * OS_RADIX * 4, s));
+    CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, (2 * npass + 2) * 4, s));
+    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, 0, s>>>(keys, n, npass, hist.get()));
+    CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist.get(), npass));
+    CLD_LAUNCH_CHECK();
+    prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
     K* ki = keys;
     uint32_t* vi = vals;
     K* ko = keys_alt;
     uint32_t* vo = vals_alt;
     bool alt = false;
-    for (int shift = 0; shift < bits; shift += 8) {
-        CLD_K(K_RADIX_HIST, s, k_radix_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ki, n, shift, hist.get(), ntiles));
+    for (int p = 0; p < npass; ++p) {
+        CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * OS_RADIX * 8, s));
+        CLD_K(K_RADIX_SCATTER, s,
+              k_os_pass<K><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, 8 * p, hist.get() + p * OS_RADIX,
+                                                            status.get(), ctl.get() + p, ctl.get() + 2 * npass));
         CLD_LAUNCH_CHECK();
-        CLD_TRY(scan_exclusive_u32(hist.get(), hist.get(), (size_t)RS_RADIX * ntiles, nullptr, s));
-        CLD_K(K_RADIX_SCATTER, s, k_radix_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist.get(), ntiles));
-        CLD_LAUNCH_CHECK();
-        // algorithmic bytes: histogram reads every key; scatter reads and writes every (key, value)
-        prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
+        // algorithmic bytes: every (key, value) read once and written once
         prof_add_bytes(K_RADIX_SCATTER, 2.0 * (double)n * (sizeof(K) + sizeof(uint32_t)));
         K* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
         alt = !alt;
     }
+    uint32_t herr = 0;
+    CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 2 * npass, 4, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired");
     *in_alt = alt;
     return CLDIAM_OK;
+}
+
+// ------------------------------------------------------------------ unique runs of a sorted sequence
+// One pass over sorted (key, value) pairs: run heads get consecutive indices
+// r (a tile counts its heads with ballots, and gets the heads of all earlier
+// tiles by decoupled look-back on one status word per tile); for each run the
+// minimum value is folded in with one atomicMin per run piece per warp.
+// Output per unique key: row_out[r] = key / div (if row_out), col_out[r*cs] =
+// key % div, w_out[r*cs] = min value (w_out pre-filled with 0xFFFFFFFF).
+// Keys >= sentinel are ignored (they sort last).
+constexpr int UQ_THREADS = 256;
+constexpr int UQ_ITEMS = 8;
+constexpr int UQ_TILE = UQ_THREADS * UQ_ITEMS;
+
+template <class K>
+__global__ void __launch_bounds__(UQ_THREADS)
+    k_unique_lb(const K* __restrict__ keys, const uint32_t* __restrict__ vals, size_t cnt, K sentinel, uint64_t div,
+                uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out, uint32_t* __restrict__ w_out, int cs,
+                unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ total,
+                uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_tile, s_woff[UQ_THREADS / 32], s_prefix;
+    const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const size_t base = (size_t)tile * UQ_TILE + (size_t)w * (UQ_ITEMS * 32);
+    K key[UQ_ITEMS];
+    uint32_t val[UQ_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
+        key[i] = idx < cnt ? keys[idx] : sentinel;
+        val[i] = idx < cnt ? vals[idx] : 0xFFFFFFFFu;
+    }
+    uint32_t head_bits = 0, run = 0;
+    uint32_t ex[UQ_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
+        K prev = __shfl_up_sync(0xffffffffu, key[i], 1);
+        if (l == 0) prev = (idx > 0 && idx < cnt) ? keys[idx - 1] : sentinel;
+        const bool f = key[i] < sentinel && (idx == 0 || prev != key[i]);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        ex[i] = run + (uint32_t)__popc(bal & lanemask_lt());
+        run += (uint32_t)__popc(bal);
+        head_bits |= (f ? 1u : 0u) << i;
+    }
+    if (l == 0) s_woff[w] = run;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t acc = 0, my_off = 0;
+        for (int ww = 0; ww < UQ_THREADS / 32; ++ww) {
+            const uint32_t t = s_woff[ww];
+            if ((int)l == ww) my_off = acc;
+            acc += t;
+        }
+        __syncwarp();
+        if (l < UQ_THREADS / 32) s_woff[l] = my_off;
+        volatile unsigned long long* vst = status;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            if (l == 0) vst[0] = OS_PRE | acc;
+        } else {
+            if (l == 0) vst[tile] = OS_AGG | acc;
+            // warp-wide look-back: lane j reads tile t - j, so 32 predecessors cost one round trip
+            const long long t0 = clock64();
+            long long t = (long long)tile - 1;
+            bool done = false;
+            while (!done) {
+                const long long idx = t - (long long)l;
+                unsigned long long sw = idx >= 0 ? (unsigned long long)vst[idx] : (unsigned long long)OS_PRE;
+                while ((sw & ~0xFFFFFFFFull) == 0) {
+                    if (clock64() - t0 > OS_WAIT_CYCLES) {
+                        atomicExch(err, 1u);
+                        sw = (unsigned long long)OS_PRE;
+                        break;
+                    }
+                    __nanosleep(32);
+                    sw = vst[idx];
+                }
+                const unsigned pre = __ballot_sync(0xffffffffu, (sw & ~0xFFFFFFFFull) == OS_PRE);
+                uint32_t v = (uint32_t)sw;
+                if (pre) {
+                    const unsigned first = __ffs(pre) - 1;
+                    if (l > first) v = 0;
+                    done = true;
+                }
+                excl += warp_sum(v);
+                t -= 32;
+            }
+            if (l == 0) vst[tile] = OS_PRE | (excl + acc);
+        }
+        if (l == 0) {
+            s_prefix = excl;
+            if ((size_t)(tile + 1) * UQ_TILE >= cnt) *total = excl + acc;  // the last tile knows the count
+        }
+    }
+    __syncthreads();
+    const uint32_t tbase = s_prefix + s_woff[w];
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const bool valid = key[i] < sentinel;
+        const uint32_t v = warp_seg_min(key[i], valid, val[i]);
+        const bool tail = warp_run_tail(key[i], valid);
+        if (!valid) continue;
+        const uint32_t f = (head_bits >> i) & 1u;
+        const uint32_t r = tbase + ex[i] + f - 1u;
+        if (tail) atomicMin(&w_out[(size_t)r * cs], v);
+        if (f) {
+            const uint64_t q = (uint64_t)key[i] / div;
+            if (row_out) row_out[r] = (uint32_t)q;
+            col_out[(size_t)r * cs] = (uint32_t)((uint64_t)key[i] - q * div);
+        }
+    }
+}
+
+template <class K>
+static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size_t cnt, K sentinel, uint64_t div,
+                                       uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                       uint32_t* total_dev, cudaStream_t s) {
+    if (cnt == 0) {
+        CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
+        return CLDIAM_OK;
+    }
+    if (cnt > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "more than 2^32 - 1 items");
+    const uint32_t ntiles = (uint32_t)((cnt + UQ_TILE - 1) / UQ_TILE);
+    DBuf<unsigned long long> status;
+    DBuf<uint32_t> ctl;
+    CLD_TRY(status.alloc(ntiles, s));
+    CLD_TRY(ctl.alloc(2, s));
+    CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * 8, s));
+    CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, 8, s));
+    CLD_K(K_CSR, s, k_unique_lb<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out,
+                                                                  cs, status.get(), ctl.get(), total_dev,
+                                                                  ctl.get() + 1));
+    CLD_LAUNCH_CHECK();
+    uint32_t herr = 0;
+    CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(CLDIAM_ERR_TIMEOUT, "unique look-back wait expired");
+    return CLDIAM_OK;
+}
+
+cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, size_t cnt, uint64_t sentinel,
+                                    uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint32_t* total_dev, cudaStream_t s) {
+    return unique_min_sorted<uint64_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, total_dev, s);
+}
+cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
+                                    uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint32_t* total_dev, cudaStream_t s) {
+    return unique_min_sorted<uint32_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, total_dev, s);
 }
 
 cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,

@@ -19,6 +19,7 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
                          const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D, uint32_t k,
                          K* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ count,
                          uint32_t* __restrict__ overflow) {
+    __shared__ uint32_t scratch[33];
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < nnz; base += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t i = base + threadIdx.x;
         bool take = false;
@@ -39,46 +40,12 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
                 wq = (uint32_t)s;
             }
         }
-        uint32_t slot = warp_append(count, take);
+        uint32_t slot = block_append(count, take, scratch);  // one global atomic per CTA
         if (take) {
             keys[slot] = key;
             vals[slot] = wq;
         }
     }
-}
-
-template <class K>
-__global__ void k_q_heads(const K* __restrict__ keys, uint32_t cnt, uint32_t* __restrict__ flags) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
-        flags[i] = (i == 0 || keys[i - 1] != keys[i]) ? 1u : 0u;
-}
-
-template <class K>
-__global__ void k_q_unique(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
-                           const uint32_t* __restrict__ flags, const uint32_t* __restrict__ excl, uint32_t cnt,
-                           uint32_t k, uint32_t* __restrict__ col, uint32_t* __restrict__ w, uint32_t* __restrict__ deg) {
-    for (uint32_t base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < cnt;
-        const K key = valid ? keys[i] : (K)0;
-        uint32_t v = valid ? vals[i] : 0xFFFFFFFFu;
-        // one atomicMin per run segment of this warp instead of one per item
-        v = warp_seg_min(key, valid, v);
-        const bool tail = warp_run_tail(key, valid);  // all lanes take part in the shuffles
-        if (!valid) continue;
-        const uint32_t r = excl[i] + flags[i] - 1u;
-        if (tail) atomicMin(&w[r], v);
-        if (flags[i]) {
-            uint32_t a = (uint32_t)(key / k);
-            col[r] = (uint32_t)(key - (K)a * k);
-            atomicAdd(&deg[a], 1u);
-        }
-    }
-}
-
-__global__ void k_q_offsets(const uint32_t* __restrict__ excl, uint32_t k, uint32_t total, uint64_t* __restrict__ off) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= k; i += gridDim.x * blockDim.x)
-        off[i] = (i == k) ? (uint64_t)total : (uint64_t)excl[i];
 }
 
 template <class K>
@@ -117,35 +84,24 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     K* sk = alt ? keys2.get() : keys.get();
     uint32_t* sv = alt ? vals2.get() : vals.get();
 
-    DBuf<uint32_t> flags, excl, deg, degx;
-    CLD_TRY(flags.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(excl.alloc(cnt ? cnt : 1, s));
-    if (cnt) {
-        CLD_K(K_QUOTIENT, s, k_q_heads<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, cnt, flags.get()));
-        CLD_LAUNCH_CHECK();
-    }
-    CLD_TRY(scan_exclusive_u32(flags.get(), excl.get(), cnt, scal.get() + 2, s));
+    // unique cluster pairs with their lightest weight, in one look-back pass
+    DBuf<uint32_t> qrow, col, w;
+    DBuf<uint64_t> off;
+    CLD_TRY(qrow.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(col.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(w.alloc(cnt ? cnt : 1, s));
+    CLD_TRY(off.alloc((size_t)k + 1, s));
+    CLD_CUDA(cudaMemsetAsync(w.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 4, s));
+    if (sizeof(K) == 8)
+        CLD_TRY(unique_min_sorted_u64((const uint64_t*)sk, sv, cnt, ~0ull, k, qrow.get(), col.get(), w.get(), 1,
+                                      scal.get() + 2, s));
+    else
+        CLD_TRY(unique_min_sorted_u32((const uint32_t*)sk, sv, cnt, 0xFFFFFFFFu, k, qrow.get(), col.get(), w.get(), 1,
+                                      scal.get() + 2, s));
     CLD_CUDA(cudaMemcpyAsync(hh + 2, scal.get() + 2, 4, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nq = hh[2];
-
-    DBuf<uint32_t> col, w;
-    DBuf<uint64_t> off;
-    CLD_TRY(col.alloc(nq ? nq : 1, s));
-    CLD_TRY(w.alloc(nq ? nq : 1, s));
-    CLD_TRY(deg.alloc((size_t)k + 1, s));
-    CLD_TRY(degx.alloc((size_t)k + 1, s));
-    CLD_TRY(off.alloc((size_t)k + 1, s));
-    CLD_CUDA(cudaMemsetAsync(w.get(), 0xFF, (size_t)(nq ? nq : 1) * 4, s));
-    CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)k + 1) * 4, s));
-    if (cnt) {
-        CLD_K(K_QUOTIENT, s, k_q_unique<K><<<grid_for(cnt, 256), 256, 0, s>>>(sk, sv, flags.get(), excl.get(), cnt, k, col.get(), w.get(),
-                                                         deg.get()));
-        CLD_LAUNCH_CHECK();
-    }
-    CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), k, nullptr, s));
-    CLD_K(K_QUOTIENT, s, k_q_offsets<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(degx.get(), k, nq, off.get()));
-    CLD_LAUNCH_CHECK();
+    CLD_TRY(offsets_from_rows(qrow.get(), nq, k, off.get(), s));
     CLD_CUDA(cudaStreamSynchronize(s));
     q->k = k;
     q->nnz = nq;
@@ -173,7 +129,7 @@ cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out) {
     q->c = c;
     q->stream = c->g->stream;
     q->max_fw_k = c->max_fw_k;
-    cldiam_status st = ((uint64_t)c->k * c->k <= 0x100000000ull) ? build_quotient<uint32_t>(c, q)
+    cldiam_status st = ((uint64_t)c->k * c->k <= 0xFFFFFFFFull) ? build_quotient<uint32_t>(c, q)
                                                                   : build_quotient<uint64_t>(c, q);
     if (st != CLDIAM_OK) {
         free_quotient(q);

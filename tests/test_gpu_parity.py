@@ -181,6 +181,29 @@ def test_apsp_max(cd, seed):
         assert cd.apsp_max(og.n, og.off, og.col, og.wt) == oracle.apsp_max(q)
 
 
+@pytest.mark.parametrize("k", [65, 130, 200])
+def test_apsp_dense_floyd_warshall(cd, k):
+    # a dense quotient (>= k^2/8 entries) takes the blocked Floyd-Warshall path, across several 64-wide tiles
+    rng = np.random.default_rng(k)
+    iu = np.triu_indices(k, 1)
+    keep = rng.random(iu[0].size) < 0.6
+    s, d = iu[0][keep].astype(np.uint32), iu[1][keep].astype(np.uint32)
+    w = rng.integers(1, 1 << 20, s.size).astype(np.uint32)
+    og = oracle.build_csr(k, s, d, w, lcc=False)
+    assert og.nnz * 8 >= k * k
+    q = oracle.Quotient(og.n, np.arange(og.n, dtype=np.uint32), og.off, og.col, og.wt.astype(np.uint64))
+    assert cd.apsp_max(og.n, og.off, og.col, og.wt) == oracle.apsp_max(q)
+
+
+def test_apsp_rejects_malformed_csr(cd):
+    off = np.array([0, 2, 1, 3], np.uint64)  # decreasing offsets
+    with pytest.raises(cd.CldiamError):
+        cd.apsp_max(3, off, np.array([1, 2, 0], np.uint32), np.array([1, 1, 1], np.uint32))
+    off = np.array([0, 1, 2, 3], np.uint64)
+    with pytest.raises(cd.CldiamError):   # column id out of range
+        cd.apsp_max(3, off, np.array([1, 7, 0], np.uint32), np.array([1, 1, 1], np.uint32))
+
+
 def test_overflow_is_reported(cd):
     # a path whose length exceeds 2^32 - 1: the SSSP must refuse, not wrap
     n = 4
