@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(1024) k_apsp_msbf(const uint64_t* __restrict__
     uint32_t* soff = sm + (size_t)k * S;
     uint32_t* scol = soff + (k + 1);
     uint32_t* sw = scol + nnz;
-    __shared__ uint32_t s_changed;
+    // "some distance changed" flag of round r lives in slot r % 3: it is written during round r and
+    // read after its closing barrier, and slot (r + 1) % 3 is cleared during round r, when no thread
+    // can still be reading it (round r - 2) or writing it yet (round r + 1)
+    __shared__ uint32_t s_changed[3];
     const uint32_t s0 = blockIdx.x * S;
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id(), nwarps = blockDim.x >> 5;
     const uint32_t my_s = lane % S, slot = lane / S;
@@ -235,10 +238,11 @@ __global__ void __launch_bounds__(1024) k_apsp_msbf(const uint64_t* __restrict__
         }
     }
     bool ovf = false;
+    if (threadIdx.x == 0) s_changed[0] = s_changed[1] = s_changed[2] = 0;
     __syncthreads();
     for (uint32_t round = 0; round < k; ++round) {
-        if (threadIdx.x == 0) s_changed = 0;
-        __syncthreads();
+        const uint32_t slot_r = round % 3;
+        if (threadIdx.x == 0) s_changed[(round + 1) % 3] = 0;
         bool changed = false;
         for (uint32_t v = warp; v < k; v += nwarps) {
             const uint32_t beg = kCsrInSmem ? soff[v] : (uint32_t)goff[v];
@@ -261,9 +265,9 @@ __global__ void __launch_bounds__(1024) k_apsp_msbf(const uint64_t* __restrict__
                 changed = true;
             }
         }
-        if (__any_sync(0xffffffffu, changed) && lane == 0) s_changed = 1;
+        if (__any_sync(0xffffffffu, changed) && lane == 0) s_changed[slot_r] = 1;
         __syncthreads();
-        if (!s_changed) break;
+        if (!s_changed[slot_r]) break;
     }
     uint32_t best = 0;
     for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x)

@@ -195,6 +195,22 @@ def test_apsp_dense_floyd_warshall(cd, k):
     assert cd.apsp_max(og.n, og.off, og.col, og.wt) == oracle.apsp_max(q)
 
 
+@pytest.mark.parametrize("k,density,seed", [(3000, 0.002, 6), (2500, 0.003, 7), (700, 0.01, 5)])
+def test_apsp_sparse_batched_sssp(cd, k, density, seed):
+    # sparse graphs (possibly disconnected) take the multi-source Bellman-Ford path; many rounds
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(k, 1)
+    keep = rng.random(iu[0].size) < density
+    s, d = iu[0][keep].astype(np.uint32), iu[1][keep].astype(np.uint32)
+    w = rng.integers(1, 1 << 20, s.size).astype(np.uint32)
+    og = oracle.build_csr(k, s, d, w, lcc=False)
+    assert og.nnz * 8 < k * k
+    q = oracle.Quotient(og.n, np.arange(og.n, dtype=np.uint32), og.off, og.col, og.wt.astype(np.uint64))
+    ref = oracle.apsp_max(q)
+    for _ in range(3):
+        assert cd.apsp_max(og.n, og.off, og.col, og.wt) == ref
+
+
 def test_apsp_rejects_malformed_csr(cd):
     off = np.array([0, 2, 1, 3], np.uint64)  # decreasing offsets
     with pytest.raises(cd.CldiamError):
