@@ -182,6 +182,29 @@ cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out);
 cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
                               void* stream, uint64_t* phi);
 
+/*
+ * cldiam_apsp_max without any device allocation.  The paper has no
+ * counterpart; this exists for callers that are not allowed to allocate GPU
+ * memory themselves or through us -- for example a host application that
+ * owns the whole device memory budget through its own allocator, or code
+ * that must not risk an allocation failure or the latency of a first
+ * allocation in the middle of its work.
+ *  - Same result as cldiam_apsp_max.  off, col and w must already be in device
+ *    memory (nothing is copied); *phi is a host pointer.
+ *  - Scratch is one fixed array inside the library (about 4 MB per GPU that
+ *    loads it, resident until the process exits).  Limits: k <= 1024 when the
+ *    graph has at least k^2/8 entries (Floyd-Warshall in that array), k <=
+ *    51,200 otherwise (batched SSSP in shared memory); larger k returns
+ *    CLDIAM_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or allocating library call.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call reuses the same array, so two calls whose work overlaps on the
+ *    GPU (different streams or threads) race on it: serialise them.
+ * Errors: INVALID_ARG (NULL, host pointers, malformed CSR), UNSUPPORTED, OVERFLOW, CUDA.
+ */
+cldiam_status cldiam_apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                                      void* stream, uint64_t* phi);
+
 /* Source node of the SSSP baseline: Philox4x32-10(seed; (2^32-1, 2^32-1, 0, 0)) word 0 mod n. */
 cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t* source);
 /*

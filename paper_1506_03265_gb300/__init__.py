@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
             "cldiam_quotient_free": (None, [P]),
             "cldiam_estimate": (st, [P, P]),
             "cldiam_apsp_max": (st, [ctypes.c_uint32, P, P, P, P, P]),
+            "cldiam_apsp_max_noalloc": (st, [ctypes.c_uint32, P, P, P, P, P]),
             "cldiam_sssp_source": (st, [P, ctypes.c_uint64, P]),
             "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
             "cldiam_run": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
@@ -285,6 +286,14 @@ def apsp_max(k: int, off, col, w, stream=None) -> int:
     off = off if hasattr(off, "data_ptr") else np.ascontiguousarray(off, dtype=np.uint64)
     _check(load().cldiam_apsp_max(k, _ptr(off), _ptr(_u32(col)), _ptr(_u32(w)), _stream_ptr(stream),
                                   ctypes.byref(phi)), "cldiam_apsp_max")
+    return phi.value
+
+
+def apsp_max_noalloc(k: int, off, col, w, stream=None) -> int:
+    """cldiam_apsp_max_noalloc: same as apsp_max, device tensors only, no device allocation."""
+    phi = ctypes.c_uint64()
+    _check(load().cldiam_apsp_max_noalloc(k, _ptr(off), _ptr(col), _ptr(w), _stream_ptr(stream), ctypes.byref(phi)),
+           "cldiam_apsp_max_noalloc")
     return phi.value
 
 

@@ -241,6 +241,12 @@ cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* c
     });
 }
 
+cldiam_status cldiam_apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                                      void* stream, uint64_t* phi) {
+    if (!phi || (k > 0 && (!off || !col || !w))) return fail(CLDIAM_ERR_INVALID_ARG, "NULL argument");
+    return guarded([&] { return apsp_max_noalloc(k, off, col, w, resolve_stream(stream), phi); });
+}
+
 cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t* source) {
     if (!g || !source) return fail(CLDIAM_ERR_INVALID_ARG, "NULL graph or source");
     U4 r = philox4x32_10(seed, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);

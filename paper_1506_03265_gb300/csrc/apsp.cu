@@ -10,6 +10,7 @@
 // of two finite entries that reaches 2^32 - 1 raises the overflow flag
 // instead of wrapping.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 #include "prof.cuh"
@@ -352,6 +353,94 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 8, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     if (h[0]) return fail(CLDIAM_ERR_OVERFLOW, "a quotient distance reached 2^32 - 1");
+    *phi = h[1];
+    return CLDIAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the quotient diameter, for callers that may not
+// allocate device memory.  All scratch lives in one file-scope device array:
+// three control words (overflow, result, validation) and, for dense inputs,
+// the Floyd-Warshall matrix of up to kNoAllocMaxK x kNoAllocMaxK entries.  The
+// array exists once per GPU that loads the library and stays resident until
+// the process exits; every call reuses it, so calls whose work overlaps on the
+// GPU race on it.
+constexpr uint32_t kNoAllocMaxK = 1024;    // dense (Floyd-Warshall) inputs
+constexpr uint32_t kNoAllocMaxSparseK = 51200;  // sparse inputs: distances live in shared memory
+constexpr size_t kNoAllocCtlWords = 64;    // keeps the matrix 256-byte aligned
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocCtlWords + (size_t)kNoAllocMaxK * kNoAllocMaxK];
+
+static std::mutex g_noalloc_mu;
+static uint32_t* g_noalloc_ptr[64];  // device address of the scratch array, per device
+
+cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                               cudaStream_t s, uint64_t* phi) {
+    *phi = 0;
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CLDIAM_ERR_UNSUPPORTED, "device ordinal above 63");
+    uint32_t* scratch = nullptr;
+    {
+        // one-time set-up per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    if (k <= 1) return CLDIAM_OK;
+    if (!is_device_ptr(off) || !is_device_ptr(col) || !is_device_ptr(w))
+        return fail(CLDIAM_ERR_INVALID_ARG, "off, col and w must be device memory (nothing is copied or allocated)");
+    uint64_t nnz = 0;
+    CLD_CUDA(cudaMemcpyAsync(&nnz, off + k, 8, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (nnz > 0xFFFFFFFFull) return fail(CLDIAM_ERR_INVALID_ARG, "more than 2^32 - 1 entries");
+    const bool sparse = (double)nnz * 8.0 < (double)k * k;
+    if (sparse ? k > kNoAllocMaxSparseK : k > kNoAllocMaxK)
+        return fail(CLDIAM_ERR_UNSUPPORTED, sparse ? "k above 51200, the allocation-free limit for sparse graphs"
+                                                   : "k above 1024, the allocation-free limit for dense graphs");
+    uint32_t* ovf = scratch + 0;
+    uint32_t* best = scratch + 1;
+    uint32_t* bad = scratch + 2;
+    CLD_CUDA(cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), s));  // the array keeps the last call's values
+    k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, bad);
+    CLD_LAUNCH_CHECK();
+    uint32_t h[3] = {0, 0, 0};
+    CLD_CUDA(cudaMemcpyAsync(h, scratch, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (h[2]) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
+    if (sparse) {
+        // batched SSSP: distances (and the CSR when it fits) in shared memory, only the control words here
+        constexpr int S = 8;
+        const int S_eff = ((size_t)k * 8 * 4 <= 220 * 1024) ? 8 : (((size_t)k * 4 * 4 <= 220 * 1024) ? 4 : 1);
+        if (S_eff == S) CLD_TRY(launch_msbf<8>(k, off, col, w, nnz, s, best, ovf));
+        else if (S_eff == 4) CLD_TRY(launch_msbf<4>(k, off, col, w, nnz, s, best, ovf));
+        else CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, best, ovf));
+    } else {
+        const uint32_t nt = (k + FT - 1) / FT;
+        const uint32_t kp = nt * FT;  // <= kNoAllocMaxK
+        uint32_t* M = scratch + kNoAllocCtlWords;
+        k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M, kp, k);
+        k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M);
+        CLD_LAUNCH_CHECK();
+        for (uint32_t r = 0; r < nt; ++r) {
+            k_fw_phase1<<<1, FTH, 0, s>>>(M, kp, r, ovf);
+            if (nt > 1) {
+                k_fw_phase2<<<dim3(nt - 1, 2), FTH, 0, s>>>(M, kp, r, ovf);
+                k_fw_phase3<<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M, kp, r, ovf);
+            }
+            CLD_LAUNCH_CHECK();
+        }
+        k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M, kp, k, best);
+        CLD_LAUNCH_CHECK();
+    }
+    CLD_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (h[0]) return fail(CLDIAM_ERR_OVERFLOW, "a distance reached 2^32 - 1");
     *phi = h[1];
     return CLDIAM_OK;
 }

@@ -64,6 +64,11 @@ void free_quotient(cldiam_quotient* q);
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
                               uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k);
 
+// Same result as apsp_max_device on device-resident inputs, with all scratch in a fixed
+// device array instead of allocations.
+cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
+                               cudaStream_t s, uint64_t* phi);
+
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
                          uint64_t* rounds);
 
