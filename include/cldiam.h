@@ -68,6 +68,7 @@ typedef int32_t cldiam_status;
 typedef struct cldiam_graph cldiam_graph;           /* device-resident symmetric CSR          */
 typedef struct cldiam_clustering cldiam_clustering; /* device-resident centers, D, cluster ids */
 typedef struct cldiam_quotient cldiam_quotient;     /* device-resident quotient CSR            */
+typedef struct cldiam_arena cldiam_arena;           /* many graphs packed in one device CSR arena */
 
 /* Options of cldiam_cluster.  Zero-initialised = the defaults. */
 typedef struct {
@@ -225,6 +226,33 @@ cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta
 cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
                          uint32_t flags, double tau, uint64_t seed, const cldiam_opts* opts, void* stream,
                          cldiam_result* out);
+
+/* ------------------------------------------------------------------------
+ * Many-graph form (no counterpart in the paper, which runs one graph on a
+ * cluster): graphs are packed into one device-resident CSR arena and a batch
+ * of (graph, tau, seed) jobs runs the whole method -- CLUSTER (Algorithm 1),
+ * the weighted quotient graph and Phi_approx (Section 4) -- in one persistent
+ * launch, one graph per CTA at a time, largest graphs first.  Every result is
+ * identical to cldiam_cluster + cldiam_quotient_build + cldiam_estimate on the
+ * same graph, tau and seed with the same options.
+ */
+/* Empty arena on `stream`; hbm_budget_bytes (0 = unlimited) caps the device memory it may hold
+ * (graphs plus the batch workspace); an add that would exceed it fails with OOM. */
+cldiam_status cldiam_arena_create(uint64_t hbm_budget_bytes, void* stream, cldiam_arena** out);
+/* Build one graph's CSR (as cldiam_build_csr with `flags`) and append it; *graph_id is its index. */
+cldiam_status cldiam_arena_add(cldiam_arena* a, const uint32_t* src, const uint32_t* dst, const uint32_t* w,
+                               uint64_t m, uint32_t n, uint32_t flags, uint32_t* graph_id);
+/* Number of graphs and device bytes held (either pointer may be NULL). */
+cldiam_status cldiam_arena_info(const cldiam_arena* a, uint32_t* graphs, uint64_t* device_bytes);
+/* A graph handle viewing one arena graph, for the one-graph entry points; free it with
+ * cldiam_graph_free (the arena's memory is not released) before freeing the arena. */
+cldiam_status cldiam_arena_graph(cldiam_arena* a, uint32_t graph_id, cldiam_graph** out);
+/* Run `count` jobs: graph_ids[i], tau[i] (> 0), seed[i]; opts applies to all (NULL = defaults).
+ * out[i] (host) receives job i's result; status[i] (host, may be NULL) its status.  Returns the
+ * first failing status (OVERFLOW, DIVERGED, TIMEOUT) if any job failed, else OK. */
+cldiam_status cldiam_batch_run(cldiam_arena* a, const uint32_t* graph_ids, const double* tau, const uint64_t* seed,
+                               uint32_t count, const cldiam_opts* opts, cldiam_result* out, cldiam_status* status);
+void cldiam_arena_free(cldiam_arena* a);
 
 /* ------------------------------------------------------------------------
  * Instrumentation.  No counterpart in the method itself; it exposes what the

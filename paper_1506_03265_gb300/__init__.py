@@ -99,6 +99,12 @@ def load(build_if_missing: bool = True):
             "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
             "cldiam_run": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                 ctypes.c_uint64, P, P, P]),
+            "cldiam_arena_create": (st, [ctypes.c_uint64, P, PP]),
+            "cldiam_arena_add": (st, [P, P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, P]),
+            "cldiam_arena_info": (st, [P, P, P]),
+            "cldiam_arena_graph": (st, [P, ctypes.c_uint32, PP]),
+            "cldiam_batch_run": (st, [P, P, P, P, ctypes.c_uint32, P, P, P]),
+            "cldiam_arena_free": (None, [P]),
             "cldiam_profile_set_timing": (st, [ctypes.c_uint32]),
             "cldiam_profile_reset": (st, []),
             "cldiam_profile_num_classes": (ctypes.c_uint32, []),
@@ -236,6 +242,57 @@ class Quotient(_Handle):
         _check(load().cldiam_quotient_copy(self.handle, off.ctypes.data, col.ctypes.data if z else None,
                                            w.ctypes.data if z else None), "cldiam_quotient_copy")
         return off, col, w
+
+
+class ArenaGraph(Graph):
+    """A graph handle viewing one arena graph (keeps the arena alive)."""
+
+    def __init__(self, h, arena):
+        super().__init__(h)
+        self.arena = arena
+
+
+class Arena(_Handle):
+    """Many graphs in one device CSR arena, run as one persistent batch (cldiam_arena_* / cldiam_batch_run)."""
+    _free = "cldiam_arena_free"
+
+    def add(self, src, dst, w, n: int, lcc: bool = True) -> int:
+        src, dst, w = _u32(src), _u32(dst), _u32(w)
+        gid = ctypes.c_uint32()
+        _check(load().cldiam_arena_add(self.handle, _ptr(src), _ptr(dst), _ptr(w), int(src.shape[0]), n,
+                                       CSR_LCC if lcc else 0, ctypes.byref(gid)), "cldiam_arena_add")
+        return gid.value
+
+    def info(self):
+        g = ctypes.c_uint32(); b = ctypes.c_uint64()
+        _check(load().cldiam_arena_info(self.handle, ctypes.byref(g), ctypes.byref(b)), "cldiam_arena_info")
+        return g.value, b.value
+
+    def graph(self, gid: int) -> "ArenaGraph":
+        h = ctypes.c_void_p()
+        _check(load().cldiam_arena_graph(self.handle, gid, ctypes.byref(h)), "cldiam_arena_graph")
+        return ArenaGraph(h.value, self)
+
+    def run(self, ids, taus, seeds, delta0_mode=DELTA0_AVG, raise_on_error=True):
+        """Batch of jobs; returns (list of result dicts, list of statuses)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        cnt = int(ids.size)
+        res = (Result * max(cnt, 1))()
+        sts = np.zeros(max(cnt, 1), np.int32)
+        o = make_opts(delta0_mode)
+        st = load().cldiam_batch_run(self.handle, ids.ctypes.data, taus.ctypes.data, seeds.ctypes.data, cnt,
+                                     ctypes.byref(o), ctypes.cast(res, ctypes.c_void_p), sts.ctypes.data)
+        if raise_on_error:
+            _check(st, "cldiam_batch_run")
+        return [res[i].as_dict() for i in range(cnt)], [int(x) for x in sts[:cnt]]
+
+
+def arena_create(hbm_budget_bytes: int = 0, stream=None) -> Arena:
+    h = ctypes.c_void_p()
+    _check(load().cldiam_arena_create(hbm_budget_bytes, _stream_ptr(stream), ctypes.byref(h)), "cldiam_arena_create")
+    return Arena(h.value)
 
 
 def build_csr(src, dst, w, n: int, lcc: bool = True, stream=None) -> Graph:

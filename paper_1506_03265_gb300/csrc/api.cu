@@ -259,6 +259,33 @@ cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta
     return guarded([&] { return sssp_delta(g, source, delta, dist, ecc, rounds); });
 }
 
+cldiam_status cldiam_arena_create(uint64_t hbm_budget_bytes, void* stream, cldiam_arena** out) {
+    return guarded([&] { return arena_create(hbm_budget_bytes, resolve_stream(stream), out); });
+}
+
+cldiam_status cldiam_arena_add(cldiam_arena* a, const uint32_t* src, const uint32_t* dst, const uint32_t* w,
+                               uint64_t m, uint32_t n, uint32_t flags, uint32_t* graph_id) {
+    return guarded([&] { return arena_add(a, src, dst, w, m, n, flags, graph_id); });
+}
+
+cldiam_status cldiam_arena_info(const cldiam_arena* a, uint32_t* graphs, uint64_t* device_bytes) {
+    if (!a) return fail(CLDIAM_ERR_INVALID_ARG, "NULL arena");
+    if (graphs) *graphs = arena_count(a);
+    if (device_bytes) *device_bytes = arena_device_bytes(a);
+    return CLDIAM_OK;
+}
+
+cldiam_status cldiam_arena_graph(cldiam_arena* a, uint32_t graph_id, cldiam_graph** out) {
+    return guarded([&] { return arena_graph(a, graph_id, out); });
+}
+
+cldiam_status cldiam_batch_run(cldiam_arena* a, const uint32_t* graph_ids, const double* tau, const uint64_t* seed,
+                               uint32_t count, const cldiam_opts* opts, cldiam_result* out, cldiam_status* status) {
+    return guarded([&] { return batch_run(a, graph_ids, tau, seed, count, opts, out, status); });
+}
+
+void cldiam_arena_free(cldiam_arena* a) { arena_free(a); }
+
 cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
                          uint32_t flags, double tau, uint64_t seed, const cldiam_opts* opts, void* stream,
                          cldiam_result* out) {

@@ -1,0 +1,697 @@
+// Many-graph form: graphs packed into one device CSR arena and processed by
+// one persistent launch.  Each CTA (1024 threads, one per SM) takes whole
+// graphs from a work queue (largest first) and runs CLUSTER(tau) (the phase
+// bodies of cluster_dev.cuh, rank 0 of 1, block barriers between phases),
+// the weighted quotient graph (Section 4) and the exact Phi(G_C) for it.
+// Results are identical to the one-graph-per-launch path: the same phase
+// bodies run in the same order on the same data, and the stage control uses
+// the same host-computed log2 n.
+//
+// The quotient is deduplicated in a dense k x k matrix (atomicMin per
+// inter-cluster edge) instead of a sort; its row order equals the sorted
+// quotient CSR of the other path.  Graphs whose quotient exceeds the dense
+// capacity are finished with the one-graph path after the launch.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "cluster_dev.cuh"
+#include "internal.cuh"
+#include "prof.cuh"
+
+namespace cld {
+
+namespace {
+
+constexpr int BT = 1024;              // threads per CTA
+constexpr uint32_t kDenseCap = 1024;  // largest quotient deduplicated in the dense matrix
+constexpr uint32_t kSmemFwK = 200;    // quotients up to this size are closed by Floyd-Warshall in shared memory
+constexpr uint32_t kJobOk = 0, kJobNeedsPlain = 1, kJobOverflow = 2, kJobDiverged = 3, kJobTimeout = 4;
+
+struct ArenaDesc {  // one graph of the arena (device copy)
+    uint64_t off_base;  // into the arena's offset array (n + 1 entries, local values)
+    uint64_t adj_base;  // into the arena's adjacency / row arrays
+    uint64_t nnz;
+    uint32_t n;
+    uint32_t connected;
+};
+
+struct Job {
+    double tau;
+    double L;  // log2 n, computed on the host
+    uint64_t seed;
+    uint32_t graph;
+    uint32_t delta0;
+    uint32_t out;  // index in the caller's result array
+    uint32_t pad;
+};
+
+struct Workspace {  // one slice per CTA
+    unsigned long long* key;
+    unsigned long long* fkey[2];
+    uint32_t* center;
+    uint32_t* D;
+    uint32_t* R;
+    uint32_t* stamp;
+    uint32_t* fv[2];
+    uint32_t* fpre[2];
+    uint32_t* next;
+    uint32_t* cid;
+    uint32_t* M;      // dense quotient, kDenseCap^2
+    uint32_t* qoff;   // quotient CSR extracted from M
+    uint32_t* qcol;
+    uint32_t* qw;
+    Counters* ctr;
+};
+
+struct JobOut {
+    cldiam_result r;
+    uint32_t status;
+    uint32_t pad;
+};
+
+__device__ __forceinline__ uint32_t relax_min_u32(uint32_t c, uint32_t a, uint32_t b, bool& ovf) {
+    const uint32_t s = a + b;
+    const bool carry = s < a;
+    const bool finite = (a != kNone) & (b != kNone);
+    ovf |= finite & (carry | (s == kNone));
+    return (carry | !finite) ? c : (s < c ? s : c);
+}
+
+template <class T, class Op>
+__device__ __forceinline__ T block_all_reduce(T v, Op op, T* red) {
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 16));
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 8));
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 4));
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T x = l < nw ? red[l] : red[0];
+        x = op(x, __shfl_xor_sync(0xffffffffu, x, 16));
+        x = op(x, __shfl_xor_sync(0xffffffffu, x, 8));
+        x = op(x, __shfl_xor_sync(0xffffffffu, x, 4));
+        x = op(x, __shfl_xor_sync(0xffffffffu, x, 2));
+        x = op(x, __shfl_xor_sync(0xffffffffu, x, 1));
+        if (l == 0) red[32] = x;
+    }
+    __syncthreads();
+    const T r = red[32];
+    __syncthreads();
+    return r;
+}
+
+struct BatchSmem {
+    RelaxSmem relax;
+    unsigned long long scratch[33];
+    unsigned long long red64[33];
+    uint32_t red32[33];
+    uint32_t woff[33];
+    uint32_t job;
+    uint32_t changed[3];
+};
+
+// cid[v] = rank of v's center among all centers (block-wide scan); returns k
+__device__ uint32_t block_relabel(uint32_t n, const uint32_t* __restrict__ center, uint32_t* __restrict__ rank,
+                                  uint32_t* __restrict__ cid, BatchSmem& sm) {
+    const unsigned w = threadIdx.x >> 5, l = lane_id();
+    uint32_t running = 0;
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+        const uint32_t v = base + threadIdx.x;
+        const bool f = v < n && __ldcg(&center[v]) == v;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (l == 0) sm.woff[w] = (uint32_t)__popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t c = sm.woff[l];
+            const uint32_t incl = warp_incl_scan(c);
+            sm.woff[l] = incl - c;
+            if (l == 31) sm.woff[32] = incl;
+        }
+        __syncthreads();
+        if (f) rank[v] = running + sm.woff[w] + (uint32_t)__popc(bal & lanemask_lt());
+        running += sm.woff[32];
+        __syncthreads();
+    }
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) cid[v] = __ldcg(&rank[__ldcg(&center[v])]);
+    __syncthreads();
+    return running;
+}
+
+// exact max finite distance of the k-node quotient held densely in M (row stride k)
+__device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M, const Workspace& ws,
+                                            uint32_t* dyn, BatchSmem& sm, bool& ovf) {
+    if (k <= 1) return 0;
+    uint32_t best = 0;
+    if (k <= kSmemFwK) {
+        // Floyd-Warshall in shared memory; row p and column p are fixed during iteration p
+        for (uint32_t i = threadIdx.x; i < k * k; i += blockDim.x) dyn[i] = __ldcg(&M[i]);
+        __syncthreads();
+        for (uint32_t p = 0; p < k; ++p) {
+            for (uint32_t idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+                const uint32_t i = idx / k, j = idx - i * k;
+                dyn[idx] = relax_min_u32(dyn[idx], dyn[i * k + p], dyn[p * k + j], ovf);
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = threadIdx.x; i < k * k; i += blockDim.x)
+            if (dyn[i] != kNone && dyn[i] > best) best = dyn[i];
+    } else {
+        // quotient CSR from M (warp per row, ballot compaction keeps columns sorted), then
+        // multi-source Bellman-Ford, 8 sources at a time, distances in shared memory
+        const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
+        for (uint32_t a = w; a < k; a += nw) {
+            uint32_t c = 0;
+            for (uint32_t b0 = 0; b0 < k; b0 += 32) {
+                const uint32_t b = b0 + l;
+                c += __popc(__ballot_sync(0xffffffffu, b < k && b != a && __ldcg(&M[a * k + b]) != kNone));
+            }
+            if (l == 0) ws.qoff[a + 1] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ws.qoff[0] = 0;
+            for (uint32_t a = 0; a < k; ++a) ws.qoff[a + 1] += ws.qoff[a];
+        }
+        __syncthreads();
+        for (uint32_t a = w; a < k; a += nw) {
+            uint32_t pos = __ldcg(&ws.qoff[a]);
+            for (uint32_t b0 = 0; b0 < k; b0 += 32) {
+                const uint32_t b = b0 + l;
+                const uint32_t x = (b < k && b != a) ? __ldcg(&M[a * k + b]) : kNone;
+                const unsigned bal = __ballot_sync(0xffffffffu, x != kNone);
+                if (x != kNone) {
+                    const uint32_t at = pos + (uint32_t)__popc(bal & lanemask_lt());
+                    ws.qcol[at] = b;
+                    ws.qw[at] = x;
+                }
+                pos += (uint32_t)__popc(bal);
+            }
+        }
+        __syncthreads();
+        constexpr uint32_t S = 8, kSlots = 32 / S;
+        const uint32_t my_s = l % S, slot = l / S;
+        uint32_t* dist = dyn;  // k x S
+        for (uint32_t s0 = 0; s0 < k; s0 += S) {
+            for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x) dist[i] = (s0 + i % S == i / S) ? 0u : kNone;
+            if (threadIdx.x == 0) sm.changed[0] = sm.changed[1] = sm.changed[2] = 0;
+            __syncthreads();
+            for (uint32_t round = 0; round < k; ++round) {
+                const uint32_t slot_r = round % 3;
+                if (threadIdx.x == 0) sm.changed[(round + 1) % 3] = 0;
+                bool changed = false;
+                for (uint32_t v = w; v < k; v += nw) {
+                    const uint32_t beg = __ldcg(&ws.qoff[v]), end = __ldcg(&ws.qoff[v + 1]);
+                    uint32_t bv = kNone;
+                    for (uint32_t j = beg + slot; j < end; j += kSlots) {
+                        const uint32_t du = dist[__ldcg(&ws.qcol[j]) * S + my_s];
+                        if (du != kNone) {
+                            const uint64_t nd = (uint64_t)du + __ldcg(&ws.qw[j]);
+                            if (nd >= kNone) ovf = true;
+                            else bv = min(bv, (uint32_t)nd);
+                        }
+                    }
+#pragma unroll
+                    for (uint32_t o = S; o < 32; o <<= 1) bv = min(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+                    if (l < S && bv < dist[v * S + l]) {
+                        dist[v * S + l] = bv;
+                        changed = true;
+                    }
+                }
+                if (__any_sync(0xffffffffu, changed) && l == 0) sm.changed[slot_r] = 1;
+                __syncthreads();
+                if (!sm.changed[slot_r]) break;
+            }
+            for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x)
+                if (s0 + i % S < k && dist[i] != kNone && dist[i] > best) best = dist[i];
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    return block_all_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+}
+
+__global__ void __launch_bounds__(BT, 1)
+    k_batch(const ArenaDesc* __restrict__ descs, const Job* __restrict__ jobs, uint32_t njobs,
+            const uint64_t* __restrict__ arena_off, const uint2* __restrict__ arena_adj,
+            const uint32_t* __restrict__ arena_row, Workspace* __restrict__ wss, uint32_t* __restrict__ queue,
+            JobOut* __restrict__ outs) {
+    extern __shared__ __align__(16) uint32_t dyn[];
+    __shared__ BatchSmem sm;
+    const Workspace ws = wss[blockIdx.x];
+    Counters* ctr = ws.ctr;
+    volatile Counters* vc = ctr;
+    const unsigned tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) sm.job = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t jid = sm.job;
+        __syncthreads();
+        if (jid >= njobs) break;
+        const Job job = jobs[jid];
+        const ArenaDesc d = descs[job.graph];
+        const uint32_t n = d.n;
+        const uint64_t* off = arena_off + d.off_base;
+        const uint2* adj = arena_adj + d.adj_base;
+        const uint32_t* row = arena_row + d.adj_base;
+        cldiam_result res;
+        memset(&res, 0, sizeof res);
+        uint32_t status = kJobOk;
+
+        for (uint32_t v = tid; v < n; v += BT) {
+            ws.center[v] = kNone;
+            ws.D[v] = 0;
+            ws.R[v] = 0;
+            ws.stamp[v] = 0;
+            ws.key[v] = kInfKey;
+        }
+        if (tid == 0) memset(ctr, 0, sizeof(Counters));
+        __syncthreads();
+
+        uint64_t U = n, frozen_deg = 0, covered = 0;
+        uint32_t stage = 1, stepid = 0, delta = job.delta0, cur = 0;
+        const bool pull_ok = d.nnz < 0x80000000ull;
+        uint32_t nf = 0, E = 0;
+        for (;;) {
+            uint64_t thr = 0;
+            if (!stage_threshold(U, job.tau, job.L, &thr)) break;
+            if (stage > kMaxStages) {
+                status = kJobDiverged;
+                break;
+            }
+            if (tid == 0) {
+                ctr->selected = 0;
+                ctr->front = 0;
+            }
+            __syncthreads();
+            dev_select(n, ws.center, ws.key, job.seed, stage, thr, ctr, 0, 1);
+            __syncthreads();
+            {
+                const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
+                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
+                            sm.scratch, 0, 1);
+            }
+            __syncthreads();
+            covered = vc->selected;
+            res.centers_drawn += vc->selected;
+            nf = (uint32_t)(vc->front >> 32);
+            E = (uint32_t)vc->front;
+            __syncthreads();
+            for (;;) {
+                uint32_t updated;
+                do {
+                    ++stepid;
+                    updated = 0;
+                    if (nf > 0) {
+                        if (tid == 0) {
+                            ctr->newly_covered = 0;
+                            ctr->front = 0;
+                            ctr->nnext = 0;
+                        }
+                        __syncthreads();
+                        dev_relax(ws.fv[cur], ws.fkey[cur], ws.fpre[cur], nf, E, off, adj, ws.center, ws.key, delta,
+                                  ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
+                        __syncthreads();
+                        const uint32_t nn = vc->nnext;
+                        dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fv[cur ^ 1], ws.fkey[cur ^ 1],
+                                     ws.fpre[cur ^ 1], ctr, sm.scratch, 0, 1);
+                        __syncthreads();
+                        updated = nn;
+                        covered += vc->newly_covered;
+                        res.edges_scanned += E;
+                        nf = (uint32_t)(vc->front >> 32);
+                        E = (uint32_t)vc->front;
+                        cur ^= 1;
+                        __syncthreads();
+                    }
+                    res.steps++;
+                    res.node_updates += updated;
+                } while (updated != 0 && 2 * covered < U);
+                if (2 * covered >= U) break;
+                bool growable = false;
+                if (delta < kDeltaMax && d.connected) {
+                    growable = covered > 0 || U < n;
+                } else if (delta < kDeltaMax && d.nnz) {
+                    if (tid == 0) ctr->growable = 0;
+                    __syncthreads();
+                    dev_growable(row, adj, d.nnz, ws.key, ctr, 0, 1);
+                    __syncthreads();
+                    growable = vc->growable != 0;
+                    __syncthreads();
+                }
+                if (!growable) {
+                    res.guard_exits++;
+                    break;
+                }
+                delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
+                res.doublings++;
+                if (tid == 0) ctr->front = 0;
+                __syncthreads();
+                {
+                    const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
+                    dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
+                                sm.scratch, 0, 1);
+                }
+                __syncthreads();
+                nf = (uint32_t)(vc->front >> 32);
+                E = (uint32_t)vc->front;
+                __syncthreads();
+            }
+            if (tid == 0) {
+                ctr->frozen = 0;
+                ctr->frozen_deg = 0;
+            }
+            __syncthreads();
+            dev_finalize_d(n, ws.key, ws.center, ws.R, ws.D, ctr, 0, 1);
+            __syncthreads();
+            dev_finalize_freeze(n, ws.key, ws.center, ws.R, ws.D, off, ctr, 0, 1);
+            __syncthreads();
+            if (vc->overflow) status = kJobOverflow;
+            U -= vc->frozen;
+            frozen_deg += vc->frozen_deg;
+            res.stages++;
+            ++stage;
+            __syncthreads();
+            if (status != kJobOk) break;
+        }
+        if (status == kJobOk) {
+            dev_singletons(n, ws.center, ws.D, 0, 1);
+            __syncthreads();
+            res.delta_end = delta;
+            const uint32_t k = block_relabel(n, ws.center, ws.stamp, ws.cid, sm);  // stamp reused as rank
+            res.k = k;
+            const uint32_t rmax =
+                block_all_reduce([&] {
+                    uint32_t m = 0;
+                    for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
+                    return m;
+                }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+            res.radius = rmax;
+            if (k > kDenseCap) {
+                status = kJobNeedsPlain;
+            } else {
+                // weighted quotient graph, deduplicated densely
+                uint32_t* M = ws.M;
+                for (uint32_t i = tid; i < k * k; i += BT) M[i] = (i / k == i % k) ? 0u : kNone;
+                __syncthreads();
+                bool ovf = false;
+                for (uint64_t i = tid; i < d.nnz; i += BT) {
+                    const uint32_t u = row[i];
+                    const uint2 e = adj[i];
+                    const uint32_t a = __ldcg(&ws.cid[u]), b = __ldcg(&ws.cid[e.x]);
+                    if (a != b) {
+                        uint64_t s = (uint64_t)__ldcg(&ws.D[u]) + e.y + __ldcg(&ws.D[e.x]);
+                        if (s >= 0xFFFFFFFFull) {
+                            ovf = true;
+                            s = 0xFFFFFFFEull;
+                        }
+                        atomicMin(&M[(size_t)a * k + b], (uint32_t)s);
+                    }
+                }
+                __syncthreads();
+                const unsigned long long qe = block_all_reduce(
+                    [&] {
+                        unsigned long long c = 0;
+                        for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
+                        return c;
+                    }(),
+                    [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
+                res.quotient_edges = qe;
+                bool ovf2 = false;
+                const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2);
+                const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
+                                                          [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
+                if (any_ovf) status = kJobOverflow;
+                res.phi_gc = phi;
+                res.phi_approx = (uint64_t)phi + 2ull * rmax;
+            }
+        }
+        if (tid == 0) {
+            outs[job.out].r = res;
+            outs[job.out].status = status;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+}  // namespace cld
+
+// ---------------------------------------------------------------------------- arena
+struct cldiam_arena {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    std::vector<cld::ArenaDesc> graphs;
+    std::vector<uint64_t> wsum_upper;
+    std::vector<uint32_t> wmin;
+    uint64_t* off = nullptr;
+    uint2* adj = nullptr;
+    uint32_t* row = nullptr;
+    uint64_t off_cap = 0, adj_cap = 0, off_used = 0, adj_used = 0;
+    void* ws = nullptr;  // cached per-CTA workspaces
+    size_t ws_bytes = 0;
+};
+
+namespace cld {
+
+static uint64_t arena_bytes(const cldiam_arena* a) { return a->off_cap * 8 + a->adj_cap * 12 + a->ws_bytes; }
+
+// grow a device array to hold `need` elements (doubling), keeping the first `used`
+template <class T>
+static cldiam_status grow(T** p, uint64_t* cap, uint64_t used, uint64_t need, cudaStream_t s) {
+    if (need <= *cap) return CLDIAM_OK;
+    uint64_t nc = std::max<uint64_t>(need, *cap * 2 + 1024);
+    T* q = nullptr;
+    CLD_TRY(dmalloc(reinterpret_cast<void**>(&q), nc * sizeof(T), s));
+    if (used) CLD_CUDA(cudaMemcpyAsync(q, *p, used * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    dfree(*p, s);
+    *p = q;
+    *cap = nc;
+    return CLDIAM_OK;
+}
+
+cldiam_status arena_create(uint64_t budget, cudaStream_t s, cldiam_arena** out) {
+    if (!out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL out");
+    cldiam_arena* a = new cldiam_arena();
+    cudaGetDevice(&a->device);
+    a->stream = s;
+    a->budget = budget;
+    *out = a;
+    return CLDIAM_OK;
+}
+
+void arena_free(cldiam_arena* a) {
+    if (!a) return;
+    dfree(a->off, a->stream);
+    dfree(a->adj, a->stream);
+    dfree(a->row, a->stream);
+    dfree(a->ws, a->stream);
+    cudaStreamSynchronize(a->stream);
+    delete a;
+}
+
+cldiam_status arena_add(cldiam_arena* a, const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m,
+                        uint32_t n, uint32_t flags, uint32_t* id) {
+    if (!a || !id) return fail(CLDIAM_ERR_INVALID_ARG, "NULL arena or id");
+    cldiam_graph* g = nullptr;
+    CLD_TRY(build_csr(src, dst, w, m, n, flags, a->stream, &g));
+    struct Free {
+        cldiam_graph* g;
+        ~Free() { free_graph(g); }
+    } fg{g};
+    const uint64_t need_off = a->off_used + g->n + 1, need_adj = a->adj_used + g->nnz;
+    const uint64_t extra = (need_off > a->off_cap ? (need_off - a->off_cap) * 8 : 0) +
+                           (need_adj > a->adj_cap ? (need_adj - a->adj_cap) * 12 : 0);
+    if (a->budget && arena_bytes(a) + extra > a->budget)
+        return fail(CLDIAM_ERR_OOM, "graph does not fit the arena's device memory budget");
+    CLD_TRY(grow(&a->off, &a->off_cap, a->off_used, need_off, a->stream));
+    {
+        uint64_t cap = a->adj_cap;
+        CLD_TRY(grow(&a->adj, &cap, a->adj_used, need_adj, a->stream));
+        uint64_t cap2 = a->adj_cap;
+        CLD_TRY(grow(&a->row, &cap2, a->adj_used, need_adj, a->stream));
+        a->adj_cap = std::max(cap, cap2);
+    }
+    CLD_CUDA(cudaMemcpyAsync(a->off + a->off_used, g->off, (g->n + 1) * 8, cudaMemcpyDeviceToDevice, a->stream));
+    if (g->nnz) {
+        CLD_CUDA(cudaMemcpyAsync(a->adj + a->adj_used, g->adj, g->nnz * 8, cudaMemcpyDeviceToDevice, a->stream));
+        CLD_CUDA(cudaMemcpyAsync(a->row + a->adj_used, g->row, g->nnz * 4, cudaMemcpyDeviceToDevice, a->stream));
+    }
+    ArenaDesc dsc{};
+    dsc.off_base = a->off_used;
+    dsc.adj_base = a->adj_used;
+    dsc.nnz = g->nnz;
+    dsc.n = g->n;
+    dsc.connected = g->connected ? 1u : 0u;
+    a->graphs.push_back(dsc);
+    a->wsum_upper.push_back(g->wsum_upper);
+    a->wmin.push_back(g->wmin);
+    a->off_used = need_off;
+    a->adj_used = need_adj;
+    *id = (uint32_t)(a->graphs.size() - 1);
+    CLD_CUDA(cudaStreamSynchronize(a->stream));
+    return CLDIAM_OK;
+}
+
+// a non-owning graph handle over one arena graph (for the one-graph path)
+static void arena_view(const cldiam_arena* a, uint32_t id, cldiam_graph* g) {
+    const ArenaDesc& d = a->graphs[id];
+    g->device = a->device;
+    g->stream = a->stream;
+    g->n = d.n;
+    g->nnz = d.nnz;
+    g->off = a->off + d.off_base;
+    g->adj = a->adj + d.adj_base;
+    g->row = a->row + d.adj_base;
+    g->orig = nullptr;
+    g->wsum_upper = a->wsum_upper[id];
+    g->wmin = a->wmin[id];
+    g->connected = d.connected != 0;
+    g->borrowed = true;
+}
+
+cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out) {
+    if (!a || !out || id >= a->graphs.size()) return fail(CLDIAM_ERR_INVALID_ARG, "bad arena or graph id");
+    cldiam_graph* g = new cldiam_graph();
+    arena_view(a, id, g);
+    CLD_TRY(g->host.alloc(256));
+    *out = g;
+    return CLDIAM_OK;
+}
+
+uint32_t arena_count(const cldiam_arena* a) { return (uint32_t)a->graphs.size(); }
+uint64_t arena_device_bytes(const cldiam_arena* a) { return arena_bytes(a); }
+
+cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau, const uint64_t* seed, uint32_t count,
+                        const cldiam_opts* o, cldiam_result* out, cldiam_status* status) {
+    if (!a || (count && (!ids || !tau || !seed || !out))) return fail(CLDIAM_ERR_INVALID_ARG, "NULL argument");
+    if (count == 0) return CLDIAM_OK;
+    cldiam_opts opts{};
+    if (o) opts = *o;
+    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1] || opts.reserved[2])
+        return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
+    const cudaStream_t s = a->stream;
+    std::vector<Job> jobs(count);
+    uint32_t nmax = 1;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (ids[i] >= a->graphs.size()) return fail(CLDIAM_ERR_INVALID_ARG, "graph id out of range");
+        if (!(tau[i] > 0.0) || !std::isfinite(tau[i])) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be positive");
+        cldiam_graph view;
+        arena_view(a, ids[i], &view);
+        uint32_t d0 = 0;
+        CLD_TRY(delta0(&view, opts.delta0_mode, opts.delta0, &d0));
+        jobs[i].tau = tau[i];
+        jobs[i].L = std::log2((double)view.n);
+        jobs[i].seed = seed[i];
+        jobs[i].graph = ids[i];
+        jobs[i].delta0 = d0;
+        jobs[i].out = i;
+        nmax = std::max(nmax, view.n);
+    }
+    // largest graphs first: the work queue then balances the tail
+    std::stable_sort(jobs.begin(), jobs.end(), [&](const Job& x, const Job& y) {
+        return a->graphs[x.graph].nnz + a->graphs[x.graph].n > a->graphs[y.graph].nnz + a->graphs[y.graph].n;
+    });
+    const int nsm = num_sms();
+    // per-CTA workspace
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t n8 = al((size_t)nmax * 8), n4 = al((size_t)nmax * 4), f8 = al((size_t)nmax * 16),
+                 f4 = al((size_t)nmax * 8), mm = al((size_t)kDenseCap * kDenseCap * 4),
+                 qo = al(((size_t)kDenseCap + 1) * 4), ctrb = al(sizeof(Counters));
+    const size_t slice = n8 + 2 * f8 + 6 * n4 + 4 * f4 + mm + qo + 2 * mm + ctrb;
+    const size_t need = slice * nsm;
+    if (need > a->ws_bytes) {
+        dfree(a->ws, s);
+        a->ws = nullptr;
+        a->ws_bytes = 0;
+        CLD_TRY(dmalloc(&a->ws, need, s));
+        a->ws_bytes = need;
+    }
+    std::vector<Workspace> wsh(nsm);
+    for (int b = 0; b < nsm; ++b) {
+        char* p = static_cast<char*>(a->ws) + (size_t)b * slice;
+        Workspace& w = wsh[b];
+        w.key = reinterpret_cast<unsigned long long*>(p); p += n8;
+        w.fkey[0] = reinterpret_cast<unsigned long long*>(p); p += f8;
+        w.fkey[1] = reinterpret_cast<unsigned long long*>(p); p += f8;
+        w.center = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.D = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.R = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.stamp = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.next = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.cid = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.fv[0] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fv[1] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fpre[0] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fpre[1] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.M = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.qoff = reinterpret_cast<uint32_t*>(p); p += qo;
+        w.qcol = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.qw = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.ctr = reinterpret_cast<Counters*>(p);
+    }
+    DBuf<ArenaDesc> ddesc;
+    DBuf<Job> djobs;
+    DBuf<Workspace> dws;
+    DBuf<uint32_t> queue;
+    DBuf<JobOut> douts;
+    CLD_TRY(ddesc.alloc(a->graphs.size(), s));
+    CLD_TRY(djobs.alloc(count, s));
+    CLD_TRY(dws.alloc(nsm, s));
+    CLD_TRY(queue.alloc(1, s));
+    CLD_TRY(douts.alloc(count, s));
+    CLD_CUDA(cudaMemcpyAsync(ddesc.get(), a->graphs.data(), a->graphs.size() * sizeof(ArenaDesc),
+                             cudaMemcpyHostToDevice, s));
+    CLD_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), count * sizeof(Job), cudaMemcpyHostToDevice, s));
+    CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
+    CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
+    const size_t dyn = std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * 8 * 4);
+    static bool attr[64];
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), count, a->off, a->adj, a->row, dws.get(),
+                                                   queue.get(), douts.get()));
+    CLD_LAUNCH_CHECK();
+    std::vector<JobOut> ho(count);
+    CLD_CUDA(cudaMemcpyAsync(ho.data(), douts.get(), count * sizeof(JobOut), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    cldiam_status first_err = CLDIAM_OK;
+    for (uint32_t i = 0; i < count; ++i) {
+        cldiam_status st = CLDIAM_OK;
+        if (ho[i].status == kJobNeedsPlain) {
+            // quotient larger than the dense capacity: finish this graph with the one-graph path
+            cldiam_graph view;
+            arena_view(a, ids[i], &view);
+            CLD_TRY(view.host.alloc(256));
+            cldiam_clustering* c = nullptr;
+            cldiam_quotient* q = nullptr;
+            st = cluster(&view, tau[i], seed[i], &opts, &c);
+            if (st == CLDIAM_OK) st = quotient(c, &q);
+            if (st == CLDIAM_OK) st = cldiam_estimate(q, &ho[i].r);
+            free_quotient(q);
+            free_clustering(c);
+        } else if (ho[i].status == kJobOverflow) {
+            st = CLDIAM_ERR_OVERFLOW;
+        } else if (ho[i].status == kJobDiverged) {
+            st = CLDIAM_ERR_DIVERGED;
+        } else if (ho[i].status != kJobOk) {
+            st = CLDIAM_ERR_TIMEOUT;
+        }
+        out[i] = ho[i].r;
+        if (status) status[i] = st;
+        if (st != CLDIAM_OK && first_err == CLDIAM_OK) first_err = st;
+    }
+    if (first_err != CLDIAM_OK) return fail(first_err, "one or more graphs of the batch failed (see status[])");
+    return CLDIAM_OK;
+}
+
+}  // namespace cld

@@ -204,10 +204,12 @@ void free_graph(cldiam_graph* g) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(g->device);
-    dfree(g->off, g->stream);
-    dfree(g->adj, g->stream);
-    dfree(g->row, g->stream);
-    dfree(g->orig, g->stream);
+    if (!g->borrowed) {
+        dfree(g->off, g->stream);
+        dfree(g->adj, g->stream);
+        dfree(g->row, g->stream);
+        dfree(g->orig, g->stream);
+    }
     cudaStreamSynchronize(g->stream);
     cudaSetDevice(cur);
     delete g;

@@ -17,6 +17,7 @@ struct cldiam_graph {
     uint32_t wmin = 0;
     uint32_t max_deg = 0;
     bool connected = false;      // built with the LCC flag: one connected component
+    bool borrowed = false;       // a view into arena memory: the arrays are not ours to free
     cld::Pinned host;            // small pinned block for counter read-back
 };
 
@@ -68,6 +69,17 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
 // device array instead of allocations.
 cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
                                cudaStream_t s, uint64_t* phi);
+
+// many-graph form (batch.cu)
+cldiam_status arena_create(uint64_t budget, cudaStream_t s, cldiam_arena** out);
+void arena_free(cldiam_arena* a);
+cldiam_status arena_add(cldiam_arena* a, const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m,
+                        uint32_t n, uint32_t flags, uint32_t* id);
+cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out);
+cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau, const uint64_t* seed, uint32_t count,
+                        const cldiam_opts* o, cldiam_result* out, cldiam_status* status);
+uint32_t arena_count(const cldiam_arena* a);
+uint64_t arena_device_bytes(const cldiam_arena* a);
 
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
                          uint64_t* rounds);

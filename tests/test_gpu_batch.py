@@ -1,0 +1,89 @@
+"""Many-graph form (one persistent launch) against the one-graph path and the oracle.
+
+Every batched result must equal cldiam_cluster + cldiam_quotient_build +
+cldiam_estimate on the same graph, tau and seed (integers: bit-exact).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi_gc", "radius", "phi_approx", "k", "stages", "steps", "doublings", "delta_end", "guard_exits",
+          "node_updates", "edges_scanned", "quotient_edges", "centers_drawn")
+
+
+@pytest.fixture(scope="module")
+def cd():
+    import paper_1506_03265_gb300 as m
+    m.load()
+    return m
+
+
+def tau_for(n):
+    # about sqrt(n) clusters: each stage draws ~gamma tau log n centers, about log2(n)/2 stages
+    L = max(1.0, math.log2(max(n, 2)))
+    return max(0.05, math.sqrt(n) / (4 * math.log(2) * L * max(1.0, L / 2)))
+
+
+def plain(cd, g, tau, seed, mode=0):
+    c = cd.cluster(g, tau, seed, delta0_mode=mode)
+    return cd.estimate(cd.quotient_build(c))
+
+
+def test_mixture_matches_one_graph_path(cd):
+    arena = cd.arena_create()
+    graphs = []
+    for gi in range(24):
+        kind, scale, side, sub = inputs.mix_params(4, gi)
+        e = inputs.rmat(min(scale, 12), 8, 1000, sub) if kind == 0 else inputs.grid(min(side, 96), 1000, sub)
+        gid = arena.add(e.src, e.dst, e.w, e.n)
+        graphs.append((gid, e))
+    ids = [gid for gid, _ in graphs]
+    taus = [tau_for(arena.graph(gid).n) for gid in ids]
+    seeds = [1000 + i for i in range(len(ids))]
+    res, st = arena.run(ids, taus, seeds)
+    assert all(x == 0 for x in st)
+    for (gid, e), tau, seed, r in zip(graphs, taus, seeds, res):
+        ref = plain(cd, arena.graph(gid), tau, seed)
+        assert {f: r[f] for f in FIELDS} == {f: ref[f] for f in FIELDS}, (gid, e)
+    # a few against the oracle too
+    for (gid, e), tau, seed, r in list(zip(graphs, taus, seeds, res))[:6]:
+        og = oracle.build_csr(e.n, e.src, e.dst, e.w)
+        ores, ocl, _ = oracle.cldiam(og, tau, seed)
+        assert (r["k"], r["phi_approx"], r["steps"]) == (ores.k, ores.phi_approx, ocl.stats["steps"])
+
+
+def test_repeated_jobs_and_edge_cases(cd):
+    arena = cd.arena_create()
+    z = np.zeros(0, np.uint32)
+    g_single = arena.add(z, z, z, 1)
+    n, rng = 300, np.random.default_rng(3)
+    s = rng.integers(0, n, 200).astype(np.uint32); d = rng.integers(0, n, 200).astype(np.uint32)
+    w = rng.integers(1, 50, 200).astype(np.uint32)
+    g_disc = arena.add(s, d, w, n, lcc=False)            # disconnected: fixed-point guard path
+    e = inputs.grid(128, 100, 9)
+    g_big_k = arena.add(e.src, e.dst, e.w, e.n)          # tau huge: all singletons, k = 16384 > dense capacity
+    e2 = inputs.rmat(11, 8, 1 << 20, 5)
+    g_r = arena.add(e2.src, e2.dst, e2.w, e2.n)
+    ids = [g_single, g_disc, g_big_k, g_r, g_r, g_disc]
+    taus = [1.0, 0.2, 1e7, 0.7, 0.7, 0.05]
+    seeds = [1, 2, 3, 4, 4, 9]
+    res, st = arena.run(ids, taus, seeds)
+    assert all(x == 0 for x in st)
+    for gid, tau, seed, r in zip(ids, taus, seeds, res):
+        ref = plain(cd, arena.graph(gid), tau, seed)
+        assert {f: r[f] for f in FIELDS} == {f: ref[f] for f in FIELDS}, gid
+    assert res[2]["k"] == 16384 and res[3] == res[4]
+
+
+def test_budget_admission(cd):
+    arena = cd.arena_create(hbm_budget_bytes=1 << 20)
+    e = inputs.grid(200, 100, 1)   # ~1.9 MB of CSR: over a 1 MiB budget
+    with pytest.raises(cd.CldiamError) as ei:
+        arena.add(e.src, e.dst, e.w, e.n)
+    assert ei.value.status == -2
