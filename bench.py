@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-graph leg")
+    ap.add_argument("--batched-count", type=int, default=2000)
+    ap.add_argument("--plain-sample-every", type=int, default=10)
     ap.add_argument("--profile-pass", action="store_true",
                     help="run one pipeline pass on the workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -173,6 +176,61 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows), "in_window": window,
                 "power_w_max": max(float(r[4]) for r in rows if r[4].replace(".", "").isdigit()) if rows else None}
+
+
+# ----------------------------------------------------------------------------- many-graph leg
+def batched_leg(cd, stream, count, sample_every, reps=3):
+    """graphs/s of one persistent batch launch vs the plain one-graph-per-call loop (same jobs)."""
+    import torch
+
+    import inputs
+    from inputs.workloads import MIX_DESCRIBE, MIX_SEED, mixture, mixture_tau
+    arena = cd.arena_create(stream=stream)
+    ids, taus, seeds, edges = [], [], [], 0
+    t0 = time.perf_counter()
+    for g, e in mixture(count, MIX_SEED):
+        gid = arena.add(e.src, e.dst, e.w, e.n)
+        view = arena.graph(gid)
+        n = view.n
+        edges += view.nnz // 2
+        view.free()
+        ids.append(gid)
+        taus.append(mixture_tau(n))
+        seeds.append(MIX_SEED * 1000 + g)
+    build_s = time.perf_counter() - t0
+    res, st = arena.run(ids, taus, seeds)  # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    cd.profile_reset()
+    e0.record(stream)
+    for _ in range(reps):
+        res2, _ = arena.run(ids, taus, seeds)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    launches = sum(v["launches"] for v in cd.profile_get().values()) / reps
+    assert res2 == res
+    # plain loop over a sample of the same jobs
+    sample = list(range(0, count, sample_every))
+    same = True
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for i in sample:
+        g = arena.graph(ids[i])
+        r = cd.estimate(cd.quotient_build(cd.cluster(g, taus[i], seeds[i])))
+        same &= all(r[f] == res[i][f] for f in r)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - p0) / len(sample)
+    arena.free()
+    gps = count / t_batch
+    return {"workload": "mix2000", "describe": MIX_DESCRIBE, "graphs": count, "undirected_edges": edges,
+            "graphs_per_s": round(gps, 1), "gteps": round(edges / t_batch / 1e9, 4),
+            "ms_per_batch": round(t_batch * 1e3, 2), "kernel_launches_per_batch": launches,
+            "plain_graphs_per_s": round(1.0 / t_plain, 1), "speedup_vs_plain": round(gps * t_plain, 2),
+            "plain_sample": f"every {sample_every}th job ({len(sample)} graphs), cldiam_cluster + "
+                            "cldiam_quotient_build + cldiam_estimate per graph on the same GPU",
+            "identical_to_plain_on_sample": bool(same), "arena_build_s": round(build_s, 1)}
 
 
 # ----------------------------------------------------------------------------- GPU leg
@@ -343,6 +401,8 @@ def run_gpu(args):
                           "ms": round(t_ds * 1e3, 3), "gteps": round(m_lcc / t_ds / 1e9, 4), "ecc": ecc,
                           "upper_bound": 2 * ecc, "rounds": rounds},
     }
+    if not args.no_batched:
+        line["batched"] = batched_leg(cd, stream, args.batched_count, args.plain_sample_every)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if dist:

@@ -31,3 +31,25 @@ WORKLOADS = {
     "rmat24": Workload("rmat24", "R-MAT scale 24, edge factor 16, w in [1,1000], seed 3, LCC",
                        lambda: rmat(24, 16, 1000, 3), tau=16.0, seed=3, target_k=4096),
 }
+
+
+def mixture_tau(n: int) -> float:
+    """tau for about sqrt(n) clusters on a mixture graph of n nodes (each stage draws about
+    gamma tau log2 n centers over roughly log2(n)/2 stages)."""
+    import math
+    L = max(1.0, math.log2(max(n, 2)))
+    return max(0.05, math.sqrt(n) / (4 * math.log(2) * L * max(1.0, L / 2)))
+
+
+MIX_SEED = 4
+MIX_COUNT = 2000
+MIX_DESCRIBE = ("2,000 graphs, seed 4: each an R-MAT (scale uniform 8..16, edge factor 8) or a mesh "
+                "(side round(2^U), U uniform in [5,9)) with probability 1/2; w in [1,1000]; LCC; "
+                "tau per graph for about sqrt(n) clusters")
+
+
+def mixture(count: int = MIX_COUNT, seed: int = MIX_SEED, W: int = 1000):
+    """Yield (g, EdgeList) for the many-graph workload."""
+    from . import mix_graph
+    for g in range(count):
+        yield g, mix_graph(seed, g, W)
