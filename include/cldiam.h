@@ -69,6 +69,7 @@ typedef struct cldiam_graph cldiam_graph;           /* device-resident symmetric
 typedef struct cldiam_clustering cldiam_clustering; /* device-resident centers, D, cluster ids */
 typedef struct cldiam_quotient cldiam_quotient;     /* device-resident quotient CSR            */
 typedef struct cldiam_arena cldiam_arena;           /* many graphs packed in one device CSR arena */
+typedef struct cldiam_server cldiam_server;         /* request server over an arena              */
 
 /* Options of cldiam_cluster.  Zero-initialised = the defaults. */
 typedef struct {
@@ -253,6 +254,40 @@ cldiam_status cldiam_arena_graph(cldiam_arena* a, uint32_t graph_id, cldiam_grap
 cldiam_status cldiam_batch_run(cldiam_arena* a, const uint32_t* graph_ids, const double* tau, const uint64_t* seed,
                                uint32_t count, const cldiam_opts* opts, cldiam_result* out, cldiam_status* status);
 void cldiam_arena_free(cldiam_arena* a);
+
+/* ------------------------------------------------------------------------
+ * Served form (no counterpart in the paper): diameter queries on arena graphs
+ * with continuous batching.  A persistent kernel keeps running; each of its
+ * CTAs takes the next submitted request as soon as it finishes the previous
+ * one, so requests that arrive while others run join at once and their work
+ * overlaps on the device.  Graphs above opts.big_nodes nodes run on the
+ * one-graph path on a second stream, on the SMs the kernel leaves free, one
+ * at a time, admitted when their device memory fits the budget.  Results are
+ * identical to the one-graph path (CLDIAM_DELTA0_AVG, default options).
+ */
+typedef struct {
+    uint32_t ctas;             /* CTAs of the serving kernel; 0 = SMs - 24 (the rest serve large graphs) */
+    uint32_t capacity;         /* requests over the server's lifetime; 0 = 2^20                         */
+    uint32_t big_nodes;        /* graphs with more nodes take the one-graph path; 0 = 2^19              */
+    uint32_t reserved;         /* must be 0                                                              */
+    uint64_t hbm_budget_bytes; /* device memory cap for arena + workspaces + large requests; 0 = none   */
+    double idle_seconds;       /* CTAs leave after this long without requests (relaunched on demand); 0 = 10 */
+} cldiam_server_opts;
+/* Start serving the graphs of `a` (which must outlive the server; add no graphs meanwhile). */
+cldiam_status cldiam_server_create(cldiam_arena* a, const cldiam_server_opts* opts, cldiam_server** out);
+/* Queue one query; *ticket identifies it.  BUSY when the lifetime capacity is used up. */
+cldiam_status cldiam_server_submit(cldiam_server* s, uint32_t graph_id, double tau, uint64_t seed, uint64_t* ticket);
+/* CLDIAM_ERR_BUSY until the query has finished; then its status, and *out (host) its result. */
+cldiam_status cldiam_server_poll(cldiam_server* s, uint64_t ticket, cldiam_result* out);
+/* Replay an arrival trace natively: query i is submitted arrival_s[i] seconds after the start;
+ * latency_s[i] = completion - arrival.  plain != 0 serves the same trace one query at a time in
+ * arrival order on the one-graph path instead (the baseline).  out/latency_s are host arrays of
+ * `count`; *elapsed_s (may be NULL) = wall time of the whole replay. */
+cldiam_status cldiam_server_replay(cldiam_server* s, const uint32_t* graph_ids, const double* tau,
+                                   const uint64_t* seed, const double* arrival_s, uint32_t count, int32_t plain,
+                                   cldiam_result* out, double* latency_s, double* elapsed_s);
+/* Finish the queries already submitted, stop the kernel and release everything the server holds. */
+void cldiam_server_free(cldiam_server* s);
 
 /* ------------------------------------------------------------------------
  * Instrumentation.  No counterpart in the method itself; it exposes what the

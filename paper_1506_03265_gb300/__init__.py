@@ -105,6 +105,11 @@ def load(build_if_missing: bool = True):
             "cldiam_arena_graph": (st, [P, ctypes.c_uint32, PP]),
             "cldiam_batch_run": (st, [P, P, P, P, ctypes.c_uint32, P, P, P]),
             "cldiam_arena_free": (None, [P]),
+            "cldiam_server_create": (st, [P, P, PP]),
+            "cldiam_server_submit": (st, [P, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64, P]),
+            "cldiam_server_poll": (st, [P, ctypes.c_uint64, P]),
+            "cldiam_server_replay": (st, [P, P, P, P, P, ctypes.c_uint32, ctypes.c_int32, P, P, P]),
+            "cldiam_server_free": (None, [P]),
             "cldiam_profile_set_timing": (st, [ctypes.c_uint32]),
             "cldiam_profile_reset": (st, []),
             "cldiam_profile_num_classes": (ctypes.c_uint32, []),
@@ -287,6 +292,57 @@ class Arena(_Handle):
         if raise_on_error:
             _check(st, "cldiam_batch_run")
         return [res[i].as_dict() for i in range(cnt)], [int(x) for x in sts[:cnt]]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("ctas", ctypes.c_uint32), ("capacity", ctypes.c_uint32), ("big_nodes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64), ("idle_seconds", ctypes.c_double)]
+
+
+class Server(_Handle):
+    """Continuous-batching query server over an arena (cldiam_server_*)."""
+    _free = "cldiam_server_free"
+
+    def __init__(self, h, arena):
+        super().__init__(h)
+        self.arena = arena
+
+    def submit(self, graph_id: int, tau: float, seed: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load().cldiam_server_submit(self.handle, graph_id, float(tau), seed, ctypes.byref(t)),
+               "cldiam_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """Result dict when finished, None while busy."""
+        r = Result()
+        st = load().cldiam_server_poll(self.handle, ticket, ctypes.byref(r))
+        if st == -6:
+            return None
+        _check(st, "cldiam_server_poll")
+        return r.as_dict()
+
+    def replay(self, ids, taus, seeds, arrivals, plain=False):
+        """Native trace replay; returns (results, latencies in s, elapsed s)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        arr = np.ascontiguousarray(arrivals, dtype=np.float64)
+        cnt = int(ids.size)
+        res = (Result * max(cnt, 1))()
+        lat = np.zeros(max(cnt, 1), np.float64)
+        el = ctypes.c_double()
+        _check(load().cldiam_server_replay(self.handle, ids.ctypes.data, taus.ctypes.data, seeds.ctypes.data,
+                                           arr.ctypes.data, cnt, 1 if plain else 0, ctypes.cast(res, ctypes.c_void_p),
+                                           lat.ctypes.data, ctypes.byref(el)), "cldiam_server_replay")
+        return [res[i].as_dict() for i in range(cnt)], lat[:cnt], el.value
+
+
+def server_create(arena: "Arena", ctas=0, capacity=0, big_nodes=0, hbm_budget_bytes=0, idle_seconds=0.0) -> Server:
+    o = ServerOpts(ctas, capacity, big_nodes, 0, hbm_budget_bytes, idle_seconds)
+    h = ctypes.c_void_p()
+    _check(load().cldiam_server_create(arena.handle, ctypes.byref(o), ctypes.byref(h)), "cldiam_server_create")
+    return Server(h.value, arena)
 
 
 def arena_create(hbm_budget_bytes: int = 0, stream=None) -> Arena:

@@ -286,6 +286,29 @@ cldiam_status cldiam_batch_run(cldiam_arena* a, const uint32_t* graph_ids, const
 
 void cldiam_arena_free(cldiam_arena* a) { arena_free(a); }
 
+cldiam_status cldiam_server_create(cldiam_arena* a, const cldiam_server_opts* opts, cldiam_server** out) {
+    if (opts && opts->reserved) return fail(CLDIAM_ERR_INVALID_ARG, "reserved must be 0");
+    return guarded([&] { return server_create(a, opts, out); });
+}
+
+cldiam_status cldiam_server_submit(cldiam_server* s, uint32_t graph_id, double tau, uint64_t seed, uint64_t* ticket) {
+    return guarded([&] { return server_submit(s, graph_id, tau, seed, ticket); });
+}
+
+cldiam_status cldiam_server_poll(cldiam_server* s, uint64_t ticket, cldiam_result* out) {
+    return guarded([&] { return server_poll(s, ticket, out); });
+}
+
+cldiam_status cldiam_server_replay(cldiam_server* s, const uint32_t* graph_ids, const double* tau,
+                                   const uint64_t* seed, const double* arrival_s, uint32_t count, int32_t plain,
+                                   cldiam_result* out, double* latency_s, double* elapsed_s) {
+    return guarded([&] {
+        return server_replay(s, graph_ids, tau, seed, arrival_s, count, plain, out, latency_s, elapsed_s);
+    });
+}
+
+void cldiam_server_free(cldiam_server* s) { server_free(s); }
+
 cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
                          uint32_t flags, double tau, uint64_t seed, const cldiam_opts* opts, void* stream,
                          cldiam_result* out) {

@@ -12,8 +12,14 @@
 // quotient CSR of the other path.  Graphs whose quotient exceeds the dense
 // capacity are finished with the one-graph path after the launch.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "cluster_dev.cuh"
@@ -234,6 +240,196 @@ __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M
     return block_all_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
 }
 
+// One job: CLUSTER + quotient + Phi(G_C) of one arena graph by this CTA; thread 0 stores the result.
+__device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __restrict__ arena_off,
+                        const uint2* __restrict__ arena_adj, const uint32_t* __restrict__ arena_row,
+                        const Workspace& ws, BatchSmem& sm, uint32_t* dyn, JobOut* out) {
+    Counters* ctr = ws.ctr;
+    volatile Counters* vc = ctr;
+    const unsigned tid = threadIdx.x;
+    const uint32_t n = d.n;
+    const uint64_t* off = arena_off + d.off_base;
+    const uint2* adj = arena_adj + d.adj_base;
+    const uint32_t* row = arena_row + d.adj_base;
+    cldiam_result res;
+    memset(&res, 0, sizeof res);
+    uint32_t status = kJobOk;
+
+    for (uint32_t v = tid; v < n; v += BT) {
+        ws.center[v] = kNone;
+        ws.D[v] = 0;
+        ws.R[v] = 0;
+        ws.stamp[v] = 0;
+        ws.key[v] = kInfKey;
+    }
+    if (tid == 0) memset(ctr, 0, sizeof(Counters));
+    __syncthreads();
+
+    uint64_t U = n, frozen_deg = 0, covered = 0;
+    uint32_t stage = 1, stepid = 0, delta = job.delta0, cur = 0;
+    const bool pull_ok = d.nnz < 0x80000000ull;
+    uint32_t nf = 0, E = 0;
+    for (;;) {
+        uint64_t thr = 0;
+        if (!stage_threshold(U, job.tau, job.L, &thr)) break;
+        if (stage > kMaxStages) {
+            status = kJobDiverged;
+            break;
+        }
+        if (tid == 0) {
+            ctr->selected = 0;
+            ctr->front = 0;
+        }
+        __syncthreads();
+        dev_select(n, ws.center, ws.key, job.seed, stage, thr, ctr, 0, 1);
+        __syncthreads();
+        {
+            const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
+            dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
+                        sm.scratch, 0, 1);
+        }
+        __syncthreads();
+        covered = vc->selected;
+        res.centers_drawn += vc->selected;
+        nf = (uint32_t)(vc->front >> 32);
+        E = (uint32_t)vc->front;
+        __syncthreads();
+        for (;;) {
+            uint32_t updated;
+            do {
+                ++stepid;
+                updated = 0;
+                if (nf > 0) {
+                    if (tid == 0) {
+                        ctr->newly_covered = 0;
+                        ctr->front = 0;
+                        ctr->nnext = 0;
+                    }
+                    __syncthreads();
+                    dev_relax(ws.fv[cur], ws.fkey[cur], ws.fpre[cur], nf, E, off, adj, ws.center, ws.key, delta,
+                              ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
+                    __syncthreads();
+                    const uint32_t nn = vc->nnext;
+                    dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fv[cur ^ 1], ws.fkey[cur ^ 1],
+                                 ws.fpre[cur ^ 1], ctr, sm.scratch, 0, 1);
+                    __syncthreads();
+                    updated = nn;
+                    covered += vc->newly_covered;
+                    res.edges_scanned += E;
+                    nf = (uint32_t)(vc->front >> 32);
+                    E = (uint32_t)vc->front;
+                    cur ^= 1;
+                    __syncthreads();
+                }
+                res.steps++;
+                res.node_updates += updated;
+            } while (updated != 0 && 2 * covered < U);
+            if (2 * covered >= U) break;
+            bool growable = false;
+            if (delta < kDeltaMax && d.connected) {
+                growable = covered > 0 || U < n;
+            } else if (delta < kDeltaMax && d.nnz) {
+                if (tid == 0) ctr->growable = 0;
+                __syncthreads();
+                dev_growable(row, adj, d.nnz, ws.key, ctr, 0, 1);
+                __syncthreads();
+                growable = vc->growable != 0;
+                __syncthreads();
+            }
+            if (!growable) {
+                res.guard_exits++;
+                break;
+            }
+            delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
+            res.doublings++;
+            if (tid == 0) ctr->front = 0;
+            __syncthreads();
+            {
+                const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
+                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
+                            sm.scratch, 0, 1);
+            }
+            __syncthreads();
+            nf = (uint32_t)(vc->front >> 32);
+            E = (uint32_t)vc->front;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            ctr->frozen = 0;
+            ctr->frozen_deg = 0;
+        }
+        __syncthreads();
+        dev_finalize_d(n, ws.key, ws.center, ws.R, ws.D, ctr, 0, 1);
+        __syncthreads();
+        dev_finalize_freeze(n, ws.key, ws.center, ws.R, ws.D, off, ctr, 0, 1);
+        __syncthreads();
+        if (vc->overflow) status = kJobOverflow;
+        U -= vc->frozen;
+        frozen_deg += vc->frozen_deg;
+        res.stages++;
+        ++stage;
+        __syncthreads();
+        if (status != kJobOk) break;
+    }
+    if (status == kJobOk) {
+        dev_singletons(n, ws.center, ws.D, 0, 1);
+        __syncthreads();
+        res.delta_end = delta;
+        const uint32_t k = block_relabel(n, ws.center, ws.stamp, ws.cid, sm);  // stamp reused as rank
+        res.k = k;
+        const uint32_t rmax =
+            block_all_reduce([&] {
+                uint32_t m = 0;
+                for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
+                return m;
+            }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+        res.radius = rmax;
+        if (k > kDenseCap) {
+            status = kJobNeedsPlain;
+        } else {
+            // weighted quotient graph, deduplicated densely
+            uint32_t* M = ws.M;
+            for (uint32_t i = tid; i < k * k; i += BT) M[i] = (i / k == i % k) ? 0u : kNone;
+            __syncthreads();
+            bool ovf = false;
+            for (uint64_t i = tid; i < d.nnz; i += BT) {
+                const uint32_t u = row[i];
+                const uint2 e = adj[i];
+                const uint32_t a = __ldcg(&ws.cid[u]), b = __ldcg(&ws.cid[e.x]);
+                if (a != b) {
+                    uint64_t s = (uint64_t)__ldcg(&ws.D[u]) + e.y + __ldcg(&ws.D[e.x]);
+                    if (s >= 0xFFFFFFFFull) {
+                        ovf = true;
+                        s = 0xFFFFFFFEull;
+                    }
+                    atomicMin(&M[(size_t)a * k + b], (uint32_t)s);
+                }
+            }
+            __syncthreads();
+            const unsigned long long qe = block_all_reduce(
+                [&] {
+                    unsigned long long c = 0;
+                    for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
+                    return c;
+                }(),
+                [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
+            res.quotient_edges = qe;
+            bool ovf2 = false;
+            const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2);
+            const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
+                                                      [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
+            if (any_ovf) status = kJobOverflow;
+            res.phi_gc = phi;
+            res.phi_approx = (uint64_t)phi + 2ull * rmax;
+        }
+    }
+    if (tid == 0) {
+        out->r = res;
+        out->status = status;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(BT, 1)
     k_batch(const ArenaDesc* __restrict__ descs, const Job* __restrict__ jobs, uint32_t njobs,
             const uint64_t* __restrict__ arena_off, const uint2* __restrict__ arena_adj,
@@ -242,196 +438,89 @@ __global__ void __launch_bounds__(BT, 1)
     extern __shared__ __align__(16) uint32_t dyn[];
     __shared__ BatchSmem sm;
     const Workspace ws = wss[blockIdx.x];
-    Counters* ctr = ws.ctr;
-    volatile Counters* vc = ctr;
-    const unsigned tid = threadIdx.x;
     for (;;) {
-        if (tid == 0) sm.job = atomicAdd(queue, 1u);
+        if (threadIdx.x == 0) sm.job = atomicAdd(queue, 1u);
         __syncthreads();
         const uint32_t jid = sm.job;
         __syncthreads();
         if (jid >= njobs) break;
         const Job job = jobs[jid];
-        const ArenaDesc d = descs[job.graph];
-        const uint32_t n = d.n;
-        const uint64_t* off = arena_off + d.off_base;
-        const uint2* adj = arena_adj + d.adj_base;
-        const uint32_t* row = arena_row + d.adj_base;
-        cldiam_result res;
-        memset(&res, 0, sizeof res);
-        uint32_t status = kJobOk;
+        run_job(job, descs[job.graph], arena_off, arena_adj, arena_row, ws, sm, dyn, &outs[job.out]);
+    }
+}
 
-        for (uint32_t v = tid; v < n; v += BT) {
-            ws.center[v] = kNone;
-            ws.D[v] = 0;
-            ws.R[v] = 0;
-            ws.stamp[v] = 0;
-            ws.key[v] = kInfKey;
-        }
-        if (tid == 0) memset(ctr, 0, sizeof(Counters));
-        __syncthreads();
+// ---------------------------------------------------------------------------- serving
+// Host-mapped control block of the serving kernel.
+struct ServeCtl {
+    uint32_t tail;   // requests published by the host (store-release)
+    uint32_t stop;   // host asks the CTAs to leave
+    uint32_t idle;   // a CTA left after the idle limit with no request
+    uint32_t pad;
+};
 
-        uint64_t U = n, frozen_deg = 0, covered = 0;
-        uint32_t stage = 1, stepid = 0, delta = job.delta0, cur = 0;
-        const bool pull_ok = d.nnz < 0x80000000ull;
-        uint32_t nf = 0, E = 0;
-        for (;;) {
-            uint64_t thr = 0;
-            if (!stage_threshold(U, job.tau, job.L, &thr)) break;
-            if (stage > kMaxStages) {
-                status = kJobDiverged;
-                break;
-            }
-            if (tid == 0) {
-                ctr->selected = 0;
-                ctr->front = 0;
-            }
-            __syncthreads();
-            dev_select(n, ws.center, ws.key, job.seed, stage, thr, ctr, 0, 1);
-            __syncthreads();
-            {
-                const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
-                            sm.scratch, 0, 1);
-            }
-            __syncthreads();
-            covered = vc->selected;
-            res.centers_drawn += vc->selected;
-            nf = (uint32_t)(vc->front >> 32);
-            E = (uint32_t)vc->front;
-            __syncthreads();
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Continuous batching: every CTA takes the next published request as soon as
+// it finishes its previous one, so requests that arrive while others run join
+// immediately.  Waiting for work is bounded by idle_cycles; the host
+// relaunches the kernel when a request arrives after the CTAs left.
+__global__ void __launch_bounds__(BT, 1)
+    k_serve(const ArenaDesc* __restrict__ descs, const uint64_t* __restrict__ arena_off,
+            const uint2* __restrict__ arena_adj, const uint32_t* __restrict__ arena_row,
+            Workspace* __restrict__ wss, const Job* ring, ServeCtl* ctl, uint32_t* head, JobOut* outs,
+            uint32_t* done, long long idle_cycles) {
+    extern __shared__ __align__(16) uint32_t dyn[];
+    __shared__ BatchSmem sm;
+    __shared__ Job s_job;
+    const Workspace ws = wss[blockIdx.x];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t claimed = kNone;
+            const long long t0 = clock64();
             for (;;) {
-                uint32_t updated;
-                do {
-                    ++stepid;
-                    updated = 0;
-                    if (nf > 0) {
-                        if (tid == 0) {
-                            ctr->newly_covered = 0;
-                            ctr->front = 0;
-                            ctr->nnext = 0;
-                        }
-                        __syncthreads();
-                        dev_relax(ws.fv[cur], ws.fkey[cur], ws.fpre[cur], nf, E, off, adj, ws.center, ws.key, delta,
-                                  ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
-                        __syncthreads();
-                        const uint32_t nn = vc->nnext;
-                        dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fv[cur ^ 1], ws.fkey[cur ^ 1],
-                                     ws.fpre[cur ^ 1], ctr, sm.scratch, 0, 1);
-                        __syncthreads();
-                        updated = nn;
-                        covered += vc->newly_covered;
-                        res.edges_scanned += E;
-                        nf = (uint32_t)(vc->front >> 32);
-                        E = (uint32_t)vc->front;
-                        cur ^= 1;
-                        __syncthreads();
+                const uint32_t t = ld_acquire_sys(&ctl->tail);
+                const uint32_t h = atomicAdd(head, 0u);
+                if (h < t) {
+                    if (atomicCAS(head, h, h + 1) == h) {
+                        claimed = h;
+                        break;
                     }
-                    res.steps++;
-                    res.node_updates += updated;
-                } while (updated != 0 && 2 * covered < U);
-                if (2 * covered >= U) break;
-                bool growable = false;
-                if (delta < kDeltaMax && d.connected) {
-                    growable = covered > 0 || U < n;
-                } else if (delta < kDeltaMax && d.nnz) {
-                    if (tid == 0) ctr->growable = 0;
-                    __syncthreads();
-                    dev_growable(row, adj, d.nnz, ws.key, ctr, 0, 1);
-                    __syncthreads();
-                    growable = vc->growable != 0;
-                    __syncthreads();
+                    continue;
                 }
-                if (!growable) {
-                    res.guard_exits++;
+                if (ld_acquire_sys(&ctl->stop)) break;
+                if (clock64() - t0 > idle_cycles) {
+                    atomicExch(&ctl->idle, 1u);
                     break;
                 }
-                delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
-                res.doublings++;
-                if (tid == 0) ctr->front = 0;
-                __syncthreads();
-                {
-                    const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-                    dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
-                                sm.scratch, 0, 1);
-                }
-                __syncthreads();
-                nf = (uint32_t)(vc->front >> 32);
-                E = (uint32_t)vc->front;
-                __syncthreads();
+                __nanosleep(2000);
             }
-            if (tid == 0) {
-                ctr->frozen = 0;
-                ctr->frozen_deg = 0;
-            }
-            __syncthreads();
-            dev_finalize_d(n, ws.key, ws.center, ws.R, ws.D, ctr, 0, 1);
-            __syncthreads();
-            dev_finalize_freeze(n, ws.key, ws.center, ws.R, ws.D, off, ctr, 0, 1);
-            __syncthreads();
-            if (vc->overflow) status = kJobOverflow;
-            U -= vc->frozen;
-            frozen_deg += vc->frozen_deg;
-            res.stages++;
-            ++stage;
-            __syncthreads();
-            if (status != kJobOk) break;
-        }
-        if (status == kJobOk) {
-            dev_singletons(n, ws.center, ws.D, 0, 1);
-            __syncthreads();
-            res.delta_end = delta;
-            const uint32_t k = block_relabel(n, ws.center, ws.stamp, ws.cid, sm);  // stamp reused as rank
-            res.k = k;
-            const uint32_t rmax =
-                block_all_reduce([&] {
-                    uint32_t m = 0;
-                    for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
-                    return m;
-                }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
-            res.radius = rmax;
-            if (k > kDenseCap) {
-                status = kJobNeedsPlain;
-            } else {
-                // weighted quotient graph, deduplicated densely
-                uint32_t* M = ws.M;
-                for (uint32_t i = tid; i < k * k; i += BT) M[i] = (i / k == i % k) ? 0u : kNone;
-                __syncthreads();
-                bool ovf = false;
-                for (uint64_t i = tid; i < d.nnz; i += BT) {
-                    const uint32_t u = row[i];
-                    const uint2 e = adj[i];
-                    const uint32_t a = __ldcg(&ws.cid[u]), b = __ldcg(&ws.cid[e.x]);
-                    if (a != b) {
-                        uint64_t s = (uint64_t)__ldcg(&ws.D[u]) + e.y + __ldcg(&ws.D[e.x]);
-                        if (s >= 0xFFFFFFFFull) {
-                            ovf = true;
-                            s = 0xFFFFFFFEull;
-                        }
-                        atomicMin(&M[(size_t)a * k + b], (uint32_t)s);
-                    }
-                }
-                __syncthreads();
-                const unsigned long long qe = block_all_reduce(
-                    [&] {
-                        unsigned long long c = 0;
-                        for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
-                        return c;
-                    }(),
-                    [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
-                res.quotient_edges = qe;
-                bool ovf2 = false;
-                const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2);
-                const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
-                                                          [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
-                if (any_ovf) status = kJobOverflow;
-                res.phi_gc = phi;
-                res.phi_approx = (uint64_t)phi + 2ull * rmax;
+            sm.job = claimed;
+            if (claimed != kNone) {
+                const volatile Job* vj = ring + claimed;
+                s_job.tau = vj->tau;
+                s_job.L = vj->L;
+                s_job.seed = vj->seed;
+                s_job.graph = vj->graph;
+                s_job.delta0 = vj->delta0;
+                s_job.out = vj->out;
             }
         }
-        if (tid == 0) {
-            outs[job.out].r = res;
-            outs[job.out].status = status;
+        __syncthreads();
+        const uint32_t slot = sm.job;
+        if (slot == kNone) break;
+        const Job job = s_job;
+        __syncthreads();
+        run_job(job, descs[job.graph], arena_off, arena_adj, arena_row, ws, sm, dyn, &outs[job.out]);
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            st_release_sys(&done[job.out], 1u);
         }
         __syncthreads();
     }
@@ -567,6 +656,61 @@ cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out) {
 uint32_t arena_count(const cldiam_arena* a) { return (uint32_t)a->graphs.size(); }
 uint64_t arena_device_bytes(const cldiam_arena* a) { return arena_bytes(a); }
 
+// Per-CTA workspaces for graphs of up to nmax nodes, carved from one (cached) device buffer.
+static cldiam_status make_workspaces(uint32_t nmax, int ctas, cudaStream_t s, void** buf, size_t* buf_bytes,
+                                     std::vector<Workspace>* out) {
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t n8 = al((size_t)nmax * 8), n4 = al((size_t)nmax * 4), f8 = al((size_t)nmax * 16),
+                 f4 = al((size_t)nmax * 8), mm = al((size_t)kDenseCap * kDenseCap * 4),
+                 qo = al(((size_t)kDenseCap + 1) * 4), ctrb = al(sizeof(Counters));
+    const size_t slice = n8 + 2 * f8 + 6 * n4 + 4 * f4 + mm + qo + 2 * mm + ctrb;
+    const size_t need = slice * ctas;
+    if (need > *buf_bytes) {
+        dfree(*buf, s);
+        *buf = nullptr;
+        *buf_bytes = 0;
+        CLD_TRY(dmalloc(buf, need, s));
+        *buf_bytes = need;
+    }
+    out->assign(ctas, Workspace{});
+    for (int b = 0; b < ctas; ++b) {
+        char* p = static_cast<char*>(*buf) + (size_t)b * slice;
+        Workspace& w = (*out)[b];
+        w.key = reinterpret_cast<unsigned long long*>(p); p += n8;
+        w.fkey[0] = reinterpret_cast<unsigned long long*>(p); p += f8;
+        w.fkey[1] = reinterpret_cast<unsigned long long*>(p); p += f8;
+        w.center = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.D = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.R = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.stamp = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.next = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.cid = reinterpret_cast<uint32_t*>(p); p += n4;
+        w.fv[0] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fv[1] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fpre[0] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fpre[1] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.M = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.qoff = reinterpret_cast<uint32_t*>(p); p += qo;
+        w.qcol = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.qw = reinterpret_cast<uint32_t*>(p); p += mm;
+        w.ctr = reinterpret_cast<Counters*>(p);
+    }
+    return CLDIAM_OK;
+}
+
+static size_t batch_dyn_smem() { return std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * 8 * 4); }
+
+template <class Kern>
+static cldiam_status set_dyn_smem(Kern k, bool* done_flags) {
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !done_flags[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_dyn_smem()));
+        if (dev >= 0 && dev < 64) done_flags[dev] = true;
+    }
+    return CLDIAM_OK;
+}
+
 cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau, const uint64_t* seed, uint32_t count,
                         const cldiam_opts* o, cldiam_result* out, cldiam_status* status) {
     if (!a || (count && (!ids || !tau || !seed || !out))) return fail(CLDIAM_ERR_INVALID_ARG, "NULL argument");
@@ -598,43 +742,8 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         return a->graphs[x.graph].nnz + a->graphs[x.graph].n > a->graphs[y.graph].nnz + a->graphs[y.graph].n;
     });
     const int nsm = num_sms();
-    // per-CTA workspace
-    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t n8 = al((size_t)nmax * 8), n4 = al((size_t)nmax * 4), f8 = al((size_t)nmax * 16),
-                 f4 = al((size_t)nmax * 8), mm = al((size_t)kDenseCap * kDenseCap * 4),
-                 qo = al(((size_t)kDenseCap + 1) * 4), ctrb = al(sizeof(Counters));
-    const size_t slice = n8 + 2 * f8 + 6 * n4 + 4 * f4 + mm + qo + 2 * mm + ctrb;
-    const size_t need = slice * nsm;
-    if (need > a->ws_bytes) {
-        dfree(a->ws, s);
-        a->ws = nullptr;
-        a->ws_bytes = 0;
-        CLD_TRY(dmalloc(&a->ws, need, s));
-        a->ws_bytes = need;
-    }
-    std::vector<Workspace> wsh(nsm);
-    for (int b = 0; b < nsm; ++b) {
-        char* p = static_cast<char*>(a->ws) + (size_t)b * slice;
-        Workspace& w = wsh[b];
-        w.key = reinterpret_cast<unsigned long long*>(p); p += n8;
-        w.fkey[0] = reinterpret_cast<unsigned long long*>(p); p += f8;
-        w.fkey[1] = reinterpret_cast<unsigned long long*>(p); p += f8;
-        w.center = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.D = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.R = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.stamp = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.next = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.cid = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.fv[0] = reinterpret_cast<uint32_t*>(p); p += f4;
-        w.fv[1] = reinterpret_cast<uint32_t*>(p); p += f4;
-        w.fpre[0] = reinterpret_cast<uint32_t*>(p); p += f4;
-        w.fpre[1] = reinterpret_cast<uint32_t*>(p); p += f4;
-        w.M = reinterpret_cast<uint32_t*>(p); p += mm;
-        w.qoff = reinterpret_cast<uint32_t*>(p); p += qo;
-        w.qcol = reinterpret_cast<uint32_t*>(p); p += mm;
-        w.qw = reinterpret_cast<uint32_t*>(p); p += mm;
-        w.ctr = reinterpret_cast<Counters*>(p);
-    }
+    std::vector<Workspace> wsh;
+    CLD_TRY(make_workspaces(nmax, nsm, s, &a->ws, &a->ws_bytes, &wsh));
     DBuf<ArenaDesc> ddesc;
     DBuf<Job> djobs;
     DBuf<Workspace> dws;
@@ -650,14 +759,9 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     CLD_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), count * sizeof(Job), cudaMemcpyHostToDevice, s));
     CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
     CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
-    const size_t dyn = std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * 8 * 4);
+    const size_t dyn = batch_dyn_smem();
     static bool attr[64];
-    int dev = 0;
-    CLD_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !attr[dev]) {
-        CLD_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        if (dev >= 0 && dev < 64) attr[dev] = true;
-    }
+    CLD_TRY(set_dyn_smem(k_batch, attr));
     CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), count, a->off, a->adj, a->row, dws.get(),
                                                    queue.get(), douts.get()));
     CLD_LAUNCH_CHECK();
@@ -691,6 +795,355 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         if (st != CLDIAM_OK && first_err == CLDIAM_OK) first_err = st;
     }
     if (first_err != CLDIAM_OK) return fail(first_err, "one or more graphs of the batch failed (see status[])");
+    return CLDIAM_OK;
+}
+
+// ---------------------------------------------------------------------------- server
+namespace {
+inline void host_store_release(uint32_t* p, uint32_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+inline uint32_t host_load_acquire(const uint32_t* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+}  // namespace
+
+}  // namespace cld
+
+struct cldiam_server {
+    cldiam_arena* arena = nullptr;
+    int device = 0;
+    cudaStream_t kstream = nullptr, bstream = nullptr;
+    uint32_t ctas = 0, cap = 0, big_nodes = 0;
+    uint64_t budget = 0;
+    long long idle_cycles = 0;
+    // host-mapped (pinned) memory, shared with the serving kernel
+    cld::ServeCtl* ctl = nullptr;
+    cld::Job* ring = nullptr;
+    cld::JobOut* outs = nullptr;
+    uint32_t* done = nullptr;
+    // device memory
+    uint32_t* head = nullptr;
+    cld::Workspace* wss = nullptr;
+    cld::ArenaDesc* descs = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // host state
+    std::mutex mu;
+    uint32_t next_ticket = 0, next_ring = 0;
+    bool kernel_live = false;
+    std::vector<uint32_t> big_graph;
+    std::vector<double> big_tau;
+    std::vector<uint64_t> big_seed;
+    std::thread big;
+    std::mutex bmu;
+    std::condition_variable bcv;
+    std::deque<uint32_t> bq;
+    bool bstop = false;
+    cld::Pinned bhost;  // counter block of the big lane's one-graph runs
+};
+
+namespace cld {
+
+static cldiam_status server_launch(cldiam_server* sv) {
+    static bool attr[64];
+    CLD_TRY(set_dyn_smem(k_serve, attr));
+    sv->ctl->idle = 0;
+    CLD_K(K_MISC, sv->kstream,
+          k_serve<<<sv->ctas, BT, batch_dyn_smem(), sv->kstream>>>(sv->descs, sv->arena->off, sv->arena->adj,
+                                                                   sv->arena->row, sv->wss, sv->ring, sv->ctl,
+                                                                   sv->head, sv->outs, sv->done, sv->idle_cycles));
+    CLD_LAUNCH_CHECK();
+    sv->kernel_live = true;
+    return CLDIAM_OK;
+}
+
+// relaunch the serving kernel if its CTAs left after the idle limit (caller holds sv->mu)
+static cldiam_status server_ensure_live(cldiam_server* sv) {
+    if (sv->kernel_live) {
+        cudaError_t q = cudaStreamQuery(sv->kstream);
+        if (q == cudaErrorNotReady) return CLDIAM_OK;
+        if (q != cudaSuccess) return cuda_fail(q, "serving kernel", __FILE__, __LINE__);
+        sv->kernel_live = false;
+    }
+    return server_launch(sv);
+}
+
+static void big_lane(cldiam_server* sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        uint32_t t;
+        {
+            std::unique_lock<std::mutex> lk(sv->bmu);
+            sv->bcv.wait(lk, [&] { return sv->bstop || !sv->bq.empty(); });
+            if (sv->bq.empty()) return;
+            t = sv->bq.front();
+            sv->bq.pop_front();
+        }
+        cldiam_graph view;
+        arena_view(sv->arena, sv->big_graph[t], &view);
+        view.stream = sv->bstream;
+        view.host.h = sv->bhost.h;  // borrowed pinned block; released with the server
+        cldiam_result r{};
+        cldiam_status st = CLDIAM_OK;
+        // admission by device memory: the one-graph path needs ~100 B per node plus ~40 B per entry
+        const uint64_t need = (uint64_t)view.n * 100 + view.nnz * 40;
+        if (sv->budget && arena_bytes(sv->arena) + sv->ws_bytes + need > sv->budget) {
+            st = fail(CLDIAM_ERR_OOM, "request does not fit the server's device memory budget");
+        } else {
+            cldiam_clustering* c = nullptr;
+            cldiam_quotient* q = nullptr;
+            cldiam_opts o{};
+            st = cluster(&view, sv->big_tau[t], sv->big_seed[t], &o, &c);
+            if (st == CLDIAM_OK) st = quotient(c, &q);
+            if (st == CLDIAM_OK) st = cldiam_estimate(q, &r);
+            free_quotient(q);
+            free_clustering(c);
+        }
+        view.host.h = nullptr;
+        sv->outs[t].r = r;
+        sv->outs[t].status = st == CLDIAM_OK ? kJobOk
+                             : st == CLDIAM_ERR_OVERFLOW ? kJobOverflow
+                             : st == CLDIAM_ERR_DIVERGED ? kJobDiverged : kJobTimeout;
+        host_store_release(&sv->done[t], 1u);
+    }
+}
+
+cldiam_status server_free(cldiam_server* sv);
+
+cldiam_status server_create(cldiam_arena* a, const cldiam_server_opts* o, cldiam_server** out) {
+    if (!a || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL arena or out");
+    *out = nullptr;
+    cldiam_server_opts opts{};
+    if (o) opts = *o;
+    cldiam_server* sv = new cldiam_server();
+    sv->arena = a;
+    CLD_CUDA(cudaGetDevice(&sv->device));
+    const int nsm = num_sms();
+    sv->ctas = opts.ctas ? std::min<uint32_t>(opts.ctas, nsm) : (uint32_t)std::max(1, nsm - 24);
+    sv->cap = opts.capacity ? opts.capacity : (1u << 20);
+    sv->big_nodes = opts.big_nodes ? opts.big_nodes : (1u << 19);
+    sv->budget = opts.hbm_budget_bytes;
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, sv->device);
+    const double idle_s = opts.idle_seconds > 0 ? opts.idle_seconds : 10.0;
+    sv->idle_cycles = (long long)(idle_s * (khz > 0 ? khz : 2000000) * 1e3);
+    auto cleanup = [&](cldiam_status st) {
+        server_free(sv);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&sv->kstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->bstream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(CLDIAM_ERR_CUDA, "stream creation failed"));
+    void* p = nullptr;
+    const size_t host_bytes = sizeof(ServeCtl) + (size_t)sv->cap * (sizeof(Job) + sizeof(JobOut) + sizeof(uint32_t));
+    if (cudaHostAlloc(&p, host_bytes, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(CLDIAM_ERR_OOM, "pinned host memory for the request ring"));
+    }
+    memset(p, 0, host_bytes);
+    char* c = static_cast<char*>(p);
+    sv->ctl = reinterpret_cast<ServeCtl*>(c); c += sizeof(ServeCtl);
+    sv->ring = reinterpret_cast<Job*>(c); c += (size_t)sv->cap * sizeof(Job);
+    sv->outs = reinterpret_cast<JobOut*>(c); c += (size_t)sv->cap * sizeof(JobOut);
+    sv->done = reinterpret_cast<uint32_t*>(c);
+    cldiam_status st = sv->bhost.alloc(256);
+    if (st != CLDIAM_OK) return cleanup(st);
+    // device state: descriptors, head counter, workspaces for the graphs the kernel serves
+    uint32_t nmax = 1;
+    for (const ArenaDesc& d : a->graphs)
+        if (d.n <= sv->big_nodes) nmax = std::max(nmax, d.n);
+    std::vector<Workspace> wsh;
+    if ((st = make_workspaces(nmax, (int)sv->ctas, sv->kstream, &sv->ws, &sv->ws_bytes, &wsh)) != CLDIAM_OK)
+        return cleanup(st);
+    if (sv->budget && arena_bytes(a) + sv->ws_bytes > sv->budget)
+        return cleanup(fail(CLDIAM_ERR_OOM, "arena plus serving workspace exceed the budget"));
+    if ((st = dmalloc((void**)&sv->head, 4, sv->kstream)) != CLDIAM_OK ||
+        (st = dmalloc((void**)&sv->wss, wsh.size() * sizeof(Workspace), sv->kstream)) != CLDIAM_OK ||
+        (st = dmalloc((void**)&sv->descs, std::max<size_t>(1, a->graphs.size()) * sizeof(ArenaDesc), sv->kstream)) !=
+            CLDIAM_OK)
+        return cleanup(st);
+    cudaMemsetAsync(sv->head, 0, 4, sv->kstream);
+    cudaMemcpyAsync(sv->wss, wsh.data(), wsh.size() * sizeof(Workspace), cudaMemcpyHostToDevice, sv->kstream);
+    if (!a->graphs.empty())
+        cudaMemcpyAsync(sv->descs, a->graphs.data(), a->graphs.size() * sizeof(ArenaDesc), cudaMemcpyHostToDevice,
+                        sv->kstream);
+    if (cudaStreamSynchronize(sv->kstream) != cudaSuccess) return cleanup(fail(CLDIAM_ERR_CUDA, "server set-up"));
+    sv->big_graph.resize(sv->cap);
+    sv->big_tau.resize(sv->cap);
+    sv->big_seed.resize(sv->cap);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if ((st = server_launch(sv)) != CLDIAM_OK) return cleanup(st);
+    }
+    sv->big = std::thread(big_lane, sv);
+    *out = sv;
+    return CLDIAM_OK;
+}
+
+cldiam_status server_submit(cldiam_server* sv, uint32_t graph_id, double tau, uint64_t seed, uint64_t* ticket) {
+    if (!sv || !ticket) return fail(CLDIAM_ERR_INVALID_ARG, "NULL server or ticket");
+    if (graph_id >= sv->arena->graphs.size()) return fail(CLDIAM_ERR_INVALID_ARG, "graph id out of range");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be positive");
+    cldiam_graph view;
+    arena_view(sv->arena, graph_id, &view);
+    uint32_t d0 = 0;
+    CLD_TRY(delta0(&view, CLDIAM_DELTA0_AVG, 0, &d0));
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->next_ticket >= sv->cap) return fail(CLDIAM_ERR_BUSY, "server request capacity exhausted");
+    const uint32_t t = sv->next_ticket++;
+    if (view.n > sv->big_nodes) {
+        // large graph: the one-graph path on the big-lane stream, using the SMs the kernel leaves free
+        sv->big_graph[t] = graph_id;
+        sv->big_tau[t] = tau;
+        sv->big_seed[t] = seed;
+        {
+            std::lock_guard<std::mutex> bl(sv->bmu);
+            sv->bq.push_back(t);
+        }
+        sv->bcv.notify_one();
+    } else {
+        Job j{};
+        j.tau = tau;
+        j.L = std::log2((double)view.n);
+        j.seed = seed;
+        j.graph = graph_id;
+        j.delta0 = d0;
+        j.out = t;
+        sv->ring[sv->next_ring] = j;
+        host_store_release(&sv->ctl->tail, ++sv->next_ring);  // publish after the entry is written
+        CLD_TRY(server_ensure_live(sv));
+    }
+    *ticket = t;
+    return CLDIAM_OK;
+}
+
+cldiam_status server_poll(cldiam_server* sv, uint64_t ticket, cldiam_result* out) {
+    if (!sv || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL server or out");
+    if (ticket >= sv->next_ticket) return fail(CLDIAM_ERR_INVALID_ARG, "unknown ticket");
+    if (!host_load_acquire(&sv->done[ticket])) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        CLD_TRY(server_ensure_live(sv));
+        return CLDIAM_ERR_BUSY;
+    }
+    *out = sv->outs[ticket].r;
+    switch (sv->outs[ticket].status) {
+        case kJobOk: return CLDIAM_OK;
+        case kJobOverflow: return fail(CLDIAM_ERR_OVERFLOW, "distance overflow");
+        case kJobDiverged: return fail(CLDIAM_ERR_DIVERGED, "stage limit exceeded");
+        case kJobNeedsPlain: return fail(CLDIAM_ERR_UNSUPPORTED, "quotient above the serving kernel's capacity");
+        default: return fail(CLDIAM_ERR_TIMEOUT, "request failed");
+    }
+}
+
+cldiam_status server_free(cldiam_server* sv) {
+    if (!sv) return CLDIAM_OK;
+    if (sv->ctl) host_store_release(&sv->ctl->stop, 1u);
+    if (sv->big.joinable()) {
+        {
+            std::lock_guard<std::mutex> bl(sv->bmu);
+            sv->bstop = true;
+        }
+        sv->bcv.notify_all();
+        sv->big.join();
+    }
+    if (sv->kstream) cudaStreamSynchronize(sv->kstream);
+    if (sv->bstream) cudaStreamSynchronize(sv->bstream);
+    dfree(sv->head, sv->kstream);
+    dfree(sv->wss, sv->kstream);
+    dfree(sv->descs, sv->kstream);
+    dfree(sv->ws, sv->kstream);
+    if (sv->kstream) cudaStreamSynchronize(sv->kstream);
+    if (sv->ctl) cudaFreeHost(sv->ctl);
+    if (sv->kstream) cudaStreamDestroy(sv->kstream);
+    if (sv->bstream) cudaStreamDestroy(sv->bstream);
+    delete sv;
+    return CLDIAM_OK;
+}
+
+// Replay an arrival trace: request i is submitted at arrival[i] seconds after the start and its
+// latency is completion minus arrival.  plain != 0 serves the same trace one request at a time
+// in arrival order on the one-graph path instead (the one-query-per-call baseline).
+cldiam_status server_replay(cldiam_server* sv, const uint32_t* ids, const double* tau, const uint64_t* seed,
+                            const double* arrival, uint32_t count, int plain, cldiam_result* out, double* latency,
+                            double* elapsed) {
+    using clk = std::chrono::steady_clock;
+    if (!sv || (count && (!ids || !tau || !seed || !arrival || !out || !latency)))
+        return fail(CLDIAM_ERR_INVALID_ARG, "NULL argument");
+    const auto t0 = clk::now();
+    auto since = [&](clk::time_point t) { return std::chrono::duration<double>(t - t0).count(); };
+    auto wait_until = [&](double at) {
+        for (;;) {
+            const double now = since(clk::now());
+            if (now >= at) return;
+            if (at - now > 200e-6) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    };
+    cldiam_status first = CLDIAM_OK;
+    if (plain) {
+        cldiam_graph view;
+        for (uint32_t i = 0; i < count; ++i) {
+            wait_until(arrival[i]);
+            arena_view(sv->arena, ids[i], &view);
+            view.stream = sv->bstream;
+            view.host.h = sv->bhost.h;
+            cldiam_clustering* c = nullptr;
+            cldiam_quotient* q = nullptr;
+            cldiam_opts o{};
+            cldiam_status st = cluster(&view, tau[i], seed[i], &o, &c);
+            if (st == CLDIAM_OK) st = quotient(c, &q);
+            if (st == CLDIAM_OK) st = cldiam_estimate(q, &out[i]);
+            free_quotient(q);
+            free_clustering(c);
+            view.host.h = nullptr;
+            latency[i] = since(clk::now()) - arrival[i];
+            if (st != CLDIAM_OK && first == CLDIAM_OK) first = st;
+        }
+    } else {
+        std::vector<uint64_t> tickets(count, ~0ull);
+        std::atomic<uint32_t> submitted{0};
+        cldiam_status sub_err = CLDIAM_OK;
+        std::thread submitter([&] {
+            cudaSetDevice(sv->device);
+            for (uint32_t i = 0; i < count; ++i) {
+                wait_until(arrival[i]);
+                uint64_t t = 0;
+                cldiam_status st = server_submit(sv, ids[i], tau[i], seed[i], &t);
+                if (st != CLDIAM_OK) {
+                    sub_err = st;
+                    break;
+                }
+                tickets[i] = t;
+                submitted.store(i + 1, std::memory_order_release);
+            }
+        });
+        std::vector<uint32_t> pending;
+        uint32_t seen = 0, finished = 0;
+        while (finished < count) {
+            const uint32_t s = submitted.load(std::memory_order_acquire);
+            while (seen < s) pending.push_back(seen++);
+            if (sub_err != CLDIAM_OK && pending.empty()) break;
+            size_t keep = 0;
+            for (uint32_t i : pending) {
+                if (host_load_acquire(&sv->done[tickets[i]])) {
+                    latency[i] = since(clk::now()) - arrival[i];
+                    cldiam_status st = server_poll(sv, tickets[i], &out[i]);
+                    if (st != CLDIAM_OK && first == CLDIAM_OK) first = st;
+                    ++finished;
+                } else {
+                    pending[keep++] = i;
+                }
+            }
+            const bool progressed = keep < pending.size();
+            pending.resize(keep);
+            static thread_local auto last_check = clk::now();
+            if (!pending.empty() && !progressed && clk::now() - last_check > std::chrono::milliseconds(1)) {
+                last_check = clk::now();
+                std::lock_guard<std::mutex> lk(sv->mu);
+                CLD_TRY(server_ensure_live(sv));
+            }
+        }
+        submitter.join();
+        if (sub_err != CLDIAM_OK) return sub_err;
+    }
+    if (elapsed) *elapsed = since(clk::now());
+    if (first != CLDIAM_OK) return first;
     return CLDIAM_OK;
 }
 

@@ -79,6 +79,13 @@ cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out);
 cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau, const uint64_t* seed, uint32_t count,
                         const cldiam_opts* o, cldiam_result* out, cldiam_status* status);
 uint32_t arena_count(const cldiam_arena* a);
+cldiam_status server_create(cldiam_arena* a, const cldiam_server_opts* o, cldiam_server** out);
+cldiam_status server_submit(cldiam_server* sv, uint32_t graph_id, double tau, uint64_t seed, uint64_t* ticket);
+cldiam_status server_poll(cldiam_server* sv, uint64_t ticket, cldiam_result* out);
+cldiam_status server_free(cldiam_server* sv);
+cldiam_status server_replay(cldiam_server* sv, const uint32_t* ids, const double* tau, const uint64_t* seed,
+                            const double* arrival, uint32_t count, int plain, cldiam_result* out, double* latency,
+                            double* elapsed);
 uint64_t arena_device_bytes(const cldiam_arena* a);
 
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
