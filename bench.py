@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the many-graph leg")
     ap.add_argument("--batched-count", type=int, default=2000)
+    ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--plain-sample-every", type=int, default=10)
     ap.add_argument("--profile-pass", action="store_true",
                     help="run one pipeline pass on the workload and exit (for ncu captures)")
@@ -179,13 +181,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- many-graph leg
-def batched_leg(cd, stream, count, sample_every, reps=3):
-    """graphs/s of one persistent batch launch vs the plain one-graph-per-call loop (same jobs)."""
-    import torch
-
-    import inputs
-    from inputs.workloads import MIX_DESCRIBE, MIX_SEED, mixture, mixture_tau
-    arena = cd.arena_create(stream=stream)
+def build_mix_arena(cd, stream, count, budget=0):
+    """The many-graph workload packed into one arena: (arena, ids, taus, seeds, undirected edges, seconds)."""
+    from inputs.workloads import MIX_SEED, mixture, mixture_tau
+    arena = cd.arena_create(hbm_budget_bytes=budget, stream=stream)
     ids, taus, seeds, edges = [], [], [], 0
     t0 = time.perf_counter()
     for g, e in mixture(count, MIX_SEED):
@@ -197,7 +196,16 @@ def batched_leg(cd, stream, count, sample_every, reps=3):
         ids.append(gid)
         taus.append(mixture_tau(n))
         seeds.append(MIX_SEED * 1000 + g)
-    build_s = time.perf_counter() - t0
+    return arena, ids, taus, seeds, edges, time.perf_counter() - t0
+
+
+def batched_leg(cd, stream, mix, sample_every, reps=3):
+    """graphs/s of one persistent batch launch vs the plain one-graph-per-call loop (same jobs)."""
+    import torch
+
+    from inputs.workloads import MIX_DESCRIBE
+    arena, ids, taus, seeds, edges, build_s = mix
+    count = len(ids)
     res, st = arena.run(ids, taus, seeds)  # warm-up
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -222,7 +230,6 @@ def batched_leg(cd, stream, count, sample_every, reps=3):
         same &= all(r[f] == res[i][f] for f in r)
     torch.cuda.synchronize()
     t_plain = (time.perf_counter() - p0) / len(sample)
-    arena.free()
     gps = count / t_batch
     return {"workload": "mix2000", "describe": MIX_DESCRIBE, "graphs": count, "undirected_edges": edges,
             "graphs_per_s": round(gps, 1), "gteps": round(edges / t_batch / 1e9, 4),
@@ -231,6 +238,45 @@ def batched_leg(cd, stream, count, sample_every, reps=3):
             "plain_sample": f"every {sample_every}th job ({len(sample)} graphs), cldiam_cluster + "
                             "cldiam_quotient_build + cldiam_estimate per graph on the same GPU",
             "identical_to_plain_on_sample": bool(same), "arena_build_s": round(build_s, 1)}
+
+
+def served_leg(cd, mix, rates, count=20000, plain_count=1000, seed=5):
+    """Poisson query stream over the mixture + 1% R-MAT 20: continuous-batching server vs plain FIFO loop."""
+    import inputs
+    from inputs.workloads import WORKLOADS
+    arena, ids, taus, seeds, _, _ = mix
+    wl = WORKLOADS["rmat20"]
+    e = wl.make()
+    big = arena.add(e.src, e.dst, e.w, e.n)
+    g_ids = list(ids) + [big]
+    g_taus = list(taus) + [wl.tau]
+    srv = cd.server_create(arena, hbm_budget_bytes=150 * 10**9)
+    out = {"workload": "serve20k", "describe": (f"{count} queries, seed {seed}, exponential inter-arrival times; "
+                                                "each on a graph of the 2,000-graph mixture (p = 0.99) or on the "
+                                                "R-MAT 20 workload graph (p = 0.01); HBM budget 150 GB"),
+           "queries": count, "arena_device_bytes": arena.info()[1], "rates": []}
+    same = True
+    for rate in rates:
+        arr, gsel = inputs.queries(seed, count, float(rate), 0.01, len(ids))
+        q_ids = [g_ids[x] for x in gsel]
+        q_taus = [g_taus[x] for x in gsel]
+        q_seeds = [seed * 100000 + i for i in range(count)]
+        res, lat, el = srv.replay(q_ids, q_taus, q_seeds, arr)
+        k = plain_count
+        res_p, lat_p, el_p = srv.replay(q_ids[:k], q_taus[:k], q_seeds[:k], arr[:k], plain=True)
+        same &= res[:k] == res_p
+        out["rates"].append({
+            "rate_qps": rate, "qps": round(count / el, 1), "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3), "big_queries": int((gsel == len(ids)).sum()),
+            "plain_qps": round(k / el_p, 1), "plain_p50_ms": round(1e3 * float(np.percentile(lat_p, 50)), 3),
+            "plain_p99_ms": round(1e3 * float(np.percentile(lat_p, 99)), 3)})
+    srv.free()
+    out["plain"] = (f"the first {plain_count} queries of each trace served one at a time in arrival order "
+                    "(cldiam_cluster + cldiam_quotient_build + cldiam_estimate per query) on the same GPU")
+    out["identical_to_plain"] = bool(same)
+    best = max(out["rates"], key=lambda r: r["qps"])
+    out["speedup_qps_vs_plain"] = round(best["qps"] / max(r["plain_qps"] for r in out["rates"]), 2)
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU leg
@@ -402,7 +448,11 @@ def run_gpu(args):
                           "upper_bound": 2 * ecc, "rounds": rounds},
     }
     if not args.no_batched:
-        line["batched"] = batched_leg(cd, stream, args.batched_count, args.plain_sample_every)
+        mix = build_mix_arena(cd, stream, args.batched_count, budget=150 * 10**9)
+        line["batched"] = batched_leg(cd, stream, mix, args.plain_sample_every)
+        if not args.no_served:
+            line["served"] = served_leg(cd, mix, [int(x) for x in args.serve_rates.split(",")])
+        mix[0].free()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if dist:
