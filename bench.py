@@ -386,7 +386,10 @@ def run_gpu(args):
         tt = json.load(open(tpath))
         ent = tt.get(args.workload, {}).get(dominant)
         if ent:
-            traffic = ent.get("dram_bytes_per_launch")
+            src = os.path.join(ROOT, ent.get("source_file", ""))
+            same_kernel = os.path.isfile(src) and \
+                hashlib.sha256(open(src, "rb").read()).hexdigest() == ent.get("source_sha256")
+            traffic = ent.get("dram_bytes_per_launch") if same_kernel else None
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1) if achieved else None,
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                 "traffic": traffic, "launches": dk["launches"],
