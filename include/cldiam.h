@@ -78,8 +78,14 @@ typedef struct {
     int32_t contract_mode; /* 0: contracted clusters relax from distance 0 (Procedure Contract) */
     uint32_t step_cap;     /* must be 0 (no cap on growing steps per PartialGrowth)         */
     uint32_t max_fw_k;     /* largest dense quotient solved by Floyd-Warshall; 0 = 8192     */
-    uint32_t reserved[3];  /* must be 0                                                     */
+    uint32_t quotient_mode; /* CLDIAM_QUOTIENT_*: how cldiam_quotient_build deduplicates     */
+    uint32_t reserved[2];  /* must be 0                                                     */
 } cldiam_opts;
+
+/* cldiam_opts.quotient_mode (same result either way) */
+#define CLDIAM_QUOTIENT_AUTO 0  /* dense while k <= 4096, else radix sort (default) */
+#define CLDIAM_QUOTIENT_SORT 1  /* radix sort of (cid_u, cid_v) keys + segmented min */
+#define CLDIAM_QUOTIENT_DENSE 2 /* atomicMin into a k x k matrix (k <= 65535)        */
 
 /* Result of the whole method plus the paper-style counters (Table 2: rounds and work). */
 typedef struct {
@@ -154,7 +160,9 @@ void cldiam_clustering_free(cldiam_clustering* c);
 /*
  * Weighted quotient graph G_C (Section 4): node i = cluster i; for every edge
  * (u,v) with different clusters an edge of weight w(u,v) + D_u + D_v, minimum
- * per pair, stored as a symmetric CSR sorted by (row, col).
+ * per pair, stored as a symmetric CSR sorted by (row, col).  Pairs are
+ * deduplicated by a radix sort of (cid_u, cid_v) keys with a segmented min, or
+ * in a dense k x k matrix (opts.quotient_mode of the clustering).
  * Errors: OVERFLOW (a weight >= 2^32 - 1), OOM, CUDA.
  */
 cldiam_status cldiam_quotient_build(const cldiam_clustering* c, cldiam_quotient** out);

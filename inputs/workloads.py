@@ -27,9 +27,9 @@ WORKLOADS = {
     "rmat20": Workload("rmat20", "R-MAT scale 20, edge factor 16, (.57,.19,.19,.05), w in [1,2^20], seed 2, LCC",
                        lambda: rmat(20, 16, 1 << 20, 2), tau=4.65, seed=2, target_k=1024),
     "roadmesh4096": Workload("roadmesh4096", "4096x4096 mesh, 10% edges deleted, 0.1% chords, w in [1,1000], seed 3, LCC",
-                             lambda: road_mesh(4096, 1000, 3), tau=8.0, seed=3, target_k=4096),
+                             lambda: road_mesh(4096, 1000, 3), tau=5.4, seed=3, target_k=4096),
     "rmat24": Workload("rmat24", "R-MAT scale 24, edge factor 16, w in [1,1000], seed 3, LCC",
-                       lambda: rmat(24, 16, 1000, 3), tau=16.0, seed=3, target_k=4096),
+                       lambda: rmat(24, 16, 1000, 3), tau=21.0, seed=3, target_k=4096),
 }
 
 

@@ -27,6 +27,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "OVERFLOW", -4: "TIMEOUT", 
           -7: "CANCELLED", -8: "DIVERGED", -9: "UNSUPPORTED"}
 CSR_LCC = 1
 DELTA0_AVG, DELTA0_MIN, DELTA0_EXPLICIT = 0, 1, 2
+QUOTIENT_AUTO, QUOTIENT_SORT, QUOTIENT_DENSE = 0, 1, 2
 
 
 class CldiamError(RuntimeError):
@@ -37,7 +38,8 @@ class CldiamError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("delta0_mode", ctypes.c_int32), ("delta0", ctypes.c_uint32), ("contract_mode", ctypes.c_int32),
-                ("step_cap", ctypes.c_uint32), ("max_fw_k", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("step_cap", ctypes.c_uint32), ("max_fw_k", ctypes.c_uint32), ("quotient_mode", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class Result(ctypes.Structure):
@@ -363,17 +365,19 @@ def build_csr(src, dst, w, n: int, lcc: bool = True, stream=None) -> Graph:
     return Graph(h.value)
 
 
-def make_opts(delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0) -> Opts:
+def make_opts(delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0, quotient_mode=QUOTIENT_AUTO) -> Opts:
     o = Opts()
     o.delta0_mode = delta0_mode
     o.delta0 = delta0
     o.max_fw_k = max_fw_k
+    o.quotient_mode = quotient_mode
     return o
 
 
-def cluster(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0) -> Clustering:
+def cluster(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0,
+            quotient_mode=QUOTIENT_AUTO) -> Clustering:
     """cldiam_cluster: CLUSTER(G, tau) of Algorithm 1."""
-    o = make_opts(delta0_mode, delta0, max_fw_k)
+    o = make_opts(delta0_mode, delta0, max_fw_k, quotient_mode)
     h = ctypes.c_void_p()
     _check(load().cldiam_cluster(g.handle, float(tau), seed, ctypes.byref(o), ctypes.byref(h)), "cldiam_cluster")
     return Clustering(h.value, g)

@@ -717,7 +717,7 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     if (count == 0) return CLDIAM_OK;
     cldiam_opts opts{};
     if (o) opts = *o;
-    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1] || opts.reserved[2])
+    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1])
         return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
     const cudaStream_t s = a->stream;
     std::vector<Job> jobs(count);

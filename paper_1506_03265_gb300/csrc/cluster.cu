@@ -106,8 +106,9 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     if (!(tau > 0.0) || !std::isfinite(tau)) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be a positive number");
     cldiam_opts opts{};
     if (o) opts = *o;
-    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1] || opts.reserved[2])
+    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1])
         return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
+    if (opts.quotient_mode > CLDIAM_QUOTIENT_DENSE) return fail(CLDIAM_ERR_INVALID_ARG, "unknown quotient_mode");
     uint32_t delta = 0;
     CLD_TRY(delta0(g, opts.delta0_mode, opts.delta0, &delta));
 
@@ -117,6 +118,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     cldiam_clustering* cl = owner.c;
     cl->g = g;
     cl->max_fw_k = opts.max_fw_k ? opts.max_fw_k : 8192u;
+    cl->quotient_mode = opts.quotient_mode;
 
     // a frontier lists each node at most twice (push + pull entry)
     const size_t fcap = 2 * (size_t)n;

@@ -28,6 +28,7 @@ struct cldiam_clustering {
     uint32_t* cid = nullptr;     // [n] cluster id (rank of the center id)
     uint32_t k = 0;
     uint32_t max_fw_k = 8192;
+    uint32_t quotient_mode = 0;  // CLDIAM_QUOTIENT_*
     cldiam_result stats{};
 };
 

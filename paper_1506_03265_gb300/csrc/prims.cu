@@ -590,13 +590,25 @@ __global__ void __launch_bounds__(UQ_THREADS)
     const uint32_t tbase = s_prefix + s_woff[w];
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
         const bool valid = key[i] < sentinel;
         const uint32_t v = warp_seg_min(key[i], valid, val[i]);
         const bool tail = warp_run_tail(key[i], valid);
+        // a run that starts and ends inside these 32 items is written by its last lane alone: plain
+        // store; a run piece that may continue in another warp or tile is folded in with atomicMin
+        const K up = __shfl_up_sync(0xffffffffu, key[i], 1);
+        const unsigned starts = __ballot_sync(0xffffffffu, l == 0 || up != key[i]);
+        const unsigned seg0 = 31u - __clz(starts & (0xffffffffu >> (31u - l)));
+        const bool whole_head = (__shfl_sync(0xffffffffu, head_bits, seg0) >> i) & 1u;
+        K after = __shfl_down_sync(0xffffffffu, key[i], 1);
+        if (l == 31) after = (idx + 1 < cnt) ? keys[idx + 1] : sentinel;
         if (!valid) continue;
         const uint32_t f = (head_bits >> i) & 1u;
         const uint32_t r = tbase + ex[i] + f - 1u;
-        if (tail) atomicMin(&w_out[(size_t)r * cs], v);
+        if (tail) {
+            if (whole_head && after != key[i]) w_out[(size_t)r * cs] = v;
+            else atomicMin(&w_out[(size_t)r * cs], v);
+        }
         if (f) {
             const uint64_t q = (uint64_t)key[i] / div;
             if (row_out) row_out[r] = (uint32_t)q;

@@ -6,13 +6,17 @@
 // sort on the 2 log2 k significant key bits groups equal pairs, whose run
 // heads become the quotient entries and an atomicMin over each run keeps the
 // minimum.  Because the CSR is symmetric the result is symmetric, sorted by
-// (row, col).
+// (row, col).  While k is small enough for a dense k x k matrix to stay in
+// L2, the pairs are instead folded into that matrix with atomicMin and read
+// out row by row, which gives the same sorted CSR.
 #include "internal.cuh"
 #include "prof.cuh"
 
 namespace cld {
 
 namespace {
+
+constexpr uint32_t kDenseQuotientK = 4096;  // k x k uint32 = 64 MB, within the 126 MB L2
 
 template <class K>
 __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
@@ -46,6 +50,109 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
             vals[slot] = wq;
         }
     }
+}
+
+// Dense alternative for small k: fold every inter-cluster edge into M[a*k + b] with atomicMin
+// (the k x k matrix stays in L2), then read the rows out in column order.
+__global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
+                               const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D, uint32_t k,
+                               uint32_t* __restrict__ M, uint32_t* __restrict__ overflow) {
+    bool ovf = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = row[i];
+        const uint2 e = adj[i];
+        const uint32_t a = cid[u], b = cid[e.x];
+        if (a == b) continue;
+        uint64_t s = (uint64_t)D[u] + e.y + D[e.x];
+        if (s >= 0xFFFFFFFFull) {
+            ovf = true;
+            s = 0xFFFFFFFEull;
+        }
+        uint32_t* m = &M[(size_t)a * k + b];
+        if ((uint32_t)s < __ldcg(m)) atomicMin(m, (uint32_t)s);
+    }
+    if (__any_sync(0xffffffffu, ovf) && lane_id() == 0) atomicExch(overflow, 1u);
+}
+
+// row a's entry count (warp per row)
+__global__ void k_q_dense_count(const uint32_t* __restrict__ M, uint32_t k, uint32_t* __restrict__ deg) {
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < k; a += warps) {
+        uint32_t c = 0;
+        for (uint32_t b0 = 0; b0 < k; b0 += 32) {
+            const uint32_t b = b0 + lane_id();
+            c += __popc(__ballot_sync(0xffffffffu, b < k && M[(size_t)a * k + b] != 0xFFFFFFFFu));
+        }
+        if (lane_id() == 0) deg[a] = c;
+    }
+}
+
+__global__ void k_q_dense_fill(const uint32_t* __restrict__ M, uint32_t k, const uint32_t* __restrict__ start,
+                               uint32_t* __restrict__ col, uint32_t* __restrict__ w) {
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < k; a += warps) {
+        uint32_t pos = start[a];
+        for (uint32_t b0 = 0; b0 < k; b0 += 32) {
+            const uint32_t b = b0 + lane_id();
+            const uint32_t x = b < k ? M[(size_t)a * k + b] : 0xFFFFFFFFu;
+            const unsigned bal = __ballot_sync(0xffffffffu, x != 0xFFFFFFFFu);
+            if (x != 0xFFFFFFFFu) {
+                const uint32_t at = pos + (uint32_t)__popc(bal & lanemask_lt());
+                col[at] = b;
+                w[at] = x;
+            }
+            pos += (uint32_t)__popc(bal);
+        }
+    }
+}
+
+__global__ void k_q_widen(const uint32_t* __restrict__ start, uint32_t k, uint32_t total, uint64_t* __restrict__ off) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= k; i += gridDim.x * blockDim.x)
+        off[i] = (i == k) ? (uint64_t)total : (uint64_t)start[i];
+}
+
+cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* q) {
+    const cldiam_graph* g = c->g;
+    const cudaStream_t s = g->stream;
+    const uint32_t k = c->k;
+    uint32_t* hh = reinterpret_cast<uint32_t*>(static_cast<char*>(const_cast<cldiam_graph*>(g)->host.h) + 160);
+    DBuf<uint32_t> M, scal, deg, start;
+    CLD_TRY(M.alloc((size_t)k * k, s));
+    CLD_TRY(scal.alloc(2, s));
+    CLD_TRY(deg.alloc((size_t)k + 1, s));
+    CLD_TRY(start.alloc((size_t)k + 1, s));
+    CLD_CUDA(cudaMemsetAsync(M.get(), 0xFF, (size_t)k * k * 4, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8, s));
+    if (g->nnz) {
+        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, c->cid, c->D,
+                                                                                k, M.get(), scal.get()));
+        CLD_LAUNCH_CHECK();
+    }
+    CLD_K(K_QUOTIENT, s, k_q_dense_count<<<grid_for((size_t)k * 32, 256), 256, 0, s>>>(M.get(), k, deg.get()));
+    CLD_LAUNCH_CHECK();
+    CLD_TRY(scan_exclusive_u32(deg.get(), start.get(), k, scal.get() + 1, s));
+    CLD_CUDA(cudaMemcpyAsync(hh, scal.get(), 8, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (hh[0]) return fail(CLDIAM_ERR_OVERFLOW, "a quotient edge weight reached 2^32 - 1");
+    const uint32_t nq = hh[1];
+    DBuf<uint32_t> col, w;
+    DBuf<uint64_t> off;
+    CLD_TRY(col.alloc(nq ? nq : 1, s));
+    CLD_TRY(w.alloc(nq ? nq : 1, s));
+    CLD_TRY(off.alloc((size_t)k + 1, s));
+    CLD_K(K_QUOTIENT, s, k_q_dense_fill<<<grid_for((size_t)k * 32, 256), 256, 0, s>>>(M.get(), k, start.get(), col.get(),
+                                                                                    w.get()));
+    CLD_K(K_QUOTIENT, s, k_q_widen<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(start.get(), k, nq, off.get()));
+    CLD_LAUNCH_CHECK();
+    // algorithmic bytes: each CSR entry's row, (col, w) and two cluster ids and two D values
+    prof_add_bytes(K_QUOTIENT, (double)g->nnz * 28.0 + (double)k * k * 8.0);
+    CLD_CUDA(cudaStreamSynchronize(s));
+    q->k = k;
+    q->nnz = nq;
+    q->off = off.detach();
+    q->col = col.detach();
+    q->w = w.detach();
+    return CLDIAM_OK;
 }
 
 template <class K>
@@ -129,7 +236,15 @@ cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out) {
     q->c = c;
     q->stream = c->g->stream;
     q->max_fw_k = c->max_fw_k;
-    cldiam_status st = ((uint64_t)c->k * c->k <= 0xFFFFFFFFull) ? build_quotient<uint32_t>(c, q)
+    // dense deduplication while the k x k matrix fits in L2 (auto) or when asked; radix sort otherwise
+    const bool dense = c->quotient_mode == CLDIAM_QUOTIENT_DENSE ||
+                       (c->quotient_mode == CLDIAM_QUOTIENT_AUTO && c->k <= kDenseQuotientK);
+    if (dense && c->k > 65535u) {
+        free_quotient(q);
+        return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient deduplication needs k <= 65535");
+    }
+    cldiam_status st = dense ? build_quotient_dense(c, q)
+                       : ((uint64_t)c->k * c->k <= 0xFFFFFFFFull) ? build_quotient<uint32_t>(c, q)
                                                                   : build_quotient<uint64_t>(c, q);
     if (st != CLDIAM_OK) {
         free_quotient(q);

@@ -43,6 +43,7 @@ def check_csr(cd, n, src, dst, w, lcc):
 
 
 def check_cluster(cd, g, og, tau, seed, mode=0):
+    mode_d0 = mode
     c = cd.cluster(g, tau, seed, delta0_mode=mode)
     d0 = oracle.delta0(og, mode)
     assert g.delta0(mode) == d0
@@ -61,6 +62,11 @@ def check_cluster(cd, g, og, tau, seed, mode=0):
     assert np.array_equal(qoff, oq.off)
     assert np.array_equal(qcol, oq.col)
     assert np.array_equal(qw.astype(np.uint64), oq.w)
+    # both deduplication methods give the same quotient CSR
+    for mode in (cd.QUOTIENT_SORT, cd.QUOTIENT_DENSE):
+        qm = cd.quotient_build(cd.cluster(g, tau, seed, delta0_mode=mode_d0, quotient_mode=mode))
+        moff, mcol, mw = qm.copy()
+        assert np.array_equal(moff, qoff) and np.array_equal(mcol, qcol) and np.array_equal(mw, qw), mode
     r = cd.estimate(q)
     ores = oracle.estimate(oq, ocl)
     assert (r["k"], r["phi_gc"], r["radius"], r["phi_approx"]) == (ores.k, ores.phi_gc, ores.radius, ores.phi_approx)
