@@ -181,13 +181,30 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- many-graph leg
-def build_mix_arena(cd, stream, count, budget=0):
-    """The many-graph workload packed into one arena: (arena, ids, taus, seeds, undirected edges, seconds)."""
-    from inputs.workloads import MIX_SEED, mixture, mixture_tau
+def mix_shard(count, rank, world):
+    """Graph indices of this rank: largest-first bin packing on the generator's edge counts."""
+    import inputs
+    from inputs.workloads import MIX_SEED
+    from paper_1506_03265_gb300.shard import lpt_partition
+    if world == 1:
+        return list(range(count))
+    sizes = []
+    for g in range(count):
+        kind, scale, side, _ = inputs.mix_params(MIX_SEED, g)
+        sizes.append(8 * (1 << scale) if kind == 0 else 2 * side * (side - 1))
+    return lpt_partition(sizes, world)[rank]
+
+
+def build_mix_arena(cd, stream, count, budget=0, rank=0, world=1):
+    """This rank's share of the many-graph workload packed into one arena:
+    (arena, ids, taus, seeds, undirected edges, seconds)."""
+    import inputs
+    from inputs.workloads import MIX_SEED, mixture_tau
     arena = cd.arena_create(hbm_budget_bytes=budget, stream=stream)
     ids, taus, seeds, edges = [], [], [], 0
     t0 = time.perf_counter()
-    for g, e in mixture(count, MIX_SEED):
+    for g in mix_shard(count, rank, world):
+        e = inputs.mix_graph(MIX_SEED, g, 1000)
         gid = arena.add(e.src, e.dst, e.w, e.n)
         view = arena.graph(gid)
         n = view.n
@@ -199,11 +216,13 @@ def build_mix_arena(cd, stream, count, budget=0):
     return arena, ids, taus, seeds, edges, time.perf_counter() - t0
 
 
-def batched_leg(cd, stream, mix, sample_every, reps=3):
-    """graphs/s of one persistent batch launch vs the plain one-graph-per-call loop (same jobs)."""
+def batched_leg(cd, stream, mix, sample_every, reps=3, dist=None, total_count=None):
+    """graphs/s of one persistent batch launch vs the plain one-graph-per-call loop (same jobs).
+    With several ranks each runs its share; the batch time is the max over ranks."""
     import torch
 
     from inputs.workloads import MIX_DESCRIBE
+    from paper_1506_03265_gb300.shard import max_over_ranks, sum_over_ranks
     arena, ids, taus, seeds, edges, build_s = mix
     count = len(ids)
     res, st = arena.run(ids, taus, seeds)  # warm-up
@@ -230,8 +249,14 @@ def batched_leg(cd, stream, mix, sample_every, reps=3):
         same &= all(r[f] == res[i][f] for f in r)
     torch.cuda.synchronize()
     t_plain = (time.perf_counter() - p0) / len(sample)
+    if dist is not None and dist.is_initialized():
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t_batch = max_over_ranks(t_batch, dist, dev)
+        edges = int(sum_over_ranks(edges, dist, dev))
+        count = int(sum_over_ranks(count, dist, dev))
     gps = count / t_batch
     return {"workload": "mix2000", "describe": MIX_DESCRIBE, "graphs": count, "undirected_edges": edges,
+            "scaling": "strong (the 2,000 graphs are split across ranks by size)",
             "graphs_per_s": round(gps, 1), "gteps": round(edges / t_batch / 1e9, 4),
             "ms_per_batch": round(t_batch * 1e3, 2), "kernel_launches_per_batch": launches,
             "plain_graphs_per_s": round(1.0 / t_plain, 1), "speedup_vs_plain": round(gps * t_plain, 2),
@@ -366,9 +391,8 @@ def run_gpu(args):
     prof = cd.profile_get()
     launches = sum(v["launches"] for v in prof.values())
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_1506_03265_gb300.shard import max_over_ranks
+        ms = max_over_ranks(ms, dist, torch.device("cuda", local))
     value = ws * m_lcc / (ms * 1e-3) / 1e9
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -451,9 +475,10 @@ def run_gpu(args):
                           "upper_bound": 2 * ecc, "rounds": rounds},
     }
     if not args.no_batched:
-        mix = build_mix_arena(cd, stream, args.batched_count, budget=150 * 10**9)
-        line["batched"] = batched_leg(cd, stream, mix, args.plain_sample_every)
-        if not args.no_served:
+        mix = build_mix_arena(cd, stream, args.batched_count, budget=150 * 10**9, rank=rank, world=ws)
+        line["batched"] = batched_leg(cd, stream, mix, args.plain_sample_every, dist=dist)
+        if not args.no_served and ws == 1:
+            # the serving leg runs on a single GPU: its query stream is one queue
             line["served"] = served_leg(cd, mix, [int(x) for x in args.serve_rates.split(",")])
         mix[0].free()
     if rank == 0 and not args.no_cpu_baseline:
