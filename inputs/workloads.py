@@ -28,6 +28,8 @@ WORKLOADS = {
                        lambda: rmat(20, 16, 1 << 20, 2), tau=4.65, seed=2, target_k=1024),
     "roadmesh4096": Workload("roadmesh4096", "4096x4096 mesh, 10% edges deleted, 0.1% chords, w in [1,1000], seed 3, LCC",
                              lambda: road_mesh(4096, 1000, 3), tau=5.4, seed=3, target_k=4096),
+    "rmat22": Workload("rmat22", "R-MAT scale 22, edge factor 16, w in [1,1000], seed 3, LCC (profiling size)",
+                       lambda: rmat(22, 16, 1000, 3), tau=10.5, seed=3, target_k=2048),
     "rmat24": Workload("rmat24", "R-MAT scale 24, edge factor 16, w in [1,1000], seed 3, LCC",
                        lambda: rmat(24, 16, 1000, 3), tau=21.0, seed=3, target_k=4096),
 }

@@ -60,7 +60,7 @@ struct Workspace {  // one slice per CTA
     uint32_t* D;
     uint32_t* R;
     uint32_t* stamp;
-    uint32_t* fv[2];
+    uint32_t* fbase[2];
     uint32_t* fpre[2];
     uint32_t* next;
     uint32_t* cid;
@@ -285,8 +285,8 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
         __syncthreads();
         {
             const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-            dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
-                        sm.scratch, 0, 1);
+            dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr,
+                        ctr, sm.scratch, 0, 1);
         }
         __syncthreads();
         covered = vc->selected;
@@ -306,12 +306,12 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                         ctr->nnext = 0;
                     }
                     __syncthreads();
-                    dev_relax(ws.fv[cur], ws.fkey[cur], ws.fpre[cur], nf, E, off, adj, ws.center, ws.key, delta,
-                              ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
+                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr, nf, E, adj, ws.center, ws.key,
+                                 delta, ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
                     __syncthreads();
                     const uint32_t nn = vc->nnext;
-                    dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fv[cur ^ 1], ws.fkey[cur ^ 1],
-                                 ws.fpre[cur ^ 1], ctr, sm.scratch, 0, 1);
+                    dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fbase[cur ^ 1], ws.fkey[cur ^ 1],
+                                 ws.fpre[cur ^ 1], nullptr, ctr, sm.scratch, 0, 1);
                     __syncthreads();
                     updated = nn;
                     covered += vc->newly_covered;
@@ -346,8 +346,8 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
             __syncthreads();
             {
                 const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fv[cur], ws.fkey[cur], ws.fpre[cur], ctr,
-                            sm.scratch, 0, 1);
+                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr,
+                            ctr, sm.scratch, 0, 1);
             }
             __syncthreads();
             nf = (uint32_t)(vc->front >> 32);
@@ -685,8 +685,8 @@ static cldiam_status make_workspaces(uint32_t nmax, int ctas, cudaStream_t s, vo
         w.stamp = reinterpret_cast<uint32_t*>(p); p += n4;
         w.next = reinterpret_cast<uint32_t*>(p); p += n4;
         w.cid = reinterpret_cast<uint32_t*>(p); p += n4;
-        w.fv[0] = reinterpret_cast<uint32_t*>(p); p += f4;
-        w.fv[1] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fbase[0] = reinterpret_cast<uint32_t*>(p); p += f4;
+        w.fbase[1] = reinterpret_cast<uint32_t*>(p); p += f4;
         w.fpre[0] = reinterpret_cast<uint32_t*>(p); p += f4;
         w.fpre[1] = reinterpret_cast<uint32_t*>(p); p += f4;
         w.M = reinterpret_cast<uint32_t*>(p); p += mm;

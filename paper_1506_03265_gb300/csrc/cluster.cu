@@ -18,29 +18,32 @@ __global__ void k_select(uint32_t n, const uint32_t* __restrict__ center, unsign
 }
 
 __global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
-                          const uint64_t* __restrict__ off, uint32_t delta, bool pull, uint32_t* __restrict__ fv,
-                          unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
+                          const uint64_t* __restrict__ off, uint32_t delta, bool pull, uint32_t* __restrict__ fbase,
+                          unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre,
+                          uint32_t* __restrict__ cfirst, Counters* ctr) {
     __shared__ unsigned long long scratch[33];
-    dev_rebuild(n, key, center, off, delta, pull, fv, fkey, fpre, ctr, scratch, blockIdx.x, gridDim.x);
+    dev_rebuild(n, key, center, off, delta, pull, fbase, fkey, fpre, cfirst, ctr, scratch, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fv, const unsigned long long* __restrict__ fkey,
-                                              const uint32_t* __restrict__ fpre, uint32_t nf, uint32_t E,
-                                              const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
+__global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fbase,
+                                              const unsigned long long* __restrict__ fkey,
+                                              const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
+                                              uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
                                               const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
                                               uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
                                               uint32_t* __restrict__ next, Counters* ctr) {
     __shared__ RelaxSmem sm;
-    dev_relax(fv, fkey, fpre, nf, E, off, adj, center, key, delta, stamp, stepid, next, ctr, sm, blockIdx.x,
-              gridDim.x);
+    dev_relax<RU>(fbase, fkey, fpre, cfirst, nf, E, adj, center, key, delta, stamp, stepid, next, ctr, sm,
+                  blockIdx.x, gridDim.x);
 }
 
 __global__ void k_snapshot(const uint32_t* __restrict__ next, const unsigned long long* __restrict__ key,
-                           const uint64_t* __restrict__ off, uint32_t delta, uint32_t* __restrict__ fv,
-                           unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre, Counters* ctr) {
+                           const uint64_t* __restrict__ off, uint32_t delta, uint32_t* __restrict__ fbase,
+                           unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre,
+                           uint32_t* __restrict__ cfirst, Counters* ctr) {
     __shared__ unsigned long long scratch[33];
     const uint32_t nn = __ldcg(&ctr->nnext);
-    dev_snapshot(next, nn, key, off, delta, fv, fkey, fpre, ctr, scratch, blockIdx.x, gridDim.x);
+    dev_snapshot(next, nn, key, off, delta, fbase, fkey, fpre, cfirst, ctr, scratch, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_growable(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
@@ -124,7 +127,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     const size_t fcap = 2 * (size_t)n;
     DBuf<uint32_t> center, D, cid;
     DBuf<unsigned long long> key, fkeyA, fkeyB;
-    DBuf<uint32_t> R, stamp, fvA, fvB, fpA, fpB, next;
+    DBuf<uint32_t> R, stamp, fvA, fvB, fpA, fpB, cfA, cfB, next;
     DBuf<Counters> ctr;
     CLD_TRY(center.alloc(n, s));
     CLD_TRY(D.alloc(n, s));
@@ -138,6 +141,10 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     CLD_TRY(fpB.alloc(fcap, s));
     CLD_TRY(fkeyA.alloc(fcap, s));
     CLD_TRY(fkeyB.alloc(fcap, s));
+    // chunk tables: a frontier has at most 2 * nnz adjacency entries (push + pull)
+    const size_t ccap = (2 * (size_t)g->nnz) / RC + 2;
+    CLD_TRY(cfA.alloc(ccap, s));
+    CLD_TRY(cfB.alloc(ccap, s));
     CLD_TRY(next.alloc(n, s));
     CLD_TRY(ctr.alloc(1, s));
     Counters* hc = static_cast<Counters*>(g->host.h);
@@ -175,6 +182,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     uint32_t* fv2 = fvB.get();
     uint32_t* fp2 = fpB.get();
     unsigned long long* fk2 = fkeyB.get();
+    uint32_t* cf = cfA.get();
+    uint32_t* cf2 = cfB.get();
     const unsigned max_relax_grid = (unsigned)num_sms() * 8;
     uint32_t nf = 0, E = 0;
 
@@ -183,7 +192,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
         const bool pull = pull_ok && (g->nnz - frozen_deg) < frozen_deg;
         CLD_TRY(zero_field(offsetof(Counters, front), 8));
         CLD_K(K_REBUILD, s, k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), g->off, delta, pull, fv, fk, fp,
-                                                          ctr.get()));
+                                                          cf, ctr.get()));
         CLD_LAUNCH_CHECK();
         return CLDIAM_OK;
     };
@@ -214,12 +223,12 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                     CLD_TRY(zero_field(offsetof(Counters, front), 8));
                     CLD_TRY(zero_field(offsetof(Counters, nnext), 4));
                     const unsigned rg = (unsigned)std::min<uint64_t>((E + RC - 1) / RC, max_relax_grid);
-                    CLD_K(K_RELAX, s, k_relax<<<rg, RT, 0, s>>>(fv, fk, fp, nf, E, g->off, g->adj, center.get(),
+                    CLD_K(K_RELAX, s, k_relax<<<rg, RT, 0, s>>>(fv, fk, fp, cf, nf, E, g->adj, center.get(),
                                                                  key.get(), delta, stamp.get(), stepid, next.get(),
                                                                  ctr.get()));
                     CLD_LAUNCH_CHECK();
                     CLD_K(K_SNAPSHOT, s, k_snapshot<<<max_relax_grid, 256, 0, s>>>(next.get(), key.get(), g->off, delta,
-                                                                                 fv2, fk2, fp2, ctr.get()));
+                                                                                 fv2, fk2, fp2, cf2, ctr.get()));
                     CLD_LAUNCH_CHECK();
                     CLD_TRY(sync_counters());
                     updated = hc->nnext;
@@ -233,6 +242,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                     std::swap(fv, fv2);
                     std::swap(fp, fp2);
                     std::swap(fk, fk2);
+                    std::swap(cf, cf2);
                     nf = (uint32_t)(hc->front >> 32);
                     E = (uint32_t)hc->front;
                 }

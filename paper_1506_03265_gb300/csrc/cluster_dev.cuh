@@ -18,6 +18,11 @@
 // candidates that are already applied.  After a stage start or a Delta
 // doubling every relaxer is listed again.
 //
+// A frontier entry is three parallel words: key (the start-of-step key of a
+// pushing node, or kPullTag | v for a node that pulls), pre (its first
+// position in the frontier's flattened adjacency) and base = off[v] - pre
+// (mod 2^32), so that adjacency index = base + position.
+//
 // Mutable node state is read with L2 loads (__ldcg): inside one persistent
 // CTA there is no kernel boundary to drop stale L1 lines between phases.
 #pragma once
@@ -39,9 +44,23 @@ struct Counters {
     uint32_t pad;
 };
 
-constexpr unsigned long long kPull = kInfKey;  // frontier key marking a pull entry
 constexpr int RT = 256;                        // relax threads per CTA in the grid form
+constexpr int RU = 4;                          // adjacency entries per relax thread per chunk (grid form)
 constexpr int RC = 1024;                       // adjacency entries per relax chunk
+static_assert(RT * RU == RC, "the grid form's chunk is RT x RU entries");
+// In shared memory a pull entry's key is kPullTag | v: a pushed key has
+// d < Delta <= 2^31, so its high word is never all ones.
+constexpr unsigned long long kPullTag = 0xFFFFFFFF00000000ull;
+
+// Chunk table of a frontier: cfirst[c] = the entry whose adjacency range
+// holds flattened position c * RC.  The producer of each entry writes the
+// chunk starts that fall inside its range, so relax finds a chunk's entries
+// with two loads instead of a search over the frontier.
+__device__ __forceinline__ void chunk_table_put(uint32_t* __restrict__ cfirst, uint32_t slot, uint32_t pre,
+                                                uint32_t deg) {
+    const uint64_t end = (uint64_t)pre + deg;
+    for (uint64_t c = ((uint64_t)pre + RC - 1) / RC; c * RC < end; ++c) cfirst[c] = slot;
+}
 
 __device__ __forceinline__ void warp_add_u64(unsigned long long* p, unsigned long long v) {
     v = warp_sum(v);
@@ -98,16 +117,19 @@ __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restric
 // side with fewer adjacency entries.
 __device__ __forceinline__ void dev_rebuild(uint32_t n, const unsigned long long* __restrict__ key,
                                             const uint32_t* __restrict__ center, const uint64_t* __restrict__ off,
-                                            uint32_t delta, bool pull, uint32_t* __restrict__ fv,
+                                            uint32_t delta, bool pull, uint32_t* __restrict__ fbase,
                                             unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre,
-                                            Counters* ctr, unsigned long long* scratch, uint32_t br, uint32_t nb) {
+                                            uint32_t* __restrict__ cfirst, Counters* ctr, unsigned long long* scratch,
+                                            uint32_t br, uint32_t nb) {
     for (uint32_t base = br * blockDim.x; base < n; base += nb * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
         bool push = false, pl = false;
         unsigned long long k = 0;
-        uint32_t deg = 0;
+        uint32_t deg = 0, b0 = 0;
         if (v < n) {
-            deg = (uint32_t)(off[v + 1] - off[v]);
+            const uint64_t o = off[v];
+            b0 = (uint32_t)o;
+            deg = (uint32_t)(off[v + 1] - o);
             const uint32_t c = __ldcg(&center[v]);
             if (deg > 0) {
                 if (c != kNone) {
@@ -123,115 +145,203 @@ __device__ __forceinline__ void dev_rebuild(uint32_t n, const unsigned long long
         uint32_t slot = 0, pre = 0;
         front_append(&ctr->front, push, deg, slot, pre, scratch);
         if (push) {
-            fv[slot] = v;
+            fbase[slot] = b0 - pre;
             fkey[slot] = k;
             fpre[slot] = pre;
+            if (cfirst) chunk_table_put(cfirst, slot, pre, deg);
         }
         front_append(&ctr->front, pl, deg, slot, pre, scratch);
         if (pl) {
-            fv[slot] = v;
-            fkey[slot] = kPull;
+            fbase[slot] = b0 - pre;
+            fkey[slot] = kPullTag | v;
             fpre[slot] = pre;
+            if (cfirst) chunk_table_put(cfirst, slot, pre, deg);
         }
     }
 }
 
-// Shared memory of one relax chunk.
+// Shared memory of the relax chunks: the frontier entries a chunk spans,
+// double-buffered so that one block barrier per chunk separates staging from
+// use (a buffer is restaged only after every thread has passed the barrier
+// that follows its last use).
 struct RelaxSmem {
-    uint32_t pre[RC];
-    uint32_t beg[RC];
-    uint32_t v[RC];
-    unsigned long long key[RC];
-    uint32_t next[RC];  // nodes first changed by this chunk (at most one per entry)
-    uint32_t i0, cnt, nn, nbase;
+    uint32_t pre[2][RC + 1];              // entry's first position in the flattened list
+    uint32_t base[2][RC + 1];             // off[v] - pre (mod 2^32): adjacency index = base + position
+    unsigned long long key[2][RC + 1];    // start-of-step key, or kPullTag | v for a pull entry
 };
+
+// largest i < n with a[i] <= x, for nondecreasing a with a[lo] <= x: a
+// blockDim-ary search, one probe per thread and one barrier per round.
+__device__ __forceinline__ uint32_t block_last_le(const uint32_t* __restrict__ a, uint32_t lo, uint32_t n, uint32_t x) {
+    uint32_t len = n - lo;
+    while (len > 1) {
+        const uint32_t step = (len + blockDim.x - 1) / blockDim.x;
+        const uint64_t idx = (uint64_t)lo + (uint64_t)threadIdx.x * step;
+        const bool pred = threadIdx.x > 0 && idx < (uint64_t)lo + len && __ldcg(&a[idx]) <= x;
+        const uint32_t c = (uint32_t)__syncthreads_count(pred);  // probes 1..c hold, the rest do not
+        const uint32_t nlo = lo + c * step;
+        len = min(step, lo + len - nlo);
+        lo = nlo;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 // a5: one synchronous Delta-growing step over the frontier, edge-balanced:
 // the frontier's adjacency lists are viewed as one flattened range of E
-// entries cut into chunks of RC; each CTA takes chunks, loads the frontier
-// entries the chunk spans into shared memory and maps every entry position to
-// its frontier entry by binary search, so hubs spread over many CTAs.
-__device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fv, const unsigned long long* __restrict__ fkey,
-                                          const uint32_t* __restrict__ fpre, uint32_t nf, uint32_t E,
-                                          const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
+// entries cut into chunks of U x blockDim.x; each CTA takes chunks, and maps
+// each position of a chunk to its frontier entry by binary search over the
+// entries the chunk spans, held in shared memory, so hubs spread over many
+// CTAs.  With a chunk table (cfirst, chunks of RC) a chunk's entries come from
+// two loads; without one, a block-wide search finds them.  The entries of the
+// next chunk are copied into the other shared buffer (cp.async) while the
+// current one is processed, so one barrier per chunk remains.  Every thread
+// handles U positions per chunk with their loads issued together; a key is
+// lowered with a plain atomicMin whose result is not needed, and the
+// per-step stamp decides both "first change this step" (the node joins the
+// next list, one atomic per warp) and "newly covered" (a node that was never
+// lowered before had no key: centers and frozen nodes cannot be lowered).
+template <int U>
+__device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
+                                          const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
+                                          uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
                                           const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
                                           uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
                                           uint32_t* __restrict__ next, Counters* ctr, RelaxSmem& sm, uint32_t br,
                                           uint32_t nb) {
-    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, CL = U * nt;  // CL <= RC; == RC with a chunk table
     unsigned long long newly = 0;
-    for (uint32_t chunk = br; (uint64_t)chunk * RC < E; chunk += nb) {
-        const uint32_t e0 = chunk * RC;
-        const uint32_t e1 = min(E, e0 + RC);
-        if (tid == 0) {
-            uint32_t lo = 0, hi = nf - 1;  // last entry starting at or before e0
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (fpre[mid] <= e0) lo = mid; else hi = mid - 1;
-            }
-            const uint32_t i0 = lo;
-            hi = nf - 1;  // last entry starting at or before e1 - 1
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (fpre[mid] <= e1 - 1) lo = mid; else hi = mid - 1;
-            }
-            sm.i0 = i0;
-            sm.cnt = lo - i0 + 1;
-            sm.nn = 0;
+    // entries [i0, i0 + cnt) that chunk c spans (cnt <= CL + 1: every entry has >= 1 adjacency entry)
+    const auto range_of = [&](uint32_t c, uint32_t& i0, uint32_t& cnt) {
+        const uint32_t e0 = c * CL;
+        const uint32_t e1 = (uint32_t)min((uint64_t)E, (uint64_t)e0 + CL);
+        uint32_t il;
+        if (cfirst) {
+            i0 = __ldcg(&cfirst[c]);
+            il = e1 < E ? __ldcg(&cfirst[c + 1]) : nf - 1;  // may be an entry starting at e1: never matched
+        } else {
+            i0 = block_last_le(fpre, 0, nf, e0);
+            il = block_last_le(fpre, i0, nf, e1 - 1);
         }
-        __syncthreads();
-        const uint32_t i0 = sm.i0, cnt = sm.cnt;  // cnt <= RC: every entry has >= 1 adjacency entry
+        cnt = il - i0 + 1;
+    };
+    const auto stage = [&](uint32_t b, uint32_t i0, uint32_t cnt) {
         for (uint32_t j = tid; j < cnt; j += nt) {
-            const uint32_t v = fv[i0 + j];
-            sm.pre[j] = fpre[i0 + j];
-            sm.v[j] = v;
-            sm.key[j] = fkey[i0 + j];
-            sm.beg[j] = (uint32_t)off[v];
+            cp_async_4(&sm.pre[b][j], &fpre[i0 + j]);
+            cp_async_4(&sm.base[b][j], &fbase[i0 + j]);
+            cp_async_8(&sm.key[b][j], &fkey[i0 + j]);
         }
-        __syncthreads();
-        uint32_t jlo = 0;
-        for (uint32_t base = e0; base < e1; base += nt) {
-            const uint32_t e = base + tid;
-            bool changed_first = false;
-            uint32_t target = 0;
-            if (e < e1) {
-                uint32_t lo = jlo, hi = cnt - 1;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (sm.pre[mid] <= e) lo = mid; else hi = mid - 1;
-                }
-                jlo = lo;
-                const uint2 ed = adj[sm.beg[lo] + (e - sm.pre[lo])];
-                const unsigned long long ku = sm.key[lo];
-                unsigned long long nk = kInfKey;
-                if (ku != kPull) {
-                    const uint64_t cand = (ku >> 32) + ed.y;
+    };
+    uint32_t chunk = br;
+    if ((uint64_t)chunk * CL >= E) {
+        warp_add_u64(&ctr->newly_covered, newly);
+        return;
+    }
+    uint32_t i0, cnt;
+    range_of(chunk, i0, cnt);
+    stage(0, i0, cnt);
+    cp_async_commit_wait_all();
+    __syncthreads();
+    for (uint32_t b = 0;; b ^= 1) {
+        const uint32_t e0 = chunk * CL;
+        const uint32_t e1 = (uint32_t)min((uint64_t)E, (uint64_t)e0 + CL);
+        const uint32_t nchunk = chunk + nb;
+        const bool has_next = (uint64_t)nchunk * CL < E;
+        uint32_t ni0 = 0, ncnt = 0;
+        if (has_next) {
+            range_of(nchunk, ni0, ncnt);
+            stage(b ^ 1, ni0, ncnt);  // buffer b ^ 1 was last read before the previous barrier
+        }
+        uint32_t pos[U], own[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            pos[u] = e0 + tid + (uint32_t)u * nt;
+            // entry j >= 1 starts at or after e0 + j, so the owner of position r is <= r
+            uint32_t lo = 0, hi = min(cnt - 1, pos[u] - e0);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (sm.pre[b][mid] <= pos[u]) lo = mid; else hi = mid - 1;
+            }
+            own[u] = lo;
+        }
+        uint2 ed[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            ed[u] = pos[u] < e1 ? adj[sm.base[b][own[u]] + pos[u]] : make_uint2(0u, 0xFFFFFFFFu);
+        uint32_t target[U];
+        unsigned long long nk[U], cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long ku = sm.key[b][own[u]];
+            nk[u] = kInfKey;
+            target[u] = 0;
+            if (pos[u] < e1) {
+                if ((ku & kPullTag) != kPullTag) {
+                    const uint64_t cand = (ku >> 32) + ed[u].y;
                     if (cand <= delta) {
-                        target = ed.x;
-                        nk = (cand << 32) | (ku & 0xFFFFFFFFull);
+                        target[u] = ed[u].x;
+                        nk[u] = (cand << 32) | (ku & 0xFFFFFFFFull);
                     }
-                } else if (ed.y <= delta) {
-                    const uint32_t cu = __ldcg(&center[ed.x]);
+                } else if (ed[u].y <= delta) {
+                    const uint32_t cu = __ldcg(&center[ed[u].x]);
                     if (cu != kNone) {
-                        target = sm.v[lo];
-                        nk = ((unsigned long long)ed.y << 32) | cu;
-                    }
-                }
-                if (nk != kInfKey && nk < __ldcg(&key[target])) {
-                    const unsigned long long old = atomicMin(&key[target], nk);
-                    if (nk < old) {
-                        newly += (old == kInfKey) ? 1 : 0;
-                        changed_first = atomicExch(&stamp[target], stepid) != stepid;
+                        target[u] = (uint32_t)ku;
+                        nk[u] = ((unsigned long long)ed[u].y << 32) | cu;
                     }
                 }
             }
-            if (changed_first) sm.next[atomicAdd(&sm.nn, 1u)] = target;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = nk[u] != kInfKey ? __ldcg(&key[target[u]]) : 0ull;
+        bool first[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            first[u] = false;
+            if (nk[u] < cur[u]) {
+                // the key is below its start-of-step value after this, whoever wins the minimum
+                atomicMin(&key[target[u]], nk[u]);
+                const uint32_t old = atomicExch(&stamp[target[u]], stepid);
+                first[u] = old != stepid;
+                newly += old == 0u ? 1 : 0;
+            }
+        }
+        unsigned m[U];
+        uint32_t total = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            m[u] = __ballot_sync(0xffffffffu, first[u]);
+            total += (uint32_t)__popc(m[u]);
+        }
+        if (total) {
+            uint32_t wb = 0;
+            if (lane_id() == 0) wb = atomicAdd(&ctr->nnext, total);
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (first[u]) next[wb + (uint32_t)__popc(m[u] & lanemask_lt())] = target[u];
+                wb += (uint32_t)__popc(m[u]);
+            }
+        }
+        cp_async_commit_wait_all();
         __syncthreads();
-        if (tid == 0) sm.nbase = sm.nn ? atomicAdd(&ctr->nnext, sm.nn) : 0u;  // one global atomic per chunk
-        __syncthreads();
-        for (uint32_t j = tid; j < sm.nn; j += nt) next[sm.nbase + j] = sm.next[j];
-        __syncthreads();  // the next chunk reuses the shared arrays
+        if (!has_next) break;
+        chunk = nchunk;
+        i0 = ni0;
+        cnt = ncnt;
     }
     warp_add_u64(&ctr->newly_covered, newly);
 }
@@ -242,26 +352,29 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fv, const
 __device__ __forceinline__ void dev_snapshot(const uint32_t* __restrict__ next, uint32_t nn,
                                              const unsigned long long* __restrict__ key,
                                              const uint64_t* __restrict__ off, uint32_t delta,
-                                             uint32_t* __restrict__ fv, unsigned long long* __restrict__ fkey,
-                                             uint32_t* __restrict__ fpre, Counters* ctr, unsigned long long* scratch,
-                                             uint32_t br, uint32_t nb) {
+                                             uint32_t* __restrict__ fbase, unsigned long long* __restrict__ fkey,
+                                             uint32_t* __restrict__ fpre, uint32_t* __restrict__ cfirst, Counters* ctr,
+                                             unsigned long long* scratch, uint32_t br, uint32_t nb) {
     for (uint32_t base = br * blockDim.x; base < nn; base += nb * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         bool take = false;
-        uint32_t v = 0, deg = 0;
+        uint32_t v = 0, deg = 0, b0 = 0;
         unsigned long long k = 0;
         if (i < nn) {
             v = __ldcg(&next[i]);
             k = __ldcg(&key[v]);
-            deg = (uint32_t)(off[v + 1] - off[v]);
+            const uint64_t o = off[v];
+            b0 = (uint32_t)o;
+            deg = (uint32_t)(off[v + 1] - o);
             take = (uint32_t)(k >> 32) < delta && deg > 0;
         }
         uint32_t slot = 0, pre = 0;
         front_append(&ctr->front, take, deg, slot, pre, scratch);
         if (take) {
-            fv[slot] = v;
+            fbase[slot] = b0 - pre;
             fkey[slot] = k;
             fpre[slot] = pre;
+            if (cfirst) chunk_table_put(cfirst, slot, pre, deg);
         }
     }
 }

@@ -264,16 +264,25 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
+// Stable LSD radix sort of 64-bit keys alone on key bits [shift0, shift0 + bits).
+cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits,
+                                  bool* result_in_alt, cudaStream_t s);
 
 // Unique keys of a sorted sequence with the minimum value of each run:
 // row_out[r] = key / div (row_out may be null), col_out[r*cs] = key % div,
 // w_out[r*cs] = run minimum (w_out must hold 0xFFFFFFFF beforehand);
-// keys >= sentinel are skipped; *total_dev = number of unique keys.
+// keys >= sentinel are skipped; *total_dev = number of unique keys.  With
+// off_out (may be null), off_out[0..nrows] = CSR offsets of the rows.
 cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, size_t cnt, uint64_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
-                                    uint32_t* total_dev, cudaStream_t s);
+                                    uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
 cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
+// The same for packed items (row << col_bits | col) << wb | value, sorted on
+// their key bits; items whose key bits are all ones are skipped.
+cldiam_status unique_min_packed_u64(const uint64_t* items, int wb, size_t cnt, int col_bits, uint32_t* row_out,
+                                    uint32_t* col_out, uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
                                     uint32_t* total_dev, cudaStream_t s);
 
 // CSR offsets off[0..n] of entries whose (sorted) row ids are row[0..nnz):

@@ -2,9 +2,12 @@
 // merge parallel edges to their minimum weight, symmetrise, sort rows by
 // column, optionally keep the largest connected component.
 //
-// Pipeline: 2m directed keys row*n+col are radix sorted (stable, only the
-// bits n*n needs); run heads give the unique entries and an atomicMin over
-// each run gives the lightest parallel edge.  Components come from min-label
+// Pipeline: every undirected edge becomes two directed items.  When
+// 2 * bits(n - 1) + bits(max w) <= 64 an item is one packed word
+// (row << b | col) << wb | w, sorted on its (row, col) bits only; otherwise
+// it is a key row * n + col with the weight beside it.  Run heads of the
+// sorted sequence give the unique entries, and the minimum over each run the
+// lightest parallel edge.  Components come from min-label
 // hooking with pointer jumping: every tree points to a smaller id of its
 // component, so roots are component minima and the labelling is
 // deterministic.
@@ -34,6 +37,39 @@ __global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t
         keys[2 * e + 1] = k1;
         vals[2 * e] = ww;
         vals[2 * e + 1] = ww;
+    }
+}
+
+// input check (ids < n, weights >= 1) and the largest weight
+__global__ void k_check_inputs(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                               const uint32_t* __restrict__ w, uint64_t m, uint32_t n, uint32_t* __restrict__ bad,
+                               uint32_t* __restrict__ wmax) {
+    bool b = false;
+    uint32_t mx = 0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t ww = w[e];
+        b |= src[e] >= n || dst[e] >= n || ww == 0;
+        mx = max(mx, ww);
+    }
+    if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
+    mx = warp_max(mx);
+    if (lane_id() == 0 && mx) atomicMax(wmax, mx);
+}
+
+// both directions of every edge as packed items; a self-loop becomes ~0 (skipped, sorts last)
+__global__ void k_emit_packed(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                              const uint32_t* __restrict__ w, uint64_t m, int vb, int wb, uint64_t* __restrict__ items) {
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t u = src[e], v = dst[e], ww = w[e];
+        uint2 lo, hi;
+        uint64_t i0 = ~0ull, i1 = ~0ull;
+        if (u != v) {
+            i0 = (((u << vb) | v) << wb) | ww;
+            i1 = (((v << vb) | u) << wb) | ww;
+        }
+        lo = make_uint2((uint32_t)i0, (uint32_t)(i0 >> 32));
+        hi = make_uint2((uint32_t)i1, (uint32_t)(i1 >> 32));
+        reinterpret_cast<uint4*>(items)[e] = make_uint4(lo.x, lo.y, hi.x, hi.y);
     }
 }
 
@@ -146,10 +182,15 @@ __global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t*
         }
 }
 
+// copy of the kept rows with new ids (monotone, so rows stay sorted), and the
+// weight statistics of the copy: sum over u < v and minimum
 __global__ void k_lcc_copy(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid,
                            const uint64_t* __restrict__ off, const uint32_t* __restrict__ row,
                            const uint2* __restrict__ adj, uint64_t nnz, const uint64_t* __restrict__ noff,
-                           uint32_t* __restrict__ nrow, uint2* __restrict__ nadj) {
+                           uint32_t* __restrict__ nrow, uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
+                           uint32_t* __restrict__ wmin) {
+    unsigned long long sum = 0;
+    uint32_t mn = 0xFFFFFFFFu;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t u = row[i];
         if (!keep[u]) continue;
@@ -158,7 +199,13 @@ __global__ void k_lcc_copy(const uint32_t* __restrict__ keep, const uint32_t* __
         uint2 e = adj[i];
         nadj[pos] = make_uint2(newid[e.x], e.y);
         nrow[pos] = nu;
+        if (u < e.x) sum += e.y;
+        mn = e.y < mn ? e.y : mn;
     }
+    sum = block_reduce(sum, [](unsigned long long a, unsigned long long b) { return a + b; }, 0ull);
+    if (threadIdx.x == 0 && sum) atomicAdd(wsum, sum);
+    mn = block_reduce(mn, [](uint32_t a, uint32_t b) { return a < b ? a : b; }, 0xFFFFFFFFu);
+    if (threadIdx.x == 0 && mn != 0xFFFFFFFFu) atomicMin(wmin, mn);
 }
 
 __global__ void k_graph_stats(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
@@ -245,34 +292,24 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
     InFree f3{&dw, &ow, s};
 
-    // valid keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
-    const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
-    const int bits = bits_for(sentinel);
+    // input check and the weight range
     const uint64_t cnt = 2 * m;
-    DBuf<uint64_t> keys, keys2;
-    DBuf<uint32_t> vals, vals2, scal;
-    CLD_TRY(keys.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(keys2.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(vals.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(vals2.alloc(cnt ? cnt : 1, s));
+    DBuf<uint32_t> scal;
     CLD_TRY(scal.alloc(8, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(uint32_t), s));
     if (m > 0) {
-        CLD_K(K_CSR, s, k_emit_directed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
-                                                         (const uint32_t*)dw, m, n, sentinel, keys.get(),
-                                                         vals.get(), scal.get()));
+        CLD_K(K_CSR, s, k_check_inputs<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
+                                                                       (const uint32_t*)dw, m, n, scal.get(),
+                                                                       scal.get() + 2));
         CLD_LAUNCH_CHECK();
     }
-    CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     if (*hbad) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
+    const int vb = std::max(1, bits_for((uint64_t)n - 1));
+    const int wb = std::max(1, bits_for(hbad[2]));
+    const bool packed = 2 * vb + wb <= 64;
 
-    bool alt = false;
-    CLD_TRY(radix_sort_pairs_u64(keys.get(), vals.get(), keys2.get(), vals2.get(), cnt, bits, &alt, s));
-    uint64_t* sk = alt ? keys2.get() : keys.get();
-    uint32_t* sv = alt ? vals2.get() : vals.get();
-
-    // unique (row, col) runs with their lightest weight, in one look-back pass
     DBuf<uint32_t> row, deg, degx;
     DBuf<uint64_t> off;
     DBuf<uint2> adj;
@@ -282,18 +319,57 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(degx.alloc((size_t)n + 1, s));
     CLD_TRY(off.alloc((size_t)n + 1, s));
     CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));
-    CLD_TRY(unique_min_sorted_u64(sk, sv, cnt, sentinel, n, row.get(), &adj.get()->x, &adj.get()->y, 2,
-                                  scal.get() + 1, s));
+    if (packed) {
+        DBuf<uint64_t> items, items2;
+        CLD_TRY(items.alloc(cnt ? cnt : 1, s));
+        CLD_TRY(items2.alloc(cnt ? cnt : 1, s));
+        if (m > 0) {
+            CLD_K(K_CSR, s, k_emit_packed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
+                                                                          (const uint32_t*)dw, m, vb, wb, items.get()));
+            CLD_LAUNCH_CHECK();
+        }
+        bool alt = false;
+        CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s));
+        // unique (row, col) runs with their lightest weight, in one look-back pass
+        CLD_TRY(unique_min_packed_u64(alt ? items2.get() : items.get(), wb, cnt, vb, row.get(), &adj.get()->x,
+                                      &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
+    } else {
+        // keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
+        const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
+        DBuf<uint64_t> keys, keys2;
+        DBuf<uint32_t> vals, vals2;
+        CLD_TRY(keys.alloc(cnt ? cnt : 1, s));
+        CLD_TRY(keys2.alloc(cnt ? cnt : 1, s));
+        CLD_TRY(vals.alloc(cnt ? cnt : 1, s));
+        CLD_TRY(vals2.alloc(cnt ? cnt : 1, s));
+        if (m > 0) {
+            CLD_K(K_CSR, s, k_emit_directed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc,
+                                                                            (const uint32_t*)ddst, (const uint32_t*)dw,
+                                                                            m, n, sentinel, keys.get(), vals.get(),
+                                                                            scal.get()));
+            CLD_LAUNCH_CHECK();
+        }
+        bool alt = false;
+        CLD_TRY(radix_sort_pairs_u64(keys.get(), vals.get(), keys2.get(), vals2.get(), cnt, bits_for(sentinel), &alt,
+                                     s));
+        CLD_TRY(unique_min_sorted_u64(alt ? keys2.get() : keys.get(), alt ? vals2.get() : vals.get(), cnt, sentinel, n,
+                                      row.get(), &adj.get()->x, &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
+    }
     CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nnz = hbad[1];
-    keys.release(); keys2.release(); vals.release(); vals2.release();
-    // entries are sorted by row: offsets come from the row boundaries
-    CLD_TRY(offsets_from_rows(row.get(), nnz, n, off.get(), s));
+    // (the row offsets were written by the run heads)
 
     uint32_t n_out = n;
     uint64_t nnz_out = nnz;
     DBuf<uint32_t> orig;
+    // weight statistics for the initial Delta (Algorithm 1 / Section 5): sum over u < v, minimum
+    DBuf<unsigned long long> wsum;
+    CLD_TRY(wsum.alloc(1, s));
+    CLD_CUDA(cudaMemsetAsync(wsum.get(), 0, 8, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
+    bool stats_done = false;
     if (flags & CLDIAM_CSR_LCC) {
         DBuf<uint32_t> parent, size, keep, newid;
         DBuf<unsigned long long> best;
@@ -364,10 +440,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                                                           noff.get()));
         CLD_LAUNCH_CHECK();
         if (nnz) {
-            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), row.get(), adj.get(),
-                                                          nnz, noff.get(), nrow.get(), nadj.get()));
+            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(),
+                                                                         row.get(), adj.get(), nnz, noff.get(),
+                                                                         nrow.get(), nadj.get(), wsum.get(),
+                                                                         scal.get() + 6));
             CLD_LAUNCH_CHECK();
         }
+        stats_done = true;
         g->off = noff.detach();
         g->adj = nadj.detach();
         g->row = nrow.detach();
@@ -384,13 +463,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     g->nnz = nnz_out;
     g->connected = (flags & CLDIAM_CSR_LCC) != 0;
 
-    // weight statistics for the initial Delta (Algorithm 1 / Section 5)
-    DBuf<unsigned long long> wsum;
-    CLD_TRY(wsum.alloc(1, s));
-    CLD_CUDA(cudaMemsetAsync(wsum.get(), 0, 8, s));
-    CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
-    CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
-    if (g->nnz) {
+    if (g->nnz && !stats_done) {
         CLD_K(K_CSR, s, k_graph_stats<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, wsum.get(), scal.get() + 6));
         CLD_LAUNCH_CHECK();
     }

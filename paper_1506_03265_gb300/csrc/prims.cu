@@ -242,9 +242,9 @@ cldiam_status reduce_sum_u32_to_u64(const uint32_t* in, size_t n, uint64_t* out,
 // digit order and written out as contiguous runs.
 constexpr int OS_THREADS = 256;
 constexpr int OS_WARPS = OS_THREADS / 32;
-template <class K>
-struct OsCfg {  // items per thread: fewer for 64-bit keys to keep registers (and occupancy) in check
-    static constexpr int ITEMS = sizeof(K) == 8 ? 8 : 12;
+template <class K, bool KV>
+struct OsCfg {  // items per thread: fewer for 64-bit (key, value) pairs to keep registers (and occupancy) in check
+    static constexpr int ITEMS = (sizeof(K) == 8 && KV) ? 8 : 12;
     static constexpr int TILE = OS_THREADS * ITEMS;
 };
 constexpr int OS_RADIX = 256;
@@ -253,7 +253,7 @@ constexpr unsigned long long OS_PRE = 2ull << 32;   // status: inclusive prefix 
 constexpr long long OS_WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: a look-back that waits longer gives up
 
 template <class K>
-__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass,
+__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass, int shift0,
                                                  uint32_t* __restrict__ hist) {
     // one private histogram per warp and pass: shared atomics collide only within a warp
     __shared__ uint32_t h[8][4][OS_RADIX];  // warps x passes (<= 4 per launch) x digits
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, siz
             for (int u = 0; u < U; ++u) {
                 if (base + (size_t)u * stride >= n) break;
                 for (int p = 0; p < np; ++p)
-                    atomicAdd(&h[w][p][(uint32_t)((kk[u] >> (8 * (p0 + p))) & 0xFF)], 1u);
+                    atomicAdd(&h[w][p][(uint32_t)((kk[u] >> (shift0 + 8 * (p0 + p))) & 0xFF)], 1u);
             }
         }
         __syncthreads();
@@ -308,7 +308,8 @@ __global__ void k_os_hist_scan(uint32_t* __restrict__ hist, int npass) {
     }
 }
 
-template <class K, int OS_ITEMS = OsCfg<K>::ITEMS, int OS_TILE = OsCfg<K>::TILE>
+// KV: items carry a 32-bit value (vin/vout); otherwise keys only.
+template <class K, bool KV, int OS_ITEMS = OsCfg<K, KV>::ITEMS, int OS_TILE = OsCfg<K, KV>::TILE>
 __global__ void __launch_bounds__(OS_THREADS, 4)
     k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
               uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ goff,
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
     const unsigned ltmask = lanemask_lt();
 
     K key[OS_ITEMS];
-    uint32_t val[OS_ITEMS];
+    uint32_t val[KV ? OS_ITEMS : 1];
     uint32_t rank_pk[(OS_ITEMS + 1) / 2];  // warp-local ranks (< 32 * OS_ITEMS) as 16-bit halves; 0xFFFF = no item
     // issue every load of the tile before ranking, so they are in flight together
 #pragma unroll
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         const size_t idx = tbase + (size_t)w * (OS_ITEMS * 32) + (size_t)i * 32 + l;
         const bool valid = idx < n;
         key[i] = valid ? kin[idx] : (K)0;
-        val[i] = valid ? vin[idx] : 0u;
+        if constexpr (KV) val[i] = valid ? vin[idx] : 0u;
     }
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
             const uint32_t dd = (uint32_t)((key[i] >> shift) & 0xFF);
             const uint32_t pos = tstart[dd] + whist[w][dd] + rk;
             s_key[pos] = key[i];
-            s_val[pos] = val[i];
+            if constexpr (KV) s_val[pos] = val[i];
         }
     }
     __syncthreads();
@@ -434,26 +435,29 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         const uint32_t dd = (uint32_t)((k >> shift) & 0xFF);
         const size_t pos = (size_t)gbase[dd] + (i - tstart[dd]);
         kout[pos] = k;
-        vout[pos] = s_val[i];
+        if constexpr (KV) vout[pos] = s_val[i];
     }
 }
 
+// LSD sort of n items on key bits [shift0, shift0 + bits); vals == nullptr sorts keys only.
 template <class K>
-static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, size_t n,
-                                      int bits, bool* in_alt, cudaStream_t s) {
+static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, size_t n, int shift0,
+                                     int bits, bool* in_alt, cudaStream_t s) {
     *in_alt = false;
     if (n <= 1 || bits <= 0) return CLDIAM_OK;
     if (n > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "radix sort limited to 2^32 - 1 items");
+    const bool kv = vals != nullptr;
     const int npass = (bits + 7) / 8;
-    constexpr int OS_TILE = OsCfg<K>::TILE;
-    const uint32_t ntiles = (uint32_t)((n + OS_TILE - 1) / OS_TILE);
-    const size_t smem = (sizeof(K) + sizeof(uint32_t)) * OS_TILE;
-    static bool attr_set[64];
+    const int tile = kv ? OsCfg<K, true>::TILE : OsCfg<K, false>::TILE;
+    const uint32_t ntiles = (uint32_t)((n + tile - 1) / tile);
+    const size_t smem = (sizeof(K) + (kv ? sizeof(uint32_t) : 0)) * tile;
+    static bool attr_set[2][64];
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    if (dev < 0 || dev >= 64 || !attr_set[kv][dev]) {
+        if (kv) CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev >= 0 && dev < 64) attr_set[kv][dev] = true;
     }
     DBuf<uint32_t> hist, ctl;
     DBuf<unsigned long long> status;
@@ -462,7 +466,7 @@ static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint
     CLD_TRY(status.alloc((size_t)ntiles * OS_RADIX, s));
     CLD_CUDA(cudaMemsetAsync(hist.get(), 0, (size_t)npass * OS_RADIX * 4, s));
     CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, (2 * npass + 2) * 4, s));
-    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, 0, s>>>(keys, n, npass, hist.get()));
+    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, 0, s>>>(keys, n, npass, shift0, hist.get()));
     CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist.get(), npass));
     CLD_LAUNCH_CHECK();
     prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
@@ -473,12 +477,20 @@ static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint
     bool alt = false;
     for (int p = 0; p < npass; ++p) {
         CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * OS_RADIX * 8, s));
-        CLD_K(K_RADIX_SCATTER, s,
-              k_os_pass<K><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, 8 * p, hist.get() + p * OS_RADIX,
-                                                            status.get(), ctl.get() + p, ctl.get() + 2 * npass));
+        if (kv) {
+            CLD_K(K_RADIX_SCATTER, s,
+                  k_os_pass<K, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, shift0 + 8 * p,
+                                                                      hist.get() + p * OS_RADIX, status.get(),
+                                                                      ctl.get() + p, ctl.get() + 2 * npass));
+        } else {
+            CLD_K(K_RADIX_SCATTER, s,
+                  k_os_pass<K, false><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n, shift0 + 8 * p,
+                                                                       hist.get() + p * OS_RADIX, status.get(),
+                                                                       ctl.get() + p, ctl.get() + 2 * npass));
+        }
         CLD_LAUNCH_CHECK();
-        // algorithmic bytes: every (key, value) read once and written once
-        prof_add_bytes(K_RADIX_SCATTER, 2.0 * (double)n * (sizeof(K) + sizeof(uint32_t)));
+        // algorithmic bytes: every item (key and value) read once and written once
+        prof_add_bytes(K_RADIX_SCATTER, 2.0 * (double)n * (sizeof(K) + (kv ? sizeof(uint32_t) : 0)));
         K* tk = ki; ki = ko; ko = tk;
         uint32_t* tv = vi; vi = vo; vo = tv;
         alt = !alt;
@@ -498,15 +510,22 @@ static cldiam_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint
 // minimum value is folded in with one atomicMin per run piece per warp.
 // Output per unique key: row_out[r] = key / div (if row_out), col_out[r*cs] =
 // key % div, w_out[r*cs] = min value (w_out pre-filled with 0xFFFFFFFF).
-// Keys >= sentinel are ignored (they sort last).
+// Keys >= sentinel are ignored (they sort last).  Packed items (vals ==
+// nullptr, wb > 0) hold the value in their low wb bits and the key above it;
+// div_shift >= 0 replaces the division by a shift (div = 2^div_shift).
+// With off_out, the run heads also write the CSR offsets of rows
+// 0..nrows: off_out[q] = index of the first unique key with row >= q (a head
+// fills the rows after its predecessor's row up to its own; the last run
+// fills the rows after it with the total).
 constexpr int UQ_THREADS = 256;
 constexpr int UQ_ITEMS = 8;
 constexpr int UQ_TILE = UQ_THREADS * UQ_ITEMS;
 
 template <class K>
-__global__ void __launch_bounds__(UQ_THREADS)
-    k_unique_lb(const K* __restrict__ keys, const uint32_t* __restrict__ vals, size_t cnt, K sentinel, uint64_t div,
-                uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out, uint32_t* __restrict__ w_out, int cs,
+__global__ void __launch_bounds__(UQ_THREADS, 4)
+    k_unique_lb(const K* __restrict__ keys, const uint32_t* __restrict__ vals, int wb, size_t cnt, K sentinel,
+                uint64_t div, int div_shift, uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out,
+                uint32_t* __restrict__ w_out, int cs, uint64_t* __restrict__ off_out, uint32_t nrows,
                 unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ total,
                 uint32_t* __restrict__ err) {
     __shared__ uint32_t s_tile, s_woff[UQ_THREADS / 32], s_prefix;
@@ -517,19 +536,27 @@ __global__ void __launch_bounds__(UQ_THREADS)
     const size_t base = (size_t)tile * UQ_TILE + (size_t)w * (UQ_ITEMS * 32);
     K key[UQ_ITEMS];
     uint32_t val[UQ_ITEMS];
+    const K wmask = (K)((1ull << wb) - 1ull);
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
-        key[i] = idx < cnt ? keys[idx] : sentinel;
-        val[i] = idx < cnt ? vals[idx] : 0xFFFFFFFFu;
+        if (vals) {
+            key[i] = idx < cnt ? keys[idx] : sentinel;
+            val[i] = idx < cnt ? vals[idx] : 0xFFFFFFFFu;
+        } else {
+            const K it = idx < cnt ? keys[idx] : (K)0;
+            key[i] = idx < cnt ? (K)(it >> wb) : sentinel;
+            val[i] = idx < cnt ? (uint32_t)(it & wmask) : 0xFFFFFFFFu;
+        }
     }
+    const int ks = vals ? 0 : wb;  // key of a neighbouring item read from memory
     uint32_t head_bits = 0, run = 0;
     uint32_t ex[UQ_ITEMS];
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
         K prev = __shfl_up_sync(0xffffffffu, key[i], 1);
-        if (l == 0) prev = (idx > 0 && idx < cnt) ? keys[idx - 1] : sentinel;
+        if (l == 0) prev = (idx > 0 && idx < cnt) ? (K)(keys[idx - 1] >> ks) : sentinel;
         const bool f = key[i] < sentinel && (idx == 0 || prev != key[i]);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
         ex[i] = run + (uint32_t)__popc(bal & lanemask_lt());
@@ -601,7 +628,9 @@ __global__ void __launch_bounds__(UQ_THREADS)
         const unsigned seg0 = 31u - __clz(starts & (0xffffffffu >> (31u - l)));
         const bool whole_head = (__shfl_sync(0xffffffffu, head_bits, seg0) >> i) & 1u;
         K after = __shfl_down_sync(0xffffffffu, key[i], 1);
-        if (l == 31) after = (idx + 1 < cnt) ? keys[idx + 1] : sentinel;
+        if (l == 31) after = (idx + 1 < cnt) ? (K)(keys[idx + 1] >> ks) : sentinel;
+        K before = up;
+        if (l == 0) before = idx > 0 ? (K)(keys[idx - 1] >> ks) : sentinel;
         if (!valid) continue;
         const uint32_t f = (head_bits >> i) & 1u;
         const uint32_t r = tbase + ex[i] + f - 1u;
@@ -609,20 +638,31 @@ __global__ void __launch_bounds__(UQ_THREADS)
             if (whole_head && after != key[i]) w_out[(size_t)r * cs] = v;
             else atomicMin(&w_out[(size_t)r * cs], v);
         }
+        const auto row_of = [&](K kk) -> uint64_t {
+            return div_shift >= 0 ? ((uint64_t)kk >> div_shift) : (uint64_t)kk / div;
+        };
+        const uint64_t q = row_of(key[i]);
         if (f) {
-            const uint64_t q = (uint64_t)key[i] / div;
             if (row_out) row_out[r] = (uint32_t)q;
             col_out[(size_t)r * cs] = (uint32_t)((uint64_t)key[i] - q * div);
+            if (off_out) {
+                const uint64_t q0 = idx == 0 ? 0ull : row_of(before) + 1ull;  // rows after the previous run's row
+                for (uint64_t qq = q0; qq <= q && qq <= nrows; ++qq) off_out[qq] = r;
+            }
         }
+        if (off_out && tail && !(after < sentinel))  // the last run: the remaining rows end at the total
+            for (uint64_t qq = q + 1; qq <= nrows; ++qq) off_out[qq] = (uint64_t)r + 1;
     }
 }
 
 template <class K>
-static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size_t cnt, K sentinel, uint64_t div,
-                                       uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, int wb, size_t cnt, K sentinel,
+                                       uint64_t div, int div_shift, uint32_t* row_out, uint32_t* col_out,
+                                       uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
                                        uint32_t* total_dev, cudaStream_t s) {
     if (cnt == 0) {
         CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
+        if (off_out) CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));
         return CLDIAM_OK;
     }
     if (cnt > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "more than 2^32 - 1 items");
@@ -633,35 +673,50 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size
     CLD_TRY(ctl.alloc(2, s));
     CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * 8, s));
     CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, 8, s));
-    CLD_K(K_CSR, s, k_unique_lb<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out,
-                                                                  cs, status.get(), ctl.get(), total_dev,
-                                                                  ctl.get() + 1));
+    CLD_K(K_CSR, s, k_unique_lb<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, wb, cnt, sentinel, div, div_shift,
+                                                                  row_out, col_out, w_out, cs, off_out, nrows,
+                                                                  status.get(), ctl.get(), total_dev, ctl.get() + 1));
     CLD_LAUNCH_CHECK();
-    uint32_t herr = 0;
-    CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
+    uint32_t h[2] = {0, 0};
+    CLD_CUDA(cudaMemcpyAsync(&h[0], ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaMemcpyAsync(&h[1], total_dev, 4, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
-    if (herr) return fail(CLDIAM_ERR_TIMEOUT, "unique look-back wait expired");
+    if (h[0]) return fail(CLDIAM_ERR_TIMEOUT, "unique look-back wait expired");
+    if (off_out && h[1] == 0) CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));  // no valid key
     return CLDIAM_OK;
 }
 
 cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, size_t cnt, uint64_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
+                                    uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
+    return unique_min_sorted<uint64_t>(keys, vals, 0, cnt, sentinel, div, -1, row_out, col_out, w_out, cs, off_out,
+                                       nrows, total_dev, s);
+}
+cldiam_status unique_min_packed_u64(const uint64_t* items, int wb, size_t cnt, int col_bits, uint32_t* row_out,
+                                    uint32_t* col_out, uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
                                     uint32_t* total_dev, cudaStream_t s) {
-    return unique_min_sorted<uint64_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, total_dev, s);
+    const uint64_t sentinel = (1ull << (2 * col_bits)) - 1ull;
+    return unique_min_sorted<uint64_t>(items, nullptr, wb, cnt, sentinel, 1ull << col_bits, col_bits, row_out,
+                                       col_out, w_out, cs, off_out, nrows, total_dev, s);
 }
 cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
-                                    uint32_t* total_dev, cudaStream_t s) {
-    return unique_min_sorted<uint32_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, total_dev, s);
+                                    uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
+    return unique_min_sorted<uint32_t>(keys, vals, 0, cnt, sentinel, div, -1, row_out, col_out, w_out, cs, off_out,
+                                       nrows, total_dev, s);
 }
 
 cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* in_alt, cudaStream_t s) {
-    return radix_sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, in_alt, s);
+    return radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, 0, bits, in_alt, s);
+}
+cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits, bool* in_alt,
+                                  cudaStream_t s) {
+    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s);
 }
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* in_alt, cudaStream_t s) {
-    return radix_sort_pairs<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, in_alt, s);
+    return radix_sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, 0, bits, in_alt, s);
 }
 
 }  // namespace cld

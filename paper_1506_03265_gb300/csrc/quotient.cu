@@ -52,8 +52,10 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
     }
 }
 
-// Dense alternative for small k: fold every inter-cluster edge into M[a*k + b] with atomicMin
-// (the k x k matrix stays in L2), then read the rows out in column order.
+// Dense alternative for small k: fold every inter-cluster edge into the k x k matrix M with
+// atomicMin (it stays in L2), then read the rows out in column order.  The quotient is symmetric
+// (an edge's weight D_u + w + D_v does not depend on its direction), so each undirected edge is
+// folded once, from its u < v entry, into the upper triangle, which is then mirrored.
 __global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
                                const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D, uint32_t k,
                                uint32_t* __restrict__ M, uint32_t* __restrict__ overflow) {
@@ -61,6 +63,7 @@ __global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t u = row[i];
         const uint2 e = adj[i];
+        if (u >= e.x) continue;
         const uint32_t a = cid[u], b = cid[e.x];
         if (a == b) continue;
         uint64_t s = (uint64_t)D[u] + e.y + D[e.x];
@@ -68,10 +71,26 @@ __global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __
             ovf = true;
             s = 0xFFFFFFFEull;
         }
-        uint32_t* m = &M[(size_t)a * k + b];
+        uint32_t* m = &M[(size_t)min(a, b) * k + max(a, b)];
         if ((uint32_t)s < __ldcg(m)) atomicMin(m, (uint32_t)s);
     }
     if (__any_sync(0xffffffffu, ovf) && lane_id() == 0) atomicExch(overflow, 1u);
+}
+
+// lower triangle := transpose of the upper one, through 32 x 32 shared-memory tiles
+__global__ void k_q_dense_mirror(uint32_t* __restrict__ M, uint32_t k) {
+    __shared__ uint32_t t[32][33];
+    const uint32_t r = blockIdx.y, c = blockIdx.x;  // source tile (r, c) with c >= r
+    if (c < r) return;
+    for (uint32_t y = threadIdx.y; y < 32; y += blockDim.y) {
+        const uint32_t a = r * 32 + y, b = c * 32 + threadIdx.x;
+        t[y][threadIdx.x] = (a < k && b < k) ? M[(size_t)a * k + b] : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    for (uint32_t y = threadIdx.y; y < 32; y += blockDim.y) {
+        const uint32_t a = c * 32 + y, b = r * 32 + threadIdx.x;  // destination (a, b) = source (b, a)
+        if (a < k && b < k && a > b) M[(size_t)a * k + b] = t[threadIdx.x][y];
+    }
 }
 
 // row a's entry count (warp per row)
@@ -128,6 +147,11 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
                                                                                 k, M.get(), scal.get()));
         CLD_LAUNCH_CHECK();
     }
+    {
+        const uint32_t nt = (k + 31) / 32;
+        CLD_K(K_QUOTIENT, s, k_q_dense_mirror<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(M.get(), k));
+        CLD_LAUNCH_CHECK();
+    }
     CLD_K(K_QUOTIENT, s, k_q_dense_count<<<grid_for((size_t)k * 32, 256), 256, 0, s>>>(M.get(), k, deg.get()));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive_u32(deg.get(), start.get(), k, scal.get() + 1, s));
@@ -144,8 +168,9 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
                                                                                     w.get()));
     CLD_K(K_QUOTIENT, s, k_q_widen<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(start.get(), k, nq, off.get()));
     CLD_LAUNCH_CHECK();
-    // algorithmic bytes: each CSR entry's row, (col, w) and two cluster ids and two D values
-    prof_add_bytes(K_QUOTIENT, (double)g->nnz * 28.0 + (double)k * k * 8.0);
+    // algorithmic bytes: each CSR entry's row and (col, w); for half of them two cluster ids and two
+    // D values; the matrix mirrored and read twice
+    prof_add_bytes(K_QUOTIENT, (double)g->nnz * 20.0 + (double)k * k * 12.0);
     CLD_CUDA(cudaStreamSynchronize(s));
     q->k = k;
     q->nnz = nq;
@@ -192,24 +217,21 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     uint32_t* sv = alt ? vals2.get() : vals.get();
 
     // unique cluster pairs with their lightest weight, in one look-back pass
-    DBuf<uint32_t> qrow, col, w;
+    DBuf<uint32_t> col, w;
     DBuf<uint64_t> off;
-    CLD_TRY(qrow.alloc(cnt ? cnt : 1, s));
     CLD_TRY(col.alloc(cnt ? cnt : 1, s));
     CLD_TRY(w.alloc(cnt ? cnt : 1, s));
     CLD_TRY(off.alloc((size_t)k + 1, s));
     CLD_CUDA(cudaMemsetAsync(w.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 4, s));
     if (sizeof(K) == 8)
-        CLD_TRY(unique_min_sorted_u64((const uint64_t*)sk, sv, cnt, ~0ull, k, qrow.get(), col.get(), w.get(), 1,
-                                      scal.get() + 2, s));
+        CLD_TRY(unique_min_sorted_u64((const uint64_t*)sk, sv, cnt, ~0ull, k, nullptr, col.get(), w.get(), 1,
+                                      off.get(), k, scal.get() + 2, s));
     else
-        CLD_TRY(unique_min_sorted_u32((const uint32_t*)sk, sv, cnt, 0xFFFFFFFFu, k, qrow.get(), col.get(), w.get(), 1,
-                                      scal.get() + 2, s));
+        CLD_TRY(unique_min_sorted_u32((const uint32_t*)sk, sv, cnt, 0xFFFFFFFFu, k, nullptr, col.get(), w.get(), 1,
+                                      off.get(), k, scal.get() + 2, s));
     CLD_CUDA(cudaMemcpyAsync(hh + 2, scal.get() + 2, 4, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     const uint32_t nq = hh[2];
-    CLD_TRY(offsets_from_rows(qrow.get(), nq, k, off.get(), s));
-    CLD_CUDA(cudaStreamSynchronize(s));
     q->k = k;
     q->nnz = nq;
     q->off = off.detach();

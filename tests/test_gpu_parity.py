@@ -79,6 +79,19 @@ def test_csr_random(cd, seed, lcc):
     check_csr(cd, *rand_edges(seed), lcc)
 
 
+@pytest.mark.parametrize("n,wmax", [(200_000, 0xFFFFFFFF), (70_000, 1 << 31), (1 << 16, 0xFFFFFFFF), (5, 0xFFFFFFFF),
+                                    (1 << 20, 1 << 24), (1 << 20, (1 << 24) - 1)])
+def test_csr_wide_items(cd, n, wmax):
+    # 2 * bits(n - 1) + bits(max w) > 64 takes the (key, weight) pair path, <= 64 the packed-word path
+    m = 3 * n
+    rng = np.random.default_rng(n)
+    src = rng.integers(0, n, m).astype(np.uint32)
+    dst = rng.integers(0, n, m).astype(np.uint32)
+    w = rng.integers(1, wmax, m, dtype=np.uint64, endpoint=True).astype(np.uint32)
+    w[:4] = wmax  # the largest weight is present
+    check_csr(cd, n, src, dst, w, False)
+
+
 def test_csr_degenerate(cd):
     z = np.zeros(0, np.uint32)
     g = cd.build_csr(z, z, z, 1)
