@@ -329,8 +329,10 @@ def run_gpu(args):
     stream.synchronize()
     in_bytes = 3 * 4 * e.m
 
-    def step():
+    def step(mid_event=None):
         g = cd.build_csr(src_d, dst_d, w_d, e.n, lcc=True, stream=stream)
+        if mid_event is not None:
+            mid_event.record(stream)  # end of the CSR build (row a1) on the device timeline
         c = cd.cluster(g, wl.tau, wl.seed)
         q = cd.quotient_build(c)
         r = cd.estimate(q)
@@ -378,21 +380,28 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_wall0 = time.time()
     ev0.record(stream)
-    for _ in range(args.steps):
-        g, c, q, r2 = step()
+    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)] + [ev1]
+    for i in range(args.steps):
+        g, c, q, r2 = step(ev_mid[i])
         del g, c, q
-    ev1.record(stream)
+        ev_end[i].record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.time()
     if dist:
         dist.barrier()
     sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
+    # split of each step: CSR build (a1) vs CLUSTER + quotient + estimate (a2-a11)
+    ms_csr = sum((ev0 if i == 0 else ev_end[i - 1]).elapsed_time(ev_mid[i]) for i in range(args.steps)) / args.steps
+    ms_rest = sum(ev_mid[i].elapsed_time(ev_end[i]) for i in range(args.steps)) / args.steps
     prof = cd.profile_get()
     launches = sum(v["launches"] for v in prof.values())
     if dist:
         from paper_1506_03265_gb300.shard import max_over_ranks
         ms = max_over_ranks(ms, dist, torch.device("cuda", local))
+        ms_csr = max_over_ranks(ms_csr, dist, torch.device("cuda", local))
+        ms_rest = max_over_ranks(ms_rest, dist, torch.device("cuda", local))
     value = ws * m_lcc / (ms * 1e-3) / 1e9
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -464,6 +473,9 @@ def run_gpu(args):
         "result": {k: r[k] for k in ("k", "phi_gc", "radius", "phi_approx", "stages", "steps", "doublings",
                                      "delta_end", "node_updates", "edges_scanned", "quotient_edges")},
         "parity": parity,
+        "step_split": {"csr_build_ms": round(ms_csr, 3), "cluster_quotient_estimate_ms": round(ms_rest, 3),
+                       "gteps_excluding_csr_build": round(ws * m_lcc / (ms_rest * 1e-3) / 1e9, 4),
+                       "what": "m_LCC / time of CLUSTER + quotient + estimate on a built CSR (the same timed steps)"},
         "e2e": e2e,
         "roofline": roofline,
         "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},

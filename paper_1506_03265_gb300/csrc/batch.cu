@@ -112,6 +112,7 @@ __device__ __forceinline__ T block_all_reduce(T v, Op op, T* red) {
 
 struct BatchSmem {
     RelaxSmem relax;
+    uint32_t relax_next[relax_nbuf_words<1>(32)];  // 1024 threads
     unsigned long long scratch[33];
     unsigned long long red64[33];
     uint32_t red32[33];
@@ -307,7 +308,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                     }
                     __syncthreads();
                     dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr, nf, E, adj, ws.center, ws.key,
-                                 delta, ws.stamp, stepid, ws.next, ctr, sm.relax, 0, 1);
+                                 delta, ws.stamp, stepid, ws.next, ctr, sm.relax, sm.relax_next, 0, 1);
                     __syncthreads();
                     const uint32_t nn = vc->nnext;
                     dev_snapshot(ws.next, nn, ws.key, off, delta, ws.fbase[cur ^ 1], ws.fkey[cur ^ 1],

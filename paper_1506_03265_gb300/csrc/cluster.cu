@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fbase
                                               uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
                                               uint32_t* __restrict__ next, Counters* ctr) {
     __shared__ RelaxSmem sm;
-    dev_relax<RU>(fbase, fkey, fpre, cfirst, nf, E, adj, center, key, delta, stamp, stepid, next, ctr, sm,
+    __shared__ uint32_t nbuf[relax_nbuf_words<RU>(RT / 32)];
+    dev_relax<RU>(fbase, fkey, fpre, cfirst, nf, E, adj, center, key, delta, stamp, stepid, next, ctr, sm, nbuf,
                   blockIdx.x, gridDim.x);
 }
 

@@ -169,6 +169,10 @@ struct RelaxSmem {
     uint32_t base[2][RC + 1];             // off[v] - pre (mod 2^32): adjacency index = base + position
     unsigned long long key[2][RC + 1];    // start-of-step key, or kPullTag | v for a pull entry
 };
+// Changed nodes waiting to be appended to the next list: 2 x U x 32 words per
+// warp, flushed once half full.
+template <int U>
+constexpr int relax_nbuf_words(int warps) { return warps * 2 * U * 32; }
 
 // largest i < n with a[i] <= x, for nondecreasing a with a[lo] <= x: a
 // blockDim-ary search, one probe per thread and one barrier per round.
@@ -213,18 +217,31 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // handles U positions per chunk with their loads issued together; a key is
 // lowered with a plain atomicMin whose result is not needed, and the
 // per-step stamp decides both "first change this step" (the node joins the
-// next list, one atomic per warp) and "newly covered" (a node that was never
-// lowered before had no key: centers and frozen nodes cannot be lowered).
+// next list) and "newly covered" (a node that was never lowered before had
+// no key: centers and frozen nodes cannot be lowered).  Changed nodes gather
+// in a per-warp shared buffer that is appended to the next list with one
+// atomic per U x 32 or more nodes.
 template <int U>
 __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
                                           const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
                                           uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
                                           const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
                                           uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
-                                          uint32_t* __restrict__ next, Counters* ctr, RelaxSmem& sm, uint32_t br,
-                                          uint32_t nb) {
+                                          uint32_t* __restrict__ next, Counters* ctr, RelaxSmem& sm,
+                                          uint32_t* nbuf, uint32_t br, uint32_t nb) {
+    constexpr uint32_t kNB = 2 * U * 32;  // a chunk adds at most U x 32 nodes per warp
     const uint32_t tid = threadIdx.x, nt = blockDim.x, CL = U * nt;  // CL <= RC; == RC with a chunk table
     unsigned long long newly = 0;
+    uint32_t* wbuf = nbuf + (tid >> 5) * kNB;
+    uint32_t wcnt = 0;  // entries in this warp's buffer (warp-uniform)
+    const auto flush = [&]() {  // one atomic per kNB / 2 or more changed nodes
+        uint32_t wb = 0;
+        if (lane_id() == 0) wb = atomicAdd(&ctr->nnext, wcnt);
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        for (uint32_t j = lane_id(); j < wcnt; j += 32) next[wb + j] = wbuf[j];
+        wcnt = 0;
+        __syncwarp();
+    };
     // entries [i0, i0 + cnt) that chunk c spans (cnt <= CL + 1: every entry has >= 1 adjacency entry)
     const auto range_of = [&](uint32_t c, uint32_t& i0, uint32_t& cnt) {
         const uint32_t e0 = c * CL;
@@ -247,10 +264,7 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
         }
     };
     uint32_t chunk = br;
-    if ((uint64_t)chunk * CL >= E) {
-        warp_add_u64(&ctr->newly_covered, newly);
-        return;
-    }
+    if ((uint64_t)chunk * CL >= E) return;
     uint32_t i0, cnt;
     range_of(chunk, i0, cnt);
     stage(0, i0, cnt);
@@ -314,28 +328,22 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
             if (nk[u] < cur[u]) {
                 // the key is below its start-of-step value after this, whoever wins the minimum
                 atomicMin(&key[target[u]], nk[u]);
-                const uint32_t old = atomicExch(&stamp[target[u]], stepid);
-                first[u] = old != stepid;
-                newly += old == 0u ? 1 : 0;
+                // only the first changers of a node this step need the exchange (hubs see many)
+                if (__ldcg(&stamp[target[u]]) != stepid) {
+                    const uint32_t old = atomicExch(&stamp[target[u]], stepid);
+                    first[u] = old != stepid;
+                    newly += old == 0u ? 1 : 0;
+                }
             }
         }
-        unsigned m[U];
-        uint32_t total = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            m[u] = __ballot_sync(0xffffffffu, first[u]);
-            total += (uint32_t)__popc(m[u]);
+            const unsigned m = __ballot_sync(0xffffffffu, first[u]);
+            if (first[u]) wbuf[wcnt + (uint32_t)__popc(m & lanemask_lt())] = target[u];
+            wcnt += (uint32_t)__popc(m);
         }
-        if (total) {
-            uint32_t wb = 0;
-            if (lane_id() == 0) wb = atomicAdd(&ctr->nnext, total);
-            wb = __shfl_sync(0xffffffffu, wb, 0);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (first[u]) next[wb + (uint32_t)__popc(m[u] & lanemask_lt())] = target[u];
-                wb += (uint32_t)__popc(m[u]);
-            }
-        }
+        __syncwarp();
+        if (wcnt >= kNB / 2) flush();
         cp_async_commit_wait_all();
         __syncthreads();
         if (!has_next) break;
@@ -343,6 +351,7 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
         i0 = ni0;
         cnt = ncnt;
     }
+    if (wcnt) flush();
     warp_add_u64(&ctr->newly_covered, newly);
 }
 

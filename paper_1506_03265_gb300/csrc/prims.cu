@@ -504,10 +504,11 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
 }
 
 // ------------------------------------------------------------------ unique runs of a sorted sequence
-// One pass over sorted (key, value) pairs: run heads get consecutive indices
-// r (a tile counts its heads with ballots, and gets the heads of all earlier
-// tiles by decoupled look-back on one status word per tile); for each run the
-// minimum value is folded in with one atomicMin per run piece per warp.
+// Two passes over sorted (key, value) pairs: the first counts each tile's run
+// heads (ballots), an exclusive scan turns the counts into each tile's first
+// output index, and the second gives the heads consecutive indices r and
+// writes them; for each run the minimum value is folded in with one store per
+// run inside a warp, or one atomicMin per run piece per warp otherwise.
 // Output per unique key: row_out[r] = key / div (if row_out), col_out[r*cs] =
 // key % div, w_out[r*cs] = min value (w_out pre-filled with 0xFFFFFFFF).
 // Keys >= sentinel are ignored (they sort last).  Packed items (vals ==
@@ -521,18 +522,46 @@ constexpr int UQ_THREADS = 256;
 constexpr int UQ_ITEMS = 8;
 constexpr int UQ_TILE = UQ_THREADS * UQ_ITEMS;
 
+// heads of each tile (first pass)
+template <class K>
+__global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const K* __restrict__ keys, int ks, size_t cnt,
+                                                              K sentinel, uint32_t* __restrict__ heads) {
+    __shared__ uint32_t s_w[UQ_THREADS / 32];
+    const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
+    const size_t base = (size_t)blockIdx.x * UQ_TILE + (size_t)w * (UQ_ITEMS * 32);
+    K key[UQ_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
+        key[i] = idx < cnt ? (K)(keys[idx] >> ks) : sentinel;
+    }
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
+        K prev = __shfl_up_sync(0xffffffffu, key[i], 1);
+        if (l == 0) prev = (idx > 0 && idx < cnt) ? (K)(keys[idx - 1] >> ks) : sentinel;
+        run += (uint32_t)__popc(__ballot_sync(0xffffffffu, key[i] < sentinel && (idx == 0 || prev != key[i])));
+    }
+    if (l == 0) s_w[w] = run;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int ww = 0; ww < UQ_THREADS / 32; ++ww) t += s_w[ww];
+        heads[blockIdx.x] = t;
+    }
+}
+
+// second pass: tile t's heads get indices from first[t] on
 template <class K>
 __global__ void __launch_bounds__(UQ_THREADS, 4)
-    k_unique_lb(const K* __restrict__ keys, const uint32_t* __restrict__ vals, int wb, size_t cnt, K sentinel,
-                uint64_t div, int div_shift, uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out,
-                uint32_t* __restrict__ w_out, int cs, uint64_t* __restrict__ off_out, uint32_t nrows,
-                unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ total,
-                uint32_t* __restrict__ err) {
-    __shared__ uint32_t s_tile, s_woff[UQ_THREADS / 32], s_prefix;
+    k_unique_write(const K* __restrict__ keys, const uint32_t* __restrict__ vals, int wb, size_t cnt, K sentinel,
+                   uint64_t div, int div_shift, uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out,
+                   uint32_t* __restrict__ w_out, int cs, uint64_t* __restrict__ off_out, uint32_t nrows,
+                   const uint32_t* __restrict__ first) {
+    __shared__ uint32_t s_woff[UQ_THREADS / 32], s_prefix;
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x;
     const size_t base = (size_t)tile * UQ_TILE + (size_t)w * (UQ_ITEMS * 32);
     K key[UQ_ITEMS];
     uint32_t val[UQ_ITEMS];
@@ -574,44 +603,7 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
         }
         __syncwarp();
         if (l < UQ_THREADS / 32) s_woff[l] = my_off;
-        volatile unsigned long long* vst = status;
-        uint32_t excl = 0;
-        if (tile == 0) {
-            if (l == 0) vst[0] = OS_PRE | acc;
-        } else {
-            if (l == 0) vst[tile] = OS_AGG | acc;
-            // warp-wide look-back: lane j reads tile t - j, so 32 predecessors cost one round trip
-            const long long t0 = clock64();
-            long long t = (long long)tile - 1;
-            bool done = false;
-            while (!done) {
-                const long long idx = t - (long long)l;
-                unsigned long long sw = idx >= 0 ? (unsigned long long)vst[idx] : (unsigned long long)OS_PRE;
-                while ((sw & ~0xFFFFFFFFull) == 0) {
-                    if (clock64() - t0 > OS_WAIT_CYCLES) {
-                        atomicExch(err, 1u);
-                        sw = (unsigned long long)OS_PRE;
-                        break;
-                    }
-                    __nanosleep(32);
-                    sw = vst[idx];
-                }
-                const unsigned pre = __ballot_sync(0xffffffffu, (sw & ~0xFFFFFFFFull) == OS_PRE);
-                uint32_t v = (uint32_t)sw;
-                if (pre) {
-                    const unsigned first = __ffs(pre) - 1;
-                    if (l > first) v = 0;
-                    done = true;
-                }
-                excl += warp_sum(v);
-                t -= 32;
-            }
-            if (l == 0) vst[tile] = OS_PRE | (excl + acc);
-        }
-        if (l == 0) {
-            s_prefix = excl;
-            if ((size_t)(tile + 1) * UQ_TILE >= cnt) *total = excl + acc;  // the last tile knows the count
-        }
+        if (l == 0) s_prefix = first[tile];
     }
     __syncthreads();
     const uint32_t tbase = s_prefix + s_woff[w];
@@ -667,22 +659,20 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, int 
     }
     if (cnt > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "more than 2^32 - 1 items");
     const uint32_t ntiles = (uint32_t)((cnt + UQ_TILE - 1) / UQ_TILE);
-    DBuf<unsigned long long> status;
-    DBuf<uint32_t> ctl;
-    CLD_TRY(status.alloc(ntiles, s));
-    CLD_TRY(ctl.alloc(2, s));
-    CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * 8, s));
-    CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, 8, s));
-    CLD_K(K_CSR, s, k_unique_lb<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, wb, cnt, sentinel, div, div_shift,
-                                                                  row_out, col_out, w_out, cs, off_out, nrows,
-                                                                  status.get(), ctl.get(), total_dev, ctl.get() + 1));
+    DBuf<uint32_t> heads, first;
+    CLD_TRY(heads.alloc(ntiles, s));
+    CLD_TRY(first.alloc(ntiles, s));
+    CLD_K(K_CSR, s, k_unique_count<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals ? 0 : wb, cnt, sentinel, heads.get()));
     CLD_LAUNCH_CHECK();
-    uint32_t h[2] = {0, 0};
-    CLD_CUDA(cudaMemcpyAsync(&h[0], ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaMemcpyAsync(&h[1], total_dev, 4, cudaMemcpyDeviceToHost, s));
+    CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, total_dev, s));
+    CLD_K(K_CSR, s, k_unique_write<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, wb, cnt, sentinel, div, div_shift,
+                                                                     row_out, col_out, w_out, cs, off_out, nrows,
+                                                                     first.get()));
+    CLD_LAUNCH_CHECK();
+    uint32_t total = 0;
+    CLD_CUDA(cudaMemcpyAsync(&total, total_dev, 4, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
-    if (h[0]) return fail(CLDIAM_ERR_TIMEOUT, "unique look-back wait expired");
-    if (off_out && h[1] == 0) CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));  // no valid key
+    if (off_out && total == 0) CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));  // no valid key
     return CLDIAM_OK;
 }
 
