@@ -207,10 +207,10 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 
 // a5: one synchronous Delta-growing step over the frontier, edge-balanced:
 // the frontier's adjacency lists are viewed as one flattened range of E
-// entries cut into chunks of U x blockDim.x; each CTA takes chunks, and maps
-// each position of a chunk to its frontier entry by binary search over the
-// entries the chunk spans, held in shared memory, so hubs spread over many
-// CTAs.  With a chunk table (cfirst, chunks of RC) a chunk's entries come from
+// entries cut into chunks of U x blockDim.x; each CTA takes chunks, each warp
+// U x 32 consecutive positions of it, and maps every position to its
+// frontier entry from the entries the chunk spans, held in shared memory, so
+// hubs spread over many CTAs.  With a chunk table (cfirst, chunks of RC) a chunk's entries come from
 // two loads; without one, a block-wide search finds them.  The entries of the
 // next chunk are copied into the other shared buffer (cp.async) while the
 // current one is processed, so one barrier per chunk remains.  Every thread
@@ -280,17 +280,34 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
             range_of(nchunk, ni0, ncnt);
             stage(b ^ 1, ni0, ncnt);  // buffer b ^ 1 was last read before the previous barrier
         }
+        // owners of this warp's U x 32 consecutive positions: one binary search for the first, then
+        // per group of 32 the entries starting inside it are found with one OR-reduction (at most 32
+        // entries start in 32 positions, and they follow the previous group's last owner)
         uint32_t pos[U], own[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            pos[u] = e0 + tid + (uint32_t)u * nt;
-            // entry j >= 1 starts at or after e0 + j, so the owner of position r is <= r
-            uint32_t lo = 0, hi = min(cnt - 1, pos[u] - e0);
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (sm.pre[b][mid] <= pos[u]) lo = mid; else hi = mid - 1;
+        {
+            const uint32_t lane = lane_id();
+            const uint32_t wp0 = e0 + (tid >> 5) * 32u * U;
+            uint32_t B = 0;
+            if (wp0 < e1) {
+                // entry j >= 1 starts at or after e0 + j, so the owner of position r is <= r
+                uint32_t lo = 0, hi = min(cnt - 1, wp0 - e0);
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (sm.pre[b][mid] <= wp0) lo = mid; else hi = mid - 1;
+                }
+                B = lo;
             }
-            own[u] = lo;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t p0 = wp0 + 32u * u;
+                pos[u] = p0 + lane;
+                const uint32_t jj = B + 1 + lane;
+                const uint32_t pj = jj < cnt ? sm.pre[b][jj] : 0xFFFFFFFFu;
+                const uint32_t d = pj - p0;  // entries after B start at or after p0
+                const unsigned word = __reduce_or_sync(0xffffffffu, d < 32u ? 1u << d : 0u);
+                own[u] = B + (uint32_t)__popc(word & (0xffffffffu >> (31u - lane)));
+                B += (uint32_t)__popc(word);
+            }
         }
         uint2 ed[U];
 #pragma unroll
