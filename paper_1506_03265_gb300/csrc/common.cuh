@@ -73,11 +73,20 @@ struct DBuf {
     }
 };
 
-// Per-call small host<->device counter block in pinned memory.
+// Per-call small host<->device counter block in pinned memory.  Blocks of up
+// to kPinnedBlock bytes come from a process-wide free list of pinned slabs
+// (pinning and unpinning memory is slow and cudaFreeHost synchronises the
+// device); larger ones are pinned individually.
+constexpr size_t kPinnedBlock = 256;
+void* pinned_take();
+void pinned_give(void* p);
 struct Pinned {
     void* h = nullptr;
+    bool pooled = false;
     ~Pinned() {
-        if (h) cudaFreeHost(h);
+        if (!h) return;
+        if (pooled) pinned_give(h);
+        else cudaFreeHost(h);
     }
     cldiam_status alloc(size_t bytes);
 };

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -63,9 +64,39 @@ void dfree(void* p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+
+void* pinned_take() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr size_t kSlab = 256 * kPinnedBlock;  // slabs are never unpinned
+        void* slab = nullptr;
+        if (cudaHostAlloc(&slab, kSlab, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (size_t i = kSlab / kPinnedBlock; i-- > 0;) g_pin_free.push_back(static_cast<char*>(slab) + i * kPinnedBlock);
+    }
+    void* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pinned_give(void* p) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 cldiam_status Pinned::alloc(size_t bytes) {
     if (h) return CLDIAM_OK;
-    CLD_CUDA(cudaMallocHost(&h, bytes));
+    if (bytes <= kPinnedBlock) {
+        h = pinned_take();
+        if (!h) return fail(CLDIAM_ERR_OOM, "pinned host allocation failed");
+        pooled = true;
+    } else {
+        CLD_CUDA(cudaMallocHost(&h, bytes));
+    }
     memset(h, 0, bytes);
     return CLDIAM_OK;
 }
