@@ -6,9 +6,14 @@
 // Blocked FW with 64 x 64 tiles (Venkataraman, Sahni, Mukhopadhyaya): for
 // each pivot tile r, (1) close the diagonal tile, (2) update the tiles of
 // row r and column r through it, (3) update every other tile from its row-r
-// and column-r tiles.  Entries are uint32 with 0xFFFFFFFF = no path; a sum
-// of two finite entries that reaches 2^32 - 1 raises the overflow flag
-// instead of wrapping.
+// and column-r tiles.  Two arithmetic forms share the kernels: the checked
+// form keeps uint32 entries with 0xFFFFFFFF = no path, and a sum of two
+// finite entries that reaches 2^32 - 1 raises the overflow flag instead of
+// wrapping; the fast form uses 0x7FFFFFFF = no path, so a sum never wraps and
+// one fused add-min per relaxation suffices (a path that would reach
+// 0x7FFFFFFF stays "no path").  The fast form runs first; its result is
+// exact when every pair ends up connected, otherwise the checked form
+// recomputes the matrix.
 #include <algorithm>
 #include <mutex>
 
@@ -20,6 +25,7 @@ namespace cld {
 namespace {
 
 constexpr uint32_t INF = 0xFFFFFFFFu;
+constexpr uint32_t INFF = 0x7FFFFFFFu;  // "no path" of the fast form
 
 __device__ __forceinline__ uint32_t relax_min(uint32_t c, uint32_t a, uint32_t b, bool& ovf) {
     uint32_t s = a + b;
@@ -29,11 +35,18 @@ __device__ __forceinline__ uint32_t relax_min(uint32_t c, uint32_t a, uint32_t b
     return (carry | !finite) ? c : (s < c ? s : c);
 }
 
-__global__ void k_fw_init(uint32_t* __restrict__ M, uint32_t kp, uint32_t k) {
+// one relaxation c = min(c, a + b) in the form's arithmetic
+template <bool FAST>
+__device__ __forceinline__ uint32_t fw_relax(uint32_t c, uint32_t a, uint32_t b, bool& ovf) {
+    if constexpr (FAST) return __viaddmin_u32(a, b, c);
+    else return relax_min(c, a, b, ovf);
+}
+
+__global__ void k_fw_init(uint32_t* __restrict__ M, uint32_t kp, uint32_t k, uint32_t none) {
     size_t total = (size_t)kp * kp;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         uint32_t r = (uint32_t)(i / kp), c = (uint32_t)(i % kp);
-        M[i] = (r == c) ? 0u : INF;
+        M[i] = (r == c) ? 0u : none;
     }
 }
 
@@ -53,13 +66,18 @@ __global__ void k_fw_validate(const uint64_t* __restrict__ off, const uint32_t* 
     if (b) atomicExch(bad, 1u);
 }
 
+// edge weights into the matrix; a weight of 0x7FFFFFFF or more sets *wide (the fast form cannot hold it)
 __global__ void k_fw_scatter(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
-                             const uint32_t* __restrict__ w, uint32_t k, uint32_t kp, uint32_t* __restrict__ M) {
+                             const uint32_t* __restrict__ w, uint32_t k, uint32_t kp, uint32_t* __restrict__ M,
+                             uint32_t* __restrict__ wide) {
+    bool wd = false;
     for (uint32_t a = blockIdx.x; a < k; a += gridDim.x)
         for (uint64_t j = off[a] + threadIdx.x; j < off[a + 1]; j += blockDim.x) {
             uint32_t b = col[j];
+            wd |= w[j] >= INFF;
             if (b != a) atomicMin(&M[(size_t)a * kp + b], w[j]);
         }
+    if (wd && wide) atomicExch(wide, 1u);
 }
 
 // Tiles are T x T = 64 x 64; a CTA of 256 threads gives each thread a 4 x 4
@@ -86,6 +104,7 @@ __device__ __forceinline__ void fw_store_tile(uint32_t (*t)[FP], uint32_t* M, ui
 }
 
 // phase 1: the pivot tile against itself
+template <bool FAST>
 __global__ void __launch_bounds__(FTH) k_fw_phase1(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
                                                    uint32_t* __restrict__ ovf_flag) {
     __shared__ uint32_t t[FT][FP];
@@ -105,7 +124,7 @@ __global__ void __launch_bounds__(FTH) k_fw_phase1(uint32_t* __restrict__ M, uin
 #pragma unroll
             for (int j = 0; j < FQ; ++j) {
                 uint32_t& c = t[ty * FQ + i][tx * FQ + j];
-                c = relax_min(c, a[i], b[j], ovf);
+                c = fw_relax<FAST>(c, a[i], b[j], ovf);
             }
         __syncthreads();
     }
@@ -114,6 +133,7 @@ __global__ void __launch_bounds__(FTH) k_fw_phase1(uint32_t* __restrict__ M, uin
 }
 
 // phase 2: tiles in pivot row r (blockIdx.y == 0) and pivot column r (blockIdx.y == 1)
+template <bool FAST>
 __global__ void __launch_bounds__(FTH) k_fw_phase2(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
                                                    uint32_t* __restrict__ ovf_flag) {
     __shared__ uint32_t piv[FT][FP];
@@ -140,7 +160,7 @@ __global__ void __launch_bounds__(FTH) k_fw_phase2(uint32_t* __restrict__ M, uin
 #pragma unroll
             for (int j = 0; j < FQ; ++j) {
                 uint32_t& c = t[ty * FQ + i][tx * FQ + j];
-                c = relax_min(c, a[i], b[j], ovf);
+                c = fw_relax<FAST>(c, a[i], b[j], ovf);
             }
         __syncthreads();
     }
@@ -148,18 +168,21 @@ __global__ void __launch_bounds__(FTH) k_fw_phase2(uint32_t* __restrict__ M, uin
     if (ovf) atomicExch(ovf_flag, 1u);
 }
 
-// phase 3: every other tile from its pivot-column and pivot-row tiles; no barrier inside the p loop
+// phase 3: every other tile from its pivot-column and pivot-row tiles; no barrier inside the p loop.
+// The pivot-column tile is held transposed, so a thread reads its 4 rows of column p as one vector.
+constexpr int FA = FT + 4;  // padded row of the transposed tile, 16-byte aligned
+template <bool FAST>
 __global__ void __launch_bounds__(FTH) k_fw_phase3(uint32_t* __restrict__ M, uint32_t kp, uint32_t r,
                                                    uint32_t* __restrict__ ovf_flag) {
-    __shared__ uint32_t A[FT][FP];
+    __shared__ __align__(16) uint32_t At[FT][FA];
     __shared__ __align__(16) uint32_t B[FT][FT];
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     uint32_t ti = blockIdx.y, tj = blockIdx.x;
     if (ti >= r) ++ti;
     if (tj >= r) ++tj;
-    fw_load_tile(A, M, kp, ti, r);
     for (int i = threadIdx.x; i < FT * FT; i += FTH) {
         int y = i / FT, x = i % FT;
+        At[x][y] = M[((size_t)ti * FT + y) * kp + (size_t)r * FT + x];
         B[y][x] = M[((size_t)r * FT + y) * kp + (size_t)tj * FT + x];
     }
     uint32_t c[FQ][FQ];
@@ -170,33 +193,37 @@ __global__ void __launch_bounds__(FTH) k_fw_phase3(uint32_t* __restrict__ M, uin
     }
     __syncthreads();
     bool ovf = false;
-#pragma unroll 4
+#pragma unroll 8
     for (int p = 0; p < FT; ++p) {
-        uint32_t a[FQ];
-#pragma unroll
-        for (int q = 0; q < FQ; ++q) a[q] = A[ty * FQ + q][p];
+        const uint4 av = *reinterpret_cast<const uint4*>(&At[p][ty * FQ]);
         const uint4 bv = *reinterpret_cast<const uint4*>(&B[p][tx * FQ]);
+        const uint32_t a[FQ] = {av.x, av.y, av.z, av.w};
         const uint32_t b[FQ] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
         for (int i = 0; i < FQ; ++i)
 #pragma unroll
-            for (int j = 0; j < FQ; ++j) c[i][j] = relax_min(c[i][j], a[i], b[j], ovf);
+            for (int j = 0; j < FQ; ++j) c[i][j] = fw_relax<FAST>(c[i][j], a[i], b[j], ovf);
     }
 #pragma unroll
     for (int i = 0; i < FQ; ++i)
         *reinterpret_cast<uint4*>(&M[((size_t)ti * FT + ty * FQ + i) * kp + (size_t)tj * FT + tx * FQ]) =
             make_uint4(c[i][0], c[i][1], c[i][2], c[i][3]);
-    if (ovf) atomicExch(ovf_flag, 1u);
+    if (!FAST && ovf) atomicExch(ovf_flag, 1u);
 }
 
-__global__ void k_fw_max_finite(const uint32_t* __restrict__ M, uint32_t kp, uint32_t k, uint32_t* __restrict__ out) {
+// largest entry below `none` among the k x k real entries; *missing = 1 if some entry is `none`
+__global__ void k_fw_max_finite(const uint32_t* __restrict__ M, uint32_t kp, uint32_t k, uint32_t none,
+                                uint32_t* __restrict__ out, uint32_t* __restrict__ missing) {
     uint32_t m = 0;
+    bool miss = false;
     size_t total = (size_t)k * kp;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         uint32_t c = (uint32_t)(i % kp);
         uint32_t v = M[i];
-        if (c < k && v != INF && v > m) m = v;
+        if (c < k && v != none && v > m) m = v;
+        miss |= c < k && v == none;
     }
+    if (missing && __any_sync(0xffffffffu, miss) && lane_id() == 0) atomicExch(missing, 1u);
     m = block_reduce(m, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u);
     if (threadIdx.x == 0) atomicMax(out, m);
 }
@@ -303,6 +330,31 @@ cldiam_status launch_msbf(uint32_t k, const uint64_t* off, const uint32_t* col, 
     return CLDIAM_OK;
 }
 
+// Blocked Floyd-Warshall over the padded kp x kp matrix M in the given form; scal[0] = overflow
+// (checked form), scal[1] = largest finite distance, scal[3] = wide weight, scal[4] = unconnected pair.
+template <bool FAST>
+cldiam_status fw_dense(uint32_t* M, uint32_t kp, uint32_t k, uint32_t nt, const uint64_t* off, const uint32_t* col,
+                       const uint32_t* w, uint32_t* scal, cudaStream_t s) {
+    const uint32_t none = FAST ? INFF : INF;
+    CLD_K(K_FW, s, k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M, kp, k, none));
+    CLD_K(K_FW, s, k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M, FAST ? scal + 3 : nullptr));
+    CLD_LAUNCH_CHECK();
+    for (uint32_t r = 0; r < nt; ++r) {
+        CLD_K(K_FW, s, k_fw_phase1<FAST><<<1, FTH, 0, s>>>(M, kp, r, scal));
+        if (nt > 1) {
+            CLD_K(K_FW, s, k_fw_phase2<FAST><<<dim3(nt - 1, 2), FTH, 0, s>>>(M, kp, r, scal));
+            CLD_K(K_FW, s, k_fw_phase3<FAST><<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M, kp, r, scal));
+        }
+        CLD_LAUNCH_CHECK();
+    }
+    CLD_K(K_FW, s, k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M, kp, k, none, scal + 1,
+                                                                                  FAST ? scal + 4 : nullptr));
+    CLD_LAUNCH_CHECK();
+    // algorithmic work: k^3 relaxations; bytes: the matrix read and written once per pivot round
+    prof_add_bytes(K_FW, 2.0 * 4.0 * (double)kp * kp * nt);
+    return CLDIAM_OK;
+}
+
 }  // namespace
 
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
@@ -312,8 +364,8 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     const uint32_t nt = (k + FT - 1) / FT;
     const uint32_t kp = nt * FT;
     DBuf<uint32_t> M, scal;
-    CLD_TRY(scal.alloc(3, s));
-    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 12, s));
+    CLD_TRY(scal.alloc(5, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 20, s));
     if (validate) {
         CLD_K(K_FW, s, k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, scal.get() + 2));
         CLD_LAUNCH_CHECK();
@@ -335,19 +387,16 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     } else {
         if (k > max_fw_k) return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient larger than max_fw_k");
         CLD_TRY(M.alloc((size_t)kp * kp, s));
-        CLD_K(K_FW, s, k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M.get(), kp, k));
-        CLD_K(K_FW, s, k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M.get()));
-        CLD_LAUNCH_CHECK();
-        for (uint32_t r = 0; r < nt; ++r) {
-            CLD_K(K_FW, s, k_fw_phase1<<<1, FTH, 0, s>>>(M.get(), kp, r, scal.get()));
-            if (nt > 1) {
-                CLD_K(K_FW, s, k_fw_phase2<<<dim3(nt - 1, 2), FTH, 0, s>>>(M.get(), kp, r, scal.get()));
-                CLD_K(K_FW, s, k_fw_phase3<<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M.get(), kp, r, scal.get()));
-            }
-            CLD_LAUNCH_CHECK();
+        // fast form first (scal[3] = a weight too wide for it, scal[4] = some pair left unconnected)
+        CLD_TRY(fw_dense<true>(M.get(), kp, k, nt, off, col, w, scal.get(), s));
+        uint32_t hf[5];
+        CLD_CUDA(cudaMemcpyAsync(hf, scal.get(), 20, cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        if (hf[3] || hf[4]) {
+            // disconnected pairs, or distances the fast form cannot hold: recompute with the checked form
+            CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8, s));
+            CLD_TRY(fw_dense<false>(M.get(), kp, k, nt, off, col, w, scal.get(), s));
         }
-        CLD_K(K_FW, s, k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M.get(), kp, k, scal.get() + 1));
-        CLD_LAUNCH_CHECK();
     }
     uint32_t h[2];
     CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 8, cudaMemcpyDeviceToHost, s));
@@ -424,18 +473,18 @@ cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* 
         const uint32_t nt = (k + FT - 1) / FT;
         const uint32_t kp = nt * FT;  // <= kNoAllocMaxK
         uint32_t* M = scratch + kNoAllocCtlWords;
-        k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M, kp, k);
-        k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M);
+        k_fw_init<<<grid_for((size_t)kp * kp, 256), 256, 0, s>>>(M, kp, k, INF);
+        k_fw_scatter<<<grid_for(k, 1, 64), 128, 0, s>>>(off, col, w, k, kp, M, nullptr);
         CLD_LAUNCH_CHECK();
         for (uint32_t r = 0; r < nt; ++r) {
-            k_fw_phase1<<<1, FTH, 0, s>>>(M, kp, r, ovf);
+            k_fw_phase1<false><<<1, FTH, 0, s>>>(M, kp, r, ovf);
             if (nt > 1) {
-                k_fw_phase2<<<dim3(nt - 1, 2), FTH, 0, s>>>(M, kp, r, ovf);
-                k_fw_phase3<<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M, kp, r, ovf);
+                k_fw_phase2<false><<<dim3(nt - 1, 2), FTH, 0, s>>>(M, kp, r, ovf);
+                k_fw_phase3<false><<<dim3(nt - 1, nt - 1), FTH, 0, s>>>(M, kp, r, ovf);
             }
             CLD_LAUNCH_CHECK();
         }
-        k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M, kp, k, best);
+        k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M, kp, k, INF, best, nullptr);
         CLD_LAUNCH_CHECK();
     }
     CLD_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -18,11 +18,17 @@ namespace {
 
 constexpr uint32_t kDenseQuotientK = 4096;  // k x k uint32 = 64 MB, within the 126 MB L2
 
+// (cid, D) of every node in one word, so an edge's far end costs one gather
+__global__ void k_q_pack_cd(uint32_t n, const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D,
+                            uint2* __restrict__ cd) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        cd[v] = make_uint2(cid[v], D[v]);
+}
+
 template <class K>
 __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
-                         const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D, uint32_t k,
-                         K* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ count,
-                         uint32_t* __restrict__ overflow) {
+                         const uint2* __restrict__ cd, uint32_t k, K* __restrict__ keys, uint32_t* __restrict__ vals,
+                         uint32_t* __restrict__ count, uint32_t* __restrict__ overflow) {
     __shared__ uint32_t scratch[33];
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < nnz; base += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t i = base + threadIdx.x;
@@ -32,9 +38,10 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
         if (i < nnz) {
             uint32_t u = row[i];
             uint2 e = adj[i];
-            uint32_t a = cid[u], b = cid[e.x];
+            const uint2 pu = cd[u], pv = cd[e.x];
+            uint32_t a = pu.x, b = pv.x;
             if (a != b) {
-                uint64_t s = (uint64_t)D[u] + e.y + D[e.x];
+                uint64_t s = (uint64_t)pu.y + e.y + pv.y;
                 if (s >= 0xFFFFFFFFull) {
                     atomicExch(overflow, 1u);
                     s = 0xFFFFFFFEull;
@@ -57,16 +64,17 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
 // (an edge's weight D_u + w + D_v does not depend on its direction), so each undirected edge is
 // folded once, from its u < v entry, into the upper triangle, which is then mirrored.
 __global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
-                               const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D, uint32_t k,
-                               uint32_t* __restrict__ M, uint32_t* __restrict__ overflow) {
+                               const uint2* __restrict__ cd, uint32_t k, uint32_t* __restrict__ M,
+                               uint32_t* __restrict__ overflow) {
     bool ovf = false;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t u = row[i];
         const uint2 e = adj[i];
         if (u >= e.x) continue;
-        const uint32_t a = cid[u], b = cid[e.x];
+        const uint2 pu = cd[u], pv = cd[e.x];
+        const uint32_t a = pu.x, b = pv.x;
         if (a == b) continue;
-        uint64_t s = (uint64_t)D[u] + e.y + D[e.x];
+        uint64_t s = (uint64_t)pu.y + e.y + pv.y;
         if (s >= 0xFFFFFFFFull) {
             ovf = true;
             s = 0xFFFFFFFEull;
@@ -143,8 +151,11 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
     CLD_CUDA(cudaMemsetAsync(M.get(), 0xFF, (size_t)k * k * 4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8, s));
     if (g->nnz) {
-        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, c->cid, c->D,
-                                                                                k, M.get(), scal.get()));
+        DBuf<uint2> cd;
+        CLD_TRY(cd.alloc(g->n, s));
+        CLD_K(K_QUOTIENT, s, k_q_pack_cd<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, c->cid, c->D, cd.get()));
+        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, cd.get(), k,
+                                                                                M.get(), scal.get()));
         CLD_LAUNCH_CHECK();
     }
     {
@@ -194,8 +205,12 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     CLD_TRY(scal.alloc(4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 16, s));
     if (g->nnz) {
-        CLD_K(K_QUOTIENT, s, k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, c->cid, c->D, k, keys.get(),
-                                                          vals.get(), scal.get(), scal.get() + 1));
+        DBuf<uint2> cd;
+        CLD_TRY(cd.alloc(g->n, s));
+        CLD_K(K_QUOTIENT, s, k_q_pack_cd<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, c->cid, c->D, cd.get()));
+        CLD_K(K_QUOTIENT, s, k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, cd.get(), k,
+                                                                              keys.get(), vals.get(), scal.get(),
+                                                                              scal.get() + 1));
         CLD_LAUNCH_CHECK();
     }
     CLD_CUDA(cudaMemcpyAsync(hh, scal.get(), 8, cudaMemcpyDeviceToHost, s));
