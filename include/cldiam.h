@@ -33,6 +33,9 @@
  *    paper's positive integral weights, Section 2).  Distances inside the
  *    library are exact uint32; a distance or quotient weight that would
  *    reach 2^32 - 1 yields CLDIAM_ERR_OVERFLOW instead of a wrong answer.
+ *    The quotient diameter is exact whenever every quotient distance is
+ *    below 2^31 - 1; beyond that, a candidate path sum that reaches 2^32 - 1
+ *    is reported as CLDIAM_ERR_OVERFLOW even if the shortest distances fit.
  *  - Threads: one handle must not be used by two threads at once.
  */
 #ifndef CLDIAM_H
@@ -186,7 +189,9 @@ cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out);
  * symmetric CSR (k nodes, off[k+1], col/w[nnz]; host or device), exact, on the
  * device: batched SSSP for sparse graphs, blocked Floyd-Warshall (k <= 8192,
  * with a k x k scratch matrix) for dense ones; used for Phi(G_C).  The CSR is
- * validated on the device first.  *phi is a host pointer.
+ * validated on the device first.  *phi is a host pointer.  Exact when every
+ * distance is below 2^31 - 1; above, OVERFLOW if a candidate path sum reaches
+ * 2^32 - 1 (see the integer rules at the top).
  * Errors: INVALID_ARG (malformed CSR), OVERFLOW, UNSUPPORTED, OOM, CUDA.
  */
 cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,

@@ -330,6 +330,122 @@ cldiam_status launch_msbf(uint32_t k, const uint64_t* off, const uint32_t* col, 
     return CLDIAM_OK;
 }
 
+// Batched exact SSSP on the quotient with a worklist (multi-source Bellman-Ford
+// that only pushes from changed nodes): a CTA owns S consecutive sources and
+// keeps dist[v][s] for all k nodes in shared memory, plus one word of change
+// bits per node (bit s: dist[v][s] decreased).  In each round one warp per
+// node v with change bits pushes dist[v][s] + w(v, u) to every neighbour u
+// (lanes = neighbours) with a shared-memory atomicMin for each changed
+// source s, and marks u for the next round when that lowers dist[u][s].
+// Distances only ever decrease and stay lengths of real paths, so when no
+// node is marked they are exact; the work is the number of distance
+// decreases times the degree, instead of rounds x entries, which wins on
+// quotients with many rounds (high hop diameter).
+template <int S, bool kCsrInSmem>
+__global__ void __launch_bounds__(1024) k_apsp_wl(const uint64_t* __restrict__ goff, const uint32_t* __restrict__ gcol,
+                                                  const uint32_t* __restrict__ gw, uint32_t k, uint32_t nnz,
+                                                  uint32_t* __restrict__ out_max, uint32_t* __restrict__ ovf_flag,
+                                                  uint32_t* __restrict__ err) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t* dist = sm;                   // k x S
+    uint32_t* chg0 = sm + (size_t)k * S;   // change bits, two rounds
+    uint32_t* chg1 = chg0 + k;
+    uint32_t* soff = chg1 + k;
+    uint32_t* scol = soff + (k + 1);
+    uint32_t* sw = scol + nnz;
+    const uint32_t s0 = blockIdx.x * S;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id(), nwarps = blockDim.x >> 5;
+    for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x) {
+        const uint32_t v = i / S, s = i % S;
+        dist[i] = (s0 + s == v) ? 0u : INF;
+    }
+    for (uint32_t v = threadIdx.x; v < k; v += blockDim.x) {
+        chg0[v] = (v >= s0 && v < s0 + S) ? 1u << (v - s0) : 0u;
+        chg1[v] = 0;
+    }
+    if (kCsrInSmem) {
+        for (uint32_t i = threadIdx.x; i <= k; i += blockDim.x) soff[i] = (uint32_t)goff[i];
+        for (uint32_t i = threadIdx.x; i < nnz; i += blockDim.x) {
+            scol[i] = gcol[i];
+            sw[i] = gw[i];
+        }
+    }
+    bool ovf = false;
+    __syncthreads();
+    const uint32_t max_rounds = 4 * k + 64;  // far above any real count: a guard, reported as an error
+    uint32_t round = 0;
+    for (;; ++round) {
+        uint32_t* cur = (round & 1) ? chg1 : chg0;
+        uint32_t* nxt = (round & 1) ? chg0 : chg1;
+        for (uint32_t v = warp; v < k; v += nwarps) {
+            const uint32_t bits = cur[v];
+            if (!bits) continue;
+            const uint32_t beg = kCsrInSmem ? soff[v] : (uint32_t)goff[v];
+            const uint32_t end = kCsrInSmem ? soff[v + 1] : (uint32_t)goff[v + 1];
+            for (uint32_t j = beg + lane; j < end; j += 32) {
+                const uint32_t u = kCsrInSmem ? scol[j] : gcol[j];
+                const uint32_t wj = kCsrInSmem ? sw[j] : gw[j];
+                for (uint32_t b = bits; b; b &= b - 1) {
+                    const uint32_t sidx = (uint32_t)__ffs(b) - 1;
+                    const uint32_t dv = dist[v * S + sidx];
+                    if (dv == INF) continue;
+                    const uint64_t nd = (uint64_t)dv + wj;
+                    if (nd >= INF) {
+                        ovf = true;
+                        continue;
+                    }
+                    uint32_t* du = &dist[u * S + sidx];
+                    if ((uint32_t)nd < *du && (uint32_t)nd < atomicMin(du, (uint32_t)nd))
+                        atomicOr(&nxt[u], 1u << sidx);
+                }
+            }
+        }
+        __syncthreads();
+        bool any = false;
+        for (uint32_t v = threadIdx.x; v < k; v += blockDim.x) {
+            cur[v] = 0;
+            any |= nxt[v] != 0;
+        }
+        if (!__syncthreads_or(any)) break;
+        if (round >= max_rounds) {
+            if (threadIdx.x == 0) atomicExch(err, 1u);
+            break;
+        }
+    }
+    uint32_t best = 0;
+    for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x)
+        if (s0 + i % S < k && dist[i] != INF && dist[i] > best) best = dist[i];
+    best = block_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u);
+    if (threadIdx.x == 0) atomicMax(out_max, best);
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicExch(ovf_flag, 1u);
+}
+
+template <int S>
+cldiam_status launch_wl(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
+                        cudaStream_t s, uint32_t* out_max, uint32_t* ovf, uint32_t* err) {
+    constexpr int kMax = 220 * 1024;
+    static bool attr[64];
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k_apsp_wl<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax));
+        CLD_CUDA(cudaFuncSetAttribute(k_apsp_wl<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax));
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    const size_t dist_bytes = (size_t)k * S * 4 + (size_t)k * 8;
+    const size_t csr_bytes = ((size_t)k + 1 + 2 * nnz) * 4;
+    const unsigned grid = (k + S - 1) / S;
+    if (dist_bytes + csr_bytes <= (size_t)kMax) {
+        CLD_K(K_FW, s, k_apsp_wl<S, true><<<grid, 1024, dist_bytes + csr_bytes, s>>>(off, col, w, k, (uint32_t)nnz,
+                                                                                   out_max, ovf, err));
+    } else {
+        CLD_K(K_FW, s, k_apsp_wl<S, false><<<grid, 1024, dist_bytes, s>>>(off, col, w, k, (uint32_t)nnz, out_max, ovf,
+                                                                          err));
+    }
+    CLD_LAUNCH_CHECK();
+    return CLDIAM_OK;
+}
+
 // Blocked Floyd-Warshall over the padded kp x kp matrix M in the given form; scal[0] = overflow
 // (checked form), scal[1] = largest finite distance, scal[3] = wide weight, scal[4] = unconnected pair.
 template <bool FAST>
@@ -364,8 +480,8 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     const uint32_t nt = (k + FT - 1) / FT;
     const uint32_t kp = nt * FT;
     DBuf<uint32_t> M, scal;
-    CLD_TRY(scal.alloc(5, s));
-    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 20, s));
+    CLD_TRY(scal.alloc(6, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 24, s));
     if (validate) {
         CLD_K(K_FW, s, k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, scal.get() + 2));
         CLD_LAUNCH_CHECK();
@@ -375,14 +491,17 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
         if (bad) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
     }
     // sparse quotient (fewer than k^2 / 8 entries): batched SSSP, S sources per CTA with
-    // k x S distances in shared memory (S = 8 while it fits in 200 KB)
+    // k x S distances (and one word of change bits per node) in shared memory, S = 8 while it fits
     constexpr size_t kSmem = 220 * 1024;
     const bool sparse = (double)nnz * 8.0 < (double)k * k;
-    if (sparse && (size_t)k * 8 * 4 <= kSmem) {
-        CLD_TRY(launch_msbf<8>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
-    } else if (sparse && (size_t)k * 4 * 4 <= kSmem) {
-        CLD_TRY(launch_msbf<4>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
+    if (sparse && (size_t)k * (8 * 4 + 8) <= kSmem) {
+        CLD_TRY(launch_wl<8>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
+    } else if (sparse && (size_t)k * (4 * 4 + 8) <= kSmem) {
+        CLD_TRY(launch_wl<4>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
+    } else if (sparse && (size_t)k * (4 + 8) <= kSmem) {
+        CLD_TRY(launch_wl<1>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
     } else if (sparse && (size_t)k * 4 <= kSmem) {
+        // too many nodes for the change bits: all-node rounds, distances alone in shared memory
         CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
     } else {
         if (k > max_fw_k) return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient larger than max_fw_k");
@@ -398,9 +517,10 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
             CLD_TRY(fw_dense<false>(M.get(), kp, k, nt, off, col, w, scal.get(), s));
         }
     }
-    uint32_t h[2];
-    CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 8, cudaMemcpyDeviceToHost, s));
+    uint32_t h[6];
+    CLD_CUDA(cudaMemcpyAsync(h, scal.get(), 24, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
+    if (h[5]) return fail(CLDIAM_ERR_DIVERGED, "quotient SSSP exceeded its round limit");
     if (h[0]) return fail(CLDIAM_ERR_OVERFLOW, "a quotient distance reached 2^32 - 1");
     *phi = h[1];
     return CLDIAM_OK;

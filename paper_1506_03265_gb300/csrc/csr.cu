@@ -40,37 +40,28 @@ __global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t
     }
 }
 
-// input check (ids < n, weights >= 1) and the largest weight
-__global__ void k_check_inputs(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
-                               const uint32_t* __restrict__ w, uint64_t m, uint32_t n, uint32_t* __restrict__ bad,
-                               uint32_t* __restrict__ wmax) {
-    bool b = false;
-    uint32_t mx = 0;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t ww = w[e];
-        b |= src[e] >= n || dst[e] >= n || ww == 0;
-        mx = max(mx, ww);
-    }
-    if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
-    mx = warp_max(mx);
-    if (lane_id() == 0 && mx) atomicMax(wmax, mx);
-}
-
-// both directions of every edge as packed items; a self-loop becomes ~0 (skipped, sorts last)
+// both directions of every edge as packed items (row << vb | col) << wb | w; a self-loop becomes ~0
+// (skipped, sorts last).  Also the input check (ids < n, weights >= 1 -> *bad) and whether a weight
+// needs more than wb bits (*wide: the caller falls back to (key, weight) pairs).
 __global__ void k_emit_packed(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
-                              const uint32_t* __restrict__ w, uint64_t m, int vb, int wb, uint64_t* __restrict__ items) {
+                              const uint32_t* __restrict__ w, uint64_t m, uint32_t n, int vb, int wb,
+                              uint64_t* __restrict__ items, uint32_t* __restrict__ bad, uint32_t* __restrict__ wide) {
+    bool b = false, wd = false;
+    const uint64_t wlim = wb >= 32 ? ~0ull : (1ull << wb);
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t u = src[e], v = dst[e], ww = w[e];
-        uint2 lo, hi;
+        b |= u >= n || v >= n || ww == 0;
+        wd |= ww >= wlim;
         uint64_t i0 = ~0ull, i1 = ~0ull;
         if (u != v) {
             i0 = (((u << vb) | v) << wb) | ww;
             i1 = (((v << vb) | u) << wb) | ww;
         }
-        lo = make_uint2((uint32_t)i0, (uint32_t)(i0 >> 32));
-        hi = make_uint2((uint32_t)i1, (uint32_t)(i1 >> 32));
-        reinterpret_cast<uint4*>(items)[e] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        reinterpret_cast<uint4*>(items)[e] =
+            make_uint4((uint32_t)i0, (uint32_t)(i0 >> 32), (uint32_t)i1, (uint32_t)(i1 >> 32));
     }
+    if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
+    if (__any_sync(0xffffffffu, wd) && lane_id() == 0) atomicExch(wide, 1u);
 }
 
 __global__ void k_widen_offsets(const uint32_t* __restrict__ excl, uint32_t n, uint32_t total, uint64_t* __restrict__ off) {
@@ -142,7 +133,26 @@ __global__ void k_cc_compress(uint32_t* __restrict__ parent, uint32_t n) {
     }
 }
 
-__global__ void k_cc_count(const uint32_t* __restrict__ parent, uint32_t n, uint32_t* __restrict__ size) {
+// size of the sampled dominant tree; when it holds more than half of the nodes it is the largest
+// component and the per-root counts below are skipped
+__global__ void k_cc_size_of(const uint32_t* __restrict__ parent, uint32_t n, uint32_t giant,
+                             uint32_t* __restrict__ count) {
+    uint32_t c = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += parent[v] == giant;
+    c = block_reduce(c, [](uint32_t a, uint32_t b) { return a + b; }, 0u);
+    if (threadIdx.x == 0 && c) atomicAdd(count, c);
+}
+__device__ __forceinline__ bool giant_is_largest(const uint32_t* count, uint32_t n) {
+    return count && 2ull * *count > n;
+}
+__global__ void k_cc_giant_best(const uint32_t* __restrict__ count, uint32_t n, uint32_t giant,
+                                unsigned long long* __restrict__ best) {
+    if (giant_is_largest(count, n)) *best = ((unsigned long long)*count << 32) | (unsigned long long)(0xFFFFFFFFu - giant);
+}
+
+__global__ void k_cc_count(const uint32_t* __restrict__ parent, uint32_t n, uint32_t* __restrict__ size,
+                           const uint32_t* __restrict__ gcount) {
+    if (giant_is_largest(gcount, n)) return;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
         const uint32_t r = v < n ? parent[v] : 0xFFFFFFFFu;
@@ -154,7 +164,8 @@ __global__ void k_cc_count(const uint32_t* __restrict__ parent, uint32_t n, uint
 
 // best component: largest size, then smallest root id
 __global__ void k_cc_best(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ size, uint32_t n,
-                          unsigned long long* __restrict__ best) {
+                          unsigned long long* __restrict__ best, const uint32_t* __restrict__ gcount) {
+    if (giant_is_largest(gcount, n)) return;
     unsigned long long b = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
         if (parent[v] == v) {
@@ -292,23 +303,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
     InFree f3{&dw, &ow, s};
 
-    // input check and the weight range
+    // items: packed words when the weight fits in the bits the two ids leave, else (key, weight) pairs
     const uint64_t cnt = 2 * m;
     DBuf<uint32_t> scal;
     CLD_TRY(scal.alloc(8, s));
     CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(uint32_t), s));
-    if (m > 0) {
-        CLD_K(K_CSR, s, k_check_inputs<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
-                                                                       (const uint32_t*)dw, m, n, scal.get(),
-                                                                       scal.get() + 2));
-        CLD_LAUNCH_CHECK();
-    }
-    CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaStreamSynchronize(s));
-    if (*hbad) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
     const int vb = std::max(1, bits_for((uint64_t)n - 1));
-    const int wb = std::max(1, bits_for(hbad[2]));
-    const bool packed = 2 * vb + wb <= 64;
+    const int wb = 64 - 2 * vb;  // weight bits of a packed item
 
     DBuf<uint32_t> row, deg, degx;
     DBuf<uint64_t> off;
@@ -319,21 +320,30 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(degx.alloc((size_t)n + 1, s));
     CLD_TRY(off.alloc((size_t)n + 1, s));
     CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));
+    bool packed = wb >= 1;
     if (packed) {
         DBuf<uint64_t> items, items2;
         CLD_TRY(items.alloc(cnt ? cnt : 1, s));
-        CLD_TRY(items2.alloc(cnt ? cnt : 1, s));
         if (m > 0) {
             CLD_K(K_CSR, s, k_emit_packed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
-                                                                          (const uint32_t*)dw, m, vb, wb, items.get()));
+                                                                          (const uint32_t*)dw, m, n, vb, wb,
+                                                                          items.get(), scal.get(), scal.get() + 2));
             CLD_LAUNCH_CHECK();
         }
-        bool alt = false;
-        CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s));
-        // unique (row, col) runs with their lightest weight, in one look-back pass
-        CLD_TRY(unique_min_packed_u64(alt ? items2.get() : items.get(), wb, cnt, vb, row.get(), &adj.get()->x,
-                                      &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
-    } else {
+        CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        if (hbad[0]) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
+        packed = hbad[2] == 0;
+        if (packed) {
+            CLD_TRY(items2.alloc(cnt ? cnt : 1, s));
+            bool alt = false;
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s));
+            // unique (row, col) runs with their lightest weight, in one look-back pass
+            CLD_TRY(unique_min_packed_u64(alt ? items2.get() : items.get(), wb, cnt, vb, row.get(), &adj.get()->x,
+                                          &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
+        }
+    }
+    if (!packed) {
         // keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
         const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
         DBuf<uint64_t> keys, keys2;
@@ -349,6 +359,9 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                                                             scal.get()));
             CLD_LAUNCH_CHECK();
         }
+        CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        if (hbad[0]) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
         bool alt = false;
         CLD_TRY(radix_sort_pairs_u64(keys.get(), vals.get(), keys2.get(), vals2.get(), cnt, bits_for(sentinel), &alt,
                                      s));
@@ -406,13 +419,20 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                                                             giant, parent.get()));
             CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
             CLD_LAUNCH_CHECK();
+            CLD_CUDA(cudaMemsetAsync(scal.get() + 3, 0, 4, s));
+            CLD_K(K_CC, s, k_cc_size_of<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, giant, scal.get() + 3));
+            CLD_CUDA(cudaMemsetAsync(best.get(), 0, 8, s));
+            CLD_K(K_CC, s, k_cc_giant_best<<<1, 1, 0, s>>>(scal.get() + 3, n, giant, best.get()));
+            CLD_LAUNCH_CHECK();
+        } else {
+            CLD_CUDA(cudaMemsetAsync(best.get(), 0, 8, s));
         }
         CLD_TRY(size.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(size.get(), 0, (size_t)n * 4, s));
-        CLD_CUDA(cudaMemsetAsync(best.get(), 0, 8, s));
-        CLD_K(K_CC, s, k_cc_count<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, size.get()));
+        const uint32_t* gcount = nnz > 0 ? scal.get() + 3 : nullptr;
+        CLD_K(K_CC, s, k_cc_count<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, size.get(), gcount));
         CLD_LAUNCH_CHECK();
-        CLD_K(K_CC, s, k_cc_best<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), size.get(), n, best.get()));
+        CLD_K(K_CC, s, k_cc_best<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), size.get(), n, best.get(), gcount));
         CLD_LAUNCH_CHECK();
         CLD_TRY(keep.alloc(n, s));
         CLD_TRY(newid.alloc(n, s));

@@ -214,6 +214,64 @@ def test_apsp_dense_floyd_warshall(cd, k):
     assert cd.apsp_max(og.n, og.off, og.col, og.wt) == oracle.apsp_max(q)
 
 
+def _dense(k, seed, lo, hi, blocks=1):
+    # dense random graph on k nodes (>= k^2/8 entries), optionally split into disconnected blocks
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(k, 1)
+    keep = rng.random(iu[0].size) < 0.6
+    if blocks > 1:
+        keep &= (iu[0] * blocks // k) == (iu[1] * blocks // k)
+    s, d = iu[0][keep].astype(np.uint32), iu[1][keep].astype(np.uint32)
+    w = rng.integers(lo, hi, s.size, dtype=np.uint64, endpoint=True).astype(np.uint32)
+    og = oracle.build_csr(k, s, d, w, lcc=False)
+    q = oracle.Quotient(og.n, np.arange(og.n, dtype=np.uint32), og.off, og.col, og.wt.astype(np.uint64))
+    return og, q
+
+
+@pytest.mark.parametrize("k,blocks,lo,hi", [
+    (150, 2, 1, 1 << 20),                      # disconnected: the fast form leaves pairs unconnected
+    (140, 1, 1 << 30, 0x7FFFFFFE),             # distances past 2^31 - 1: the fast form cannot hold them
+    (130, 1, 0x7FFFFFFF, 0x7FFFFFFF + 100),    # weights the fast form cannot hold at all
+])
+def test_apsp_dense_checked_form(cd, k, blocks, lo, hi):
+    # the fast Floyd-Warshall form must hand over to the checked form, which is exact or refuses:
+    # exact whenever every distance is below 2^31 - 1 or no candidate sum reaches 2^32 - 1; a
+    # candidate sum that reaches 2^32 - 1 is reported as OVERFLOW (never a wrapped value)
+    og, q = _dense(k, k + blocks, lo, hi, blocks)
+    assert og.nnz * 8 >= k * k
+    ref = oracle.apsp_max(q)
+    try:
+        got = cd.apsp_max(og.n, og.off, og.col, og.wt)
+    except cd.CldiamError as ex:
+        assert ex.status == -3 and ref >= 0x7FFFFFFF, (ex, hex(ref))
+        return
+    assert got == ref
+    if blocks > 1:
+        assert ref < 0x7FFFFFFF  # the disconnected case is answered exactly
+
+
+def test_apsp_dense_overflow_reported(cd):
+    # chain-like dense graph whose diameter exceeds 2^32 - 1: OVERFLOW, never a wrapped value
+    k = 70
+    s = np.arange(k - 1, dtype=np.uint32); d = s + 1
+    w = np.full(k - 1, 0x10000000, np.uint32)  # 69 x 2^28 > 2^32
+    rng = np.random.default_rng(3)
+    iu = np.triu_indices(k, 2)
+    keep = rng.random(iu[0].size) < 0.3
+    s = np.concatenate([s, iu[0][keep].astype(np.uint32)]); d = np.concatenate([d, iu[1][keep].astype(np.uint32)])
+    w = np.concatenate([w, np.full(int(keep.sum()), 0xFFFFFFF0, np.uint32)])
+    og = oracle.build_csr(k, s, d, w, lcc=False)
+    assert og.nnz * 8 >= k * k
+    q = oracle.Quotient(og.n, np.arange(og.n, dtype=np.uint32), og.off, og.col, og.wt.astype(np.uint64))
+    ref = oracle.apsp_max(q)
+    if ref >= 0xFFFFFFFF:
+        with pytest.raises(cd.CldiamError) as ei:
+            cd.apsp_max(og.n, og.off, og.col, og.wt)
+        assert ei.value.status == -3
+    else:
+        assert cd.apsp_max(og.n, og.off, og.col, og.wt) == ref
+
+
 @pytest.mark.parametrize("k,density,seed", [(3000, 0.002, 6), (2500, 0.003, 7), (700, 0.01, 5)])
 def test_apsp_sparse_batched_sssp(cd, k, density, seed):
     # sparse graphs (possibly disconnected) take the multi-source Bellman-Ford path; many rounds
