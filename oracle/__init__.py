@@ -71,11 +71,15 @@ def _lib_load():
             lib.orc_build_csr.restype = ctypes.c_int64
             lib.orc_delta0.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_int]
             lib.orc_delta0.restype = ctypes.c_uint32
-            lib.orc_growth_steps.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, ctypes.c_uint32, ctypes.c_uint32, P]
+            lib.orc_growth_steps.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, P, ctypes.c_uint32, ctypes.c_uint32, P]
             lib.orc_growth_steps.restype = None
             lib.orc_cluster.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                         P, P, ctypes.POINTER(Stats), P, ctypes.c_uint64, P]
             lib.orc_cluster.restype = ctypes.c_int
+            lib.orc_cluster_opts.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_double, ctypes.c_uint64,
+                                             ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32, P, P,
+                                             ctypes.POINTER(Stats), P, ctypes.c_uint64, P]
+            lib.orc_cluster_opts.restype = ctypes.c_int
             lib.orc_quotient.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, P, P, P, P]
             lib.orc_quotient.restype = ctypes.c_int64
             lib.orc_dijkstra.argtypes = [ctypes.c_uint32, P, P, P, P, ctypes.c_uint32, P]
@@ -147,14 +151,16 @@ def delta0(g: CSR, mode: int = DELTA0_AVG) -> int:
     return int(_lib_load().orc_delta0(g.n, _ptr(g.off), _ptr(g.col), _ptr(g.wt), mode))
 
 
-def growth_steps(g: CSR, key, frozen, center, delta: int, steps: int):
-    """t synchronous Delta-growing steps (Section 3) at fixed Delta; returns (key, updated-per-step)."""
+def growth_steps(g: CSR, key, frozen, center, delta: int, steps: int, D=None):
+    """t synchronous Delta-growing steps (Section 3) at fixed Delta; returns (key, updated-per-step).
+    D (optional): bounds of the frozen nodes for the cumulative contract mode."""
     key = _c(key, np.uint64).copy()
     frozen = _c(frozen, np.uint8)
     center = _c(center, np.uint32)
+    Dp = _c(D, np.uint64) if D is not None else None
     upd = np.zeros(max(steps, 1), np.uint64)
     _lib_load().orc_growth_steps(g.n, _ptr(g.off), _ptr(g.col), _ptr(g.wt), _ptr(key), _ptr(frozen),
-                                 _ptr(center), delta, steps, _ptr(upd))
+                                 _ptr(center), _ptr(Dp) if Dp is not None else None, delta, steps, _ptr(upd))
     return key, upd[:steps]
 
 
@@ -166,16 +172,23 @@ class Clustering:
     trace: np.ndarray
 
 
-def cluster(g: CSR, tau: float, seed: int, delta0_value: int, trace_cap: int = 1 << 16) -> Clustering:
-    """CLUSTER(G, tau) of Algorithm 1 with the Section 5 initial Delta passed in."""
+CONTRACT_RESET = 0       # contracted clusters relax as (0, c_u) (Procedure Contract)
+CONTRACT_CUMULATIVE = 1  # contracted nodes relax with their own bound D_u
+
+
+def cluster(g: CSR, tau: float, seed: int, delta0_value: int, trace_cap: int = 1 << 16,
+            contract_mode: int = CONTRACT_RESET, step_cap: int = 0) -> Clustering:
+    """CLUSTER(G, tau) of Algorithm 1 with the Section 5 initial Delta passed in; optionally the
+    cumulative contract mode and the O(n / tau) cap on growing steps per PartialGrowth (end of Section 3)."""
     lib = _lib_load()
     center = np.empty(g.n, np.uint32)
     D = np.empty(g.n, np.uint64)
     st = Stats()
     tr = np.zeros(trace_cap, TRACE_DTYPE)
     tl = ctypes.c_uint64()
-    rc = lib.orc_cluster(g.n, _ptr(g.off), _ptr(g.col), _ptr(g.wt), float(tau), seed, delta0_value,
-                         _ptr(center), _ptr(D), ctypes.byref(st), _ptr(tr), trace_cap, ctypes.addressof(tl))
+    rc = lib.orc_cluster_opts(g.n, _ptr(g.off), _ptr(g.col), _ptr(g.wt), float(tau), seed, delta0_value,
+                              int(contract_mode), int(step_cap), _ptr(center), _ptr(D), ctypes.byref(st), _ptr(tr),
+                              trace_cap, ctypes.addressof(tl))
     if rc != 0:
         raise RuntimeError(f"orc_cluster failed: {rc}")
     stats = {f: getattr(st, f) for f, _ in Stats._fields_ if f != "pad"}

@@ -13,11 +13,16 @@
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   orc_philox4x32_10   pinned: an independent Philox4x32-10 (Triton's, CPU interpreter)
  *   orc_build_csr       pinned: numpy unique/lexsort + scipy connected_components
- *   orc_growth_steps    pinned: brute-force enumeration of bounded walks (Section 3 step)
+ *   orc_growth_steps    pinned: brute-force enumeration of bounded walks (Section 3 step),
+ *                       with frozen nodes at distance 0 or, cumulative mode, at their D
  *   orc_cluster         pinned by invariants (coverage, radius bounds, D >= true distance,
  *                       stage-count bound) and by the special cases that reduce to exact
  *                       APSP; the random trajectory itself has no printed example
  *                       ("parity unpinned" beyond these invariants)
+ *   orc_cluster_opts    the same, plus: a step cap at least as long as the longest
+ *                       uncapped growth changes nothing, cap 1 bounds every growth to one
+ *                       step, the cumulative mode keeps every D within the final Delta and
+ *                       above the true distance, and its first stage equals the default's
  *   orc_quotient        pinned: independent dictionary recomputation + symmetry
  *   orc_apsp_max        pinned: scipy shortest_path
  *   orc_dijkstra        pinned: scipy dijkstra
@@ -225,7 +230,9 @@ uint32_t orc_delta0(uint32_t n, const uint64_t* off, const uint32_t* col, const 
  * from the state as it was at the start of the step (snapshot S).
  *   relaxers: unfrozen u with d_u < Delta, and every frozen u, which stands for
  *             its contracted cluster center c_u at distance 0 (Procedure
- *             Contract replaces (u,v) by (c_u,v) with weight w(u,v));
+ *             Contract replaces (u,v) by (c_u,v) with weight w(u,v)); in the
+ *             cumulative contract mode (Dfrozen != NULL) a frozen u relaxes
+ *             with its own bound D_u instead, if D_u < Delta;
  *   for each relaxer u and edge (u,v) with v unfrozen: if d_u + w <= Delta,
  *             v takes (d_u + w, c_u) if that is lexicographically smaller than
  *             its current (d_v, c_v): smallest distance first, then smallest
@@ -243,15 +250,17 @@ typedef struct {
 static uint64_t mkkey(uint64_t d, uint32_t c) { return (d << 32) | c; }
 
 static uint64_t growing_step(const orc_graph* g, uint64_t* key, uint64_t* snap, const uint8_t* frozen,
-                             const uint32_t* center, uint32_t delta, uint64_t* newly_covered,
-                             uint64_t* edges_examined)
+                             const uint32_t* center, const uint64_t* Dfrozen, uint32_t delta,
+                             uint64_t* newly_covered, uint64_t* edges_examined)
 {
     uint32_t n = g->n;
     memcpy(snap, key, sizeof(uint64_t) * n);
     for (uint32_t u = 0; u < n; ++u) {
         uint64_t du;
         uint32_t cu;
-        if (frozen[u]) { du = 0; cu = center[u]; }
+        if (frozen[u] && !Dfrozen) { du = 0; cu = center[u]; }
+        else if (frozen[u] && Dfrozen[u] < delta) { du = Dfrozen[u]; cu = center[u]; }
+        else if (frozen[u]) continue;
         else if (snap[u] != ORC_INF_KEY && (snap[u] >> 32) < delta) { du = snap[u] >> 32; cu = (uint32_t)snap[u]; }
         else continue;
         for (uint64_t j = g->off[u]; j < g->off[u + 1]; ++j) {
@@ -277,16 +286,18 @@ static uint64_t growing_step(const orc_graph* g, uint64_t* key, uint64_t* snap, 
 
 /* Exposed for the brute-force pin: t synchronous steps at fixed Delta.
  * key[] holds unfrozen nodes' keys (ORC_INF_KEY = no center yet); frozen[v]
- * marks contracted nodes whose center is center[v].  Per-step updated counts
- * go to updated_out[t]. */
+ * marks contracted nodes whose center is center[v]; Dfrozen (NULL: the
+ * default contract mode) holds their bounds for the cumulative mode.
+ * Per-step updated counts go to updated_out[t]. */
 void orc_growth_steps(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* wt,
-                      uint64_t* key, const uint8_t* frozen, const uint32_t* center, uint32_t delta,
-                      uint32_t steps, uint64_t* updated_out)
+                      uint64_t* key, const uint8_t* frozen, const uint32_t* center, const uint64_t* Dfrozen,
+                      uint32_t delta, uint32_t steps, uint64_t* updated_out)
 {
     orc_graph g = {n, off, col, wt};
     uint64_t* snap = (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
     uint64_t cov = 0, ex = 0;
-    for (uint32_t t = 0; t < steps; ++t) updated_out[t] = growing_step(&g, key, snap, frozen, center, delta, &cov, &ex);
+    for (uint32_t t = 0; t < steps; ++t)
+        updated_out[t] = growing_step(&g, key, snap, frozen, center, Dfrozen, delta, &cov, &ex);
     free(snap);
 }
 
@@ -339,10 +350,19 @@ static int exists_growable_edge(const orc_graph* g, const uint64_t* key, const u
     return 0;
 }
 
-int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* wt, double tau,
-                uint64_t seed, uint32_t delta0, uint32_t* center_out, uint64_t* D_out, orc_stats* st,
-                orc_trace* trace, uint64_t trace_cap, uint64_t* trace_len)
+/* Options beyond Algorithm 1's defaults (both off by default):
+ *  - contract_mode 1 (cumulative): contracted nodes relax with their own
+ *    distance bound D_u (not 0), so a new node's distance d_v already bounds
+ *    dist_G(c_v, v) and D_v = d_v; every D then stays within the final Delta.
+ *  - step_cap > 0: each execution of PartialGrowth performs at most step_cap
+ *    growing steps (the O(n / tau) limit of Section 3's closing remark); if
+ *    fewer than half of the nodes are covered afterwards, Delta doubles as
+ *    when growth stops. */
+int orc_cluster_opts(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* wt, double tau,
+                     uint64_t seed, uint32_t delta0, int contract_mode, uint32_t step_cap, uint32_t* center_out,
+                     uint64_t* D_out, orc_stats* st, orc_trace* trace, uint64_t trace_cap, uint64_t* trace_len)
 {
+    if (contract_mode != 0 && contract_mode != 1) return ORC_ERR_ARG;
     if (n == 0 || !(tau > 0.0) || delta0 == 0) return ORC_ERR_ARG;
     orc_graph g = {n, off, col, wt};
     uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * n);
@@ -393,12 +413,15 @@ int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint
         /* inner while loop with PartialGrowth */
         for (;;) {
             uint64_t updated;
+            uint32_t growth_steps = 0;
             do {
-                updated = growing_step(&g, key, snap, frozen, center_out, delta, &covered, &st->edges_examined);
+                updated = growing_step(&g, key, snap, frozen, center_out, contract_mode ? D_out : NULL, delta,
+                                       &covered, &st->edges_examined);
                 st->steps++;
                 st->node_updates += updated;
+                ++growth_steps;
                 TRACE(0, updated, covered);
-            } while (updated != 0 && 2 * covered < U);
+            } while (updated != 0 && 2 * covered < U && (step_cap == 0 || growth_steps < step_cap));
             if (2 * covered >= U) break;
             if (delta >= ORC_DELTA_MAX || !exists_growable_edge(&g, key, frozen)) {
                 st->guard_exits++;
@@ -415,7 +438,7 @@ int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint
         for (uint32_t v = 0; v < n; ++v) {
             if (frozen[v] || key[v] == ORC_INF_KEY) continue;
             uint32_t c = (uint32_t)key[v];
-            newD[v] = (key[v] >> 32) + R[c];
+            newD[v] = (key[v] >> 32) + (contract_mode ? 0 : R[c]);
         }
         for (uint32_t v = 0; v < n; ++v) {
             if (frozen[v] || key[v] == ORC_INF_KEY) continue;
@@ -438,6 +461,14 @@ int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint
 #undef TRACE
     free(key); free(snap); free(frozen); free(R); free(newD);
     return rc;
+}
+
+int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* wt, double tau,
+                uint64_t seed, uint32_t delta0, uint32_t* center_out, uint64_t* D_out, orc_stats* st,
+                orc_trace* trace, uint64_t trace_cap, uint64_t* trace_len)
+{
+    return orc_cluster_opts(n, off, col, wt, tau, seed, delta0, 0, 0, center_out, D_out, st, trace, trace_cap,
+                            trace_len);
 }
 
 /* ---------------------------------------------------------------------------

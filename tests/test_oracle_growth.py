@@ -59,13 +59,17 @@ def random_state(rng, g, delta):
     return key, frozen, center
 
 
-def brute_walks(g, key, frozen, center, delta, t):
+def brute_walks(g, key, frozen, center, delta, t, D=None):
+    # D given: cumulative contract mode, a frozen start u has length D_u (and relaxes only if D_u < Delta)
     A = adj(g)
     best = [int(key[v]) if not frozen[v] else None for v in range(g.n)]
     starts = []
     for s in range(g.n):
         if frozen[s]:
-            starts.append((s, 0, int(center[s])))
+            if D is None:
+                starts.append((s, 0, int(center[s])))
+            elif int(D[s]) < delta:
+                starts.append((s, int(D[s]), int(center[s])))
         elif int(key[s]) != INF:
             starts.append((s, int(key[s]) >> 32, int(key[s]) & 0xFFFFFFFF))
 
@@ -131,6 +135,30 @@ def test_t_steps_equal_bounded_walks(seed):
         ref_prev = brute_walks(g, key, frozen, center, delta, t - 1) if t > 1 else prev
         changed = sum(1 for v in range(g.n) if not frozen[v] and ref[v] < ref_prev[v])
         assert int(upd[-1]) == changed
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_cumulative_steps_equal_bounded_walks(seed):
+    # cumulative contract mode: a frozen node starts its walks at its own bound D_u instead of 0
+    rng = np.random.default_rng(500 + seed)
+    g = tiny_graph(rng)
+    delta = int(rng.integers(1, 13))
+    key, frozen, center = random_state(rng, g, delta)
+    D = np.where(frozen != 0, rng.integers(0, delta + 3, g.n), 0).astype(np.uint64)
+    prev = [int(x) for x in key]
+    for t in range(1, 5):
+        got, upd = oracle.growth_steps(g, key, frozen, center, delta, t, D=D)
+        ref = brute_walks(g, key, frozen, center, delta, t, D=D)
+        for v in range(g.n):
+            if not frozen[v]:
+                assert int(got[v]) == ref[v], (seed, t, v)
+        ref_prev = brute_walks(g, key, frozen, center, delta, t - 1, D=D) if t > 1 else prev
+        changed = sum(1 for v in range(g.n) if not frozen[v] and ref[v] < ref_prev[v])
+        assert int(upd[-1]) == changed
+    # all frozen bounds at 0 give the default mode's steps
+    got0, _ = oracle.growth_steps(g, key, frozen, center, delta, 3, D=np.zeros(g.n, np.uint64))
+    got1, _ = oracle.growth_steps(g, key, frozen, center, delta, 3)
+    assert np.array_equal(got0, got1)
 
 
 @pytest.mark.parametrize("seed", range(40))
