@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--plain-sample-every", type=int, default=10)
+    ap.add_argument("--no-delta0-experiment", action="store_true", help="skip the initial-Delta experiment")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run one pipeline pass on the workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -304,6 +305,39 @@ def served_leg(cd, mix, rates, count=20000, plain_count=1000, seed=5):
     return out
 
 
+# ----------------------------------------------------------------------------- initial-Delta experiment
+def delta0_leg(cd, side=2048, tau=5.4, seed=7):
+    """The initial-Delta experiment of Section 5 on a mesh with two edge weights (integer form of the
+    paper's 1 with probability 0.1 and 1e-6 otherwise): CL-DIAM started at the minimum weight (Delta
+    grows by doubling) against CL-DIAM started at the graph's diameter (no doubling); each ratio is
+    Phi_approx over a lower bound from farthest-node SSSP sweeps (exact Delta-stepping distances)."""
+    import inputs
+    e = inputs.grid(side, 10, seed)
+    w = np.where(e.w == 1, 1_000_000, 1).astype(np.uint32)  # a uniform draw in [1, 10] is 1 w.p. 0.1
+    g = cd.build_csr(e.src, e.dst, w, e.n)
+    # lower bound on the diameter: four farthest-node sweeps from the Philox source
+    src = cd.sssp_source(g, seed)
+    lb = 0
+    for _ in range(4):
+        dist, ecc, _ = cd.sssp_delta(g, src)
+        lb = max(lb, int(ecc))
+        src = int(np.argmax(np.where(dist == 0xFFFFFFFF, 0, dist)))
+    out = {"workload": f"mesh {side}x{side}, w = 10^6 with probability 0.1 else 1, seed {seed}, tau {tau}",
+           "diameter_lower_bound": lb}
+    for name, mode, d0, cm in (("delta0_min", cd.DELTA0_MIN, 0, cd.CONTRACT_RESET),
+                               ("delta0_diameter", cd.DELTA0_EXPLICIT, lb, cd.CONTRACT_RESET),
+                               ("delta0_min_cumulative", cd.DELTA0_MIN, 0, cd.CONTRACT_CUMULATIVE),
+                               ("delta0_diameter_cumulative", cd.DELTA0_EXPLICIT, lb, cd.CONTRACT_CUMULATIVE)):
+        t0 = time.perf_counter()
+        c = cd.cluster(g, tau, seed, delta0_mode=mode, delta0=d0, contract_mode=cm)
+        r = cd.estimate(cd.quotient_build(c))
+        out[name] = {"delta0": int(d0) if d0 else 1, "delta_end": r["delta_end"], "doublings": r["doublings"],
+                     "steps": r["steps"], "k": r["k"], "phi_approx": r["phi_approx"],
+                     "ratio": round(r["phi_approx"] / lb, 4), "ms": round((time.perf_counter() - t0) * 1e3, 2)}
+    out["paper"] = "Section 5: ratio 1.0001 (start at the minimum weight) vs about 2.5 (start at the diameter)"
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU leg
 def run_gpu(args):
     import torch
@@ -486,6 +520,8 @@ def run_gpu(args):
                           "ms": round(t_ds * 1e3, 3), "gteps": round(m_lcc / t_ds / 1e9, 4), "ecc": ecc,
                           "upper_bound": 2 * ecc, "rounds": rounds},
     }
+    if not args.no_delta0_experiment and rank == 0:
+        line["initial_delta_experiment"] = delta0_leg(cd)
     if not args.no_batched:
         mix = build_mix_arena(cd, stream, args.batched_count, budget=150 * 10**9, rank=rank, world=ws)
         line["batched"] = batched_leg(cd, stream, mix, args.plain_sample_every, dist=dist)

@@ -78,12 +78,18 @@ typedef struct cldiam_server cldiam_server;         /* request server over an ar
 typedef struct {
     int32_t delta0_mode;   /* CLDIAM_DELTA0_*                                              */
     uint32_t delta0;       /* used with CLDIAM_DELTA0_EXPLICIT; must be >= 1                */
-    int32_t contract_mode; /* 0: contracted clusters relax from distance 0 (Procedure Contract) */
-    uint32_t step_cap;     /* must be 0 (no cap on growing steps per PartialGrowth)         */
+    int32_t contract_mode; /* CLDIAM_CONTRACT_*                                             */
+    uint32_t step_cap;     /* growing steps per PartialGrowth execution; 0 = no cap         */
     uint32_t max_fw_k;     /* largest dense quotient solved by Floyd-Warshall; 0 = 8192     */
     uint32_t quotient_mode; /* CLDIAM_QUOTIENT_*: how cldiam_quotient_build deduplicates     */
     uint32_t reserved[2];  /* must be 0                                                     */
 } cldiam_opts;
+
+/* cldiam_opts.contract_mode */
+#define CLDIAM_CONTRACT_RESET 0      /* clusters of earlier stages relax from distance 0 through every
+                                        member (Procedure Contract); D_v = d_v + R[c_v] (default) */
+#define CLDIAM_CONTRACT_CUMULATIVE 1 /* a member u of an earlier cluster relaxes with its own bound
+                                        D_u (while D_u < Delta); D_v = d_v <= final Delta         */
 
 /* cldiam_opts.quotient_mode (same result either way) */
 #define CLDIAM_QUOTIENT_AUTO 0  /* dense while k <= 4096, else radix sort (default) */
@@ -117,6 +123,8 @@ cldiam_status cldiam_version(int32_t* major, int32_t* minor);
 /*
  * Build the device CSR of an undirected weighted graph (Section 2 graph model).
  *  src, dst, w : m edges (host or device arrays); node ids < n, weights >= 1.
+ *               Pinned host arrays are read in place by the device (no staging
+ *               copy); other host arrays are copied to the device first.
  *  Self-loops are dropped; parallel edges merge to their minimum weight; the
  *  result is symmetric with rows sorted by column.  With CLDIAM_CSR_LCC only
  *  the largest connected component is kept (ties: the component holding the
@@ -144,10 +152,14 @@ cldiam_status cldiam_delta0(const cldiam_graph* g, int32_t mode, uint32_t* out);
  *         p = 4 ln2 tau log2 n / |U|.
  *  Growth: synchronous Delta-growing steps (Section 3) with the
  *         (distance, center id) tie-break; PartialGrowth stops when no state
- *         changes or 2 covered >= |U|; Delta doubles (capped at 2^31) while
- *         coverage is under half and some uncovered node is still reachable.
+ *         changes, 2 covered >= |U|, or (opts->step_cap > 0) after step_cap
+ *         steps -- the O(n / tau) limit of Section 3's closing remark; Delta
+ *         doubles (capped at 2^31) while coverage is under half and some
+ *         uncovered node is still reachable.
  *  Contract: clusters of earlier stages relax from distance 0 through every
- *         member; D_v = d_v + R[c_v] bounds dist_G(c_v, v).
+ *         member; D_v = d_v + R[c_v] bounds dist_G(c_v, v).  With
+ *         CLDIAM_CONTRACT_CUMULATIVE a member u relaxes with its own D_u
+ *         instead and D_v = d_v, so every D_v is within the final Delta.
  *  Leftover nodes become singleton clusters.  Results are a deterministic
  *  function of (graph, tau, seed, opts).
  *  Errors: INVALID_ARG, OVERFLOW (a D_v >= 2^32 - 1), DIVERGED, OOM, CUDA.

@@ -28,6 +28,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "OVERFLOW", -4: "TIMEOUT", 
 CSR_LCC = 1
 DELTA0_AVG, DELTA0_MIN, DELTA0_EXPLICIT = 0, 1, 2
 QUOTIENT_AUTO, QUOTIENT_SORT, QUOTIENT_DENSE = 0, 1, 2
+CONTRACT_RESET, CONTRACT_CUMULATIVE = 0, 1
 
 
 class CldiamError(RuntimeError):
@@ -280,7 +281,8 @@ class Arena(_Handle):
         _check(load().cldiam_arena_graph(self.handle, gid, ctypes.byref(h)), "cldiam_arena_graph")
         return ArenaGraph(h.value, self)
 
-    def run(self, ids, taus, seeds, delta0_mode=DELTA0_AVG, raise_on_error=True):
+    def run(self, ids, taus, seeds, delta0_mode=DELTA0_AVG, raise_on_error=True, contract_mode=CONTRACT_RESET,
+            step_cap=0):
         """Batch of jobs; returns (list of result dicts, list of statuses)."""
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
         taus = np.ascontiguousarray(taus, dtype=np.float64)
@@ -288,7 +290,7 @@ class Arena(_Handle):
         cnt = int(ids.size)
         res = (Result * max(cnt, 1))()
         sts = np.zeros(max(cnt, 1), np.int32)
-        o = make_opts(delta0_mode)
+        o = make_opts(delta0_mode, contract_mode=contract_mode, step_cap=step_cap)
         st = load().cldiam_batch_run(self.handle, ids.ctypes.data, taus.ctypes.data, seeds.ctypes.data, cnt,
                                      ctypes.byref(o), ctypes.cast(res, ctypes.c_void_p), sts.ctypes.data)
         if raise_on_error:
@@ -365,19 +367,22 @@ def build_csr(src, dst, w, n: int, lcc: bool = True, stream=None) -> Graph:
     return Graph(h.value)
 
 
-def make_opts(delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0, quotient_mode=QUOTIENT_AUTO) -> Opts:
+def make_opts(delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0, quotient_mode=QUOTIENT_AUTO,
+              contract_mode=CONTRACT_RESET, step_cap=0) -> Opts:
     o = Opts()
     o.delta0_mode = delta0_mode
     o.delta0 = delta0
     o.max_fw_k = max_fw_k
     o.quotient_mode = quotient_mode
+    o.contract_mode = contract_mode
+    o.step_cap = step_cap
     return o
 
 
 def cluster(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0,
-            quotient_mode=QUOTIENT_AUTO) -> Clustering:
-    """cldiam_cluster: CLUSTER(G, tau) of Algorithm 1."""
-    o = make_opts(delta0_mode, delta0, max_fw_k, quotient_mode)
+            quotient_mode=QUOTIENT_AUTO, contract_mode=CONTRACT_RESET, step_cap=0) -> Clustering:
+    """cldiam_cluster: CLUSTER(G, tau) of Algorithm 1 (options: contract mode, growing-step cap)."""
+    o = make_opts(delta0_mode, delta0, max_fw_k, quotient_mode, contract_mode, step_cap)
     h = ctypes.c_void_p()
     _check(load().cldiam_cluster(g.handle, float(tau), seed, ctypes.byref(o), ctypes.byref(h)), "cldiam_cluster")
     return Clustering(h.value, g)

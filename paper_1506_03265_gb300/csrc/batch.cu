@@ -49,7 +49,9 @@ struct Job {
     uint64_t seed;
     uint32_t graph;
     uint32_t delta0;
-    uint32_t out;  // index in the caller's result array
+    uint32_t out;         // index in the caller's result array
+    uint32_t step_cap;    // growing steps per PartialGrowth, 0 = no cap
+    uint32_t cumulative;  // cumulative contract mode
     uint32_t pad;
 };
 
@@ -168,7 +170,7 @@ __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M
             if (dyn[i] != kNone && dyn[i] > best) best = dyn[i];
     } else {
         // quotient CSR from M (warp per row, ballot compaction keeps columns sorted), then
-        // multi-source Bellman-Ford, 8 sources at a time, distances in shared memory
+        // batched exact SSSP on it
         const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
         for (uint32_t a = w; a < k; a += nw) {
             uint32_t c = 0;
@@ -199,38 +201,54 @@ __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M
             }
         }
         __syncthreads();
-        constexpr uint32_t S = 8, kSlots = 32 / S;
-        const uint32_t my_s = l % S, slot = l / S;
+        // worklist multi-source Bellman-Ford, 8 sources at a time: dist[v][s] and one word of change
+        // bits per node (two rounds) in shared memory; a changed node pushes to its neighbours
+        constexpr uint32_t S = 8;
         uint32_t* dist = dyn;  // k x S
+        uint32_t* chg0 = dyn + (size_t)k * S;
+        uint32_t* chg1 = chg0 + k;
         for (uint32_t s0 = 0; s0 < k; s0 += S) {
             for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x) dist[i] = (s0 + i % S == i / S) ? 0u : kNone;
-            if (threadIdx.x == 0) sm.changed[0] = sm.changed[1] = sm.changed[2] = 0;
+            for (uint32_t v = threadIdx.x; v < k; v += blockDim.x) {
+                chg0[v] = (v >= s0 && v < s0 + S) ? 1u << (v - s0) : 0u;
+                chg1[v] = 0;
+            }
             __syncthreads();
-            for (uint32_t round = 0; round < k; ++round) {
-                const uint32_t slot_r = round % 3;
-                if (threadIdx.x == 0) sm.changed[(round + 1) % 3] = 0;
-                bool changed = false;
+            for (uint32_t round = 0;; ++round) {
+                uint32_t* cur = (round & 1) ? chg1 : chg0;
+                uint32_t* nxt = (round & 1) ? chg0 : chg1;
                 for (uint32_t v = w; v < k; v += nw) {
+                    const uint32_t bits = cur[v];
+                    if (!bits) continue;
                     const uint32_t beg = __ldcg(&ws.qoff[v]), end = __ldcg(&ws.qoff[v + 1]);
-                    uint32_t bv = kNone;
-                    for (uint32_t j = beg + slot; j < end; j += kSlots) {
-                        const uint32_t du = dist[__ldcg(&ws.qcol[j]) * S + my_s];
-                        if (du != kNone) {
-                            const uint64_t nd = (uint64_t)du + __ldcg(&ws.qw[j]);
-                            if (nd >= kNone) ovf = true;
-                            else bv = min(bv, (uint32_t)nd);
+                    for (uint32_t j = beg + l; j < end; j += 32) {
+                        const uint32_t u = __ldcg(&ws.qcol[j]), wj = __ldcg(&ws.qw[j]);
+                        for (uint32_t b = bits; b; b &= b - 1) {
+                            const uint32_t si = (uint32_t)__ffs(b) - 1;
+                            const uint32_t dv = dist[v * S + si];
+                            if (dv == kNone) continue;
+                            const uint64_t nd = (uint64_t)dv + wj;
+                            if (nd >= kNone) {
+                                ovf = true;
+                                continue;
+                            }
+                            uint32_t* du = &dist[u * S + si];
+                            if ((uint32_t)nd < *du && (uint32_t)nd < atomicMin(du, (uint32_t)nd))
+                                atomicOr(&nxt[u], 1u << si);
                         }
                     }
-#pragma unroll
-                    for (uint32_t o = S; o < 32; o <<= 1) bv = min(bv, __shfl_xor_sync(0xffffffffu, bv, o));
-                    if (l < S && bv < dist[v * S + l]) {
-                        dist[v * S + l] = bv;
-                        changed = true;
-                    }
                 }
-                if (__any_sync(0xffffffffu, changed) && l == 0) sm.changed[slot_r] = 1;
                 __syncthreads();
-                if (!sm.changed[slot_r]) break;
+                bool any = false;
+                for (uint32_t v = threadIdx.x; v < k; v += blockDim.x) {
+                    cur[v] = 0;
+                    any |= nxt[v] != 0;
+                }
+                if (!__syncthreads_or(any)) break;
+                if (round > k * S + 64) {  // distances only decrease: far above any real count, reported
+                    ovf = true;
+                    break;
+                }
             }
             for (uint32_t i = threadIdx.x; i < k * S; i += blockDim.x)
                 if (s0 + i % S < k && dist[i] != kNone && dist[i] > best) best = dist[i];
@@ -286,7 +304,8 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
         __syncthreads();
         {
             const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-            dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr,
+            dev_rebuild(n, ws.key, ws.center, job.cumulative ? ws.D : nullptr, off, delta, pull, ws.fbase[cur],
+                        ws.fkey[cur], ws.fpre[cur], nullptr,
                         ctr, sm.scratch, 0, 1);
         }
         __syncthreads();
@@ -296,8 +315,9 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
         E = (uint32_t)vc->front;
         __syncthreads();
         for (;;) {
-            uint32_t updated;
+            uint32_t updated, growth_steps = 0;
             do {
+                ++growth_steps;
                 ++stepid;
                 updated = 0;
                 if (nf > 0) {
@@ -307,7 +327,8 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                         ctr->nnext = 0;
                     }
                     __syncthreads();
-                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr, nf, E, adj, ws.center, ws.key,
+                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr, nf, E, adj, ws.center,
+                                 job.cumulative ? ws.D : nullptr, ws.key,
                                  delta, ws.stamp, stepid, ws.next, ctr, sm.relax, sm.relax_next, 0, 1);
                     __syncthreads();
                     const uint32_t nn = vc->nnext;
@@ -324,7 +345,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                 }
                 res.steps++;
                 res.node_updates += updated;
-            } while (updated != 0 && 2 * covered < U);
+            } while (updated != 0 && 2 * covered < U && (job.step_cap == 0 || growth_steps < job.step_cap));
             if (2 * covered >= U) break;
             bool growable = false;
             if (delta < kDeltaMax && d.connected) {
@@ -347,7 +368,8 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
             __syncthreads();
             {
                 const bool pull = pull_ok && (d.nnz - frozen_deg) < frozen_deg;
-                dev_rebuild(n, ws.key, ws.center, off, delta, pull, ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr,
+                dev_rebuild(n, ws.key, ws.center, job.cumulative ? ws.D : nullptr, off, delta, pull, ws.fbase[cur],
+                        ws.fkey[cur], ws.fpre[cur], nullptr,
                             ctr, sm.scratch, 0, 1);
             }
             __syncthreads();
@@ -360,7 +382,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
             ctr->frozen_deg = 0;
         }
         __syncthreads();
-        dev_finalize_d(n, ws.key, ws.center, ws.R, ws.D, ctr, 0, 1);
+        dev_finalize_d(n, ws.key, ws.center, job.cumulative ? nullptr : ws.R, ws.D, ctr, 0, 1);
         __syncthreads();
         dev_finalize_freeze(n, ws.key, ws.center, ws.R, ws.D, off, ctr, 0, 1);
         __syncthreads();
@@ -511,6 +533,9 @@ __global__ void __launch_bounds__(BT, 1)
                 s_job.graph = vj->graph;
                 s_job.delta0 = vj->delta0;
                 s_job.out = vj->out;
+                s_job.step_cap = vj->step_cap;
+                s_job.cumulative = vj->cumulative;
+                s_job.pad = 0;
             }
         }
         __syncthreads();
@@ -699,7 +724,10 @@ static cldiam_status make_workspaces(uint32_t nmax, int ctas, cudaStream_t s, vo
     return CLDIAM_OK;
 }
 
-static size_t batch_dyn_smem() { return std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * 8 * 4); }
+static size_t batch_dyn_smem() {
+    // shared Floyd-Warshall matrix, or the quotient SSSP's k x 8 distances and two words of change bits per node
+    return std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * (8 * 4 + 8));
+}
 
 template <class Kern>
 static cldiam_status set_dyn_smem(Kern k, bool* done_flags) {
@@ -718,8 +746,9 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     if (count == 0) return CLDIAM_OK;
     cldiam_opts opts{};
     if (o) opts = *o;
-    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1])
-        return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
+    if (opts.contract_mode != CLDIAM_CONTRACT_RESET && opts.contract_mode != CLDIAM_CONTRACT_CUMULATIVE)
+        return fail(CLDIAM_ERR_INVALID_ARG, "unknown contract_mode");
+    if (opts.reserved[0] || opts.reserved[1]) return fail(CLDIAM_ERR_INVALID_ARG, "reserved options must be 0");
     const cudaStream_t s = a->stream;
     std::vector<Job> jobs(count);
     uint32_t nmax = 1;
@@ -736,6 +765,8 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         jobs[i].graph = ids[i];
         jobs[i].delta0 = d0;
         jobs[i].out = i;
+        jobs[i].step_cap = opts.step_cap;
+        jobs[i].cumulative = opts.contract_mode == CLDIAM_CONTRACT_CUMULATIVE ? 1u : 0u;
         nmax = std::max(nmax, view.n);
     }
     // largest graphs first: the work queue then balances the tail

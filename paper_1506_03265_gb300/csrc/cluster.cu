@@ -18,23 +18,25 @@ __global__ void k_select(uint32_t n, const uint32_t* __restrict__ center, unsign
 }
 
 __global__ void k_rebuild(uint32_t n, const unsigned long long* __restrict__ key, const uint32_t* __restrict__ center,
-                          const uint64_t* __restrict__ off, uint32_t delta, bool pull, uint32_t* __restrict__ fbase,
-                          unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre,
-                          uint32_t* __restrict__ cfirst, Counters* ctr) {
+                          const uint32_t* __restrict__ Dcum, const uint64_t* __restrict__ off, uint32_t delta,
+                          bool pull, uint32_t* __restrict__ fbase, unsigned long long* __restrict__ fkey,
+                          uint32_t* __restrict__ fpre, uint32_t* __restrict__ cfirst, Counters* ctr) {
     __shared__ unsigned long long scratch[33];
-    dev_rebuild(n, key, center, off, delta, pull, fbase, fkey, fpre, cfirst, ctr, scratch, blockIdx.x, gridDim.x);
+    dev_rebuild(n, key, center, Dcum, off, delta, pull, fbase, fkey, fpre, cfirst, ctr, scratch, blockIdx.x,
+                gridDim.x);
 }
 
 __global__ void __launch_bounds__(RT) k_relax(const uint32_t* __restrict__ fbase,
                                               const unsigned long long* __restrict__ fkey,
                                               const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
                                               uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
-                                              const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
-                                              uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
+                                              const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
+                                              unsigned long long* __restrict__ key, uint32_t delta,
+                                              uint32_t* __restrict__ stamp, uint32_t stepid,
                                               uint32_t* __restrict__ next, Counters* ctr) {
     __shared__ RelaxSmem sm;
     __shared__ uint32_t nbuf[relax_nbuf_words<RU>(RT / 32)];
-    dev_relax<RU>(fbase, fkey, fpre, cfirst, nf, E, adj, center, key, delta, stamp, stepid, next, ctr, sm, nbuf,
+    dev_relax<RU>(fbase, fkey, fpre, cfirst, nf, E, adj, center, Dcum, key, delta, stamp, stepid, next, ctr, sm, nbuf,
                   blockIdx.x, gridDim.x);
 }
 
@@ -110,8 +112,11 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     if (!(tau > 0.0) || !std::isfinite(tau)) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be a positive number");
     cldiam_opts opts{};
     if (o) opts = *o;
-    if (opts.contract_mode != 0 || opts.step_cap != 0 || opts.reserved[0] || opts.reserved[1])
-        return fail(CLDIAM_ERR_UNSUPPORTED, "only contract_mode 0 without a step cap is implemented");
+    if (opts.contract_mode != CLDIAM_CONTRACT_RESET && opts.contract_mode != CLDIAM_CONTRACT_CUMULATIVE)
+        return fail(CLDIAM_ERR_INVALID_ARG, "unknown contract_mode");
+    if (opts.reserved[0] || opts.reserved[1]) return fail(CLDIAM_ERR_INVALID_ARG, "reserved options must be 0");
+    const bool cumulative = opts.contract_mode == CLDIAM_CONTRACT_CUMULATIVE;
+    const uint32_t step_cap = opts.step_cap;  // growing steps per PartialGrowth, 0 = no cap
     if (opts.quotient_mode > CLDIAM_QUOTIENT_DENSE) return fail(CLDIAM_ERR_INVALID_ARG, "unknown quotient_mode");
     uint32_t delta = 0;
     CLD_TRY(delta0(g, opts.delta0_mode, opts.delta0, &delta));
@@ -192,8 +197,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     auto rebuild = [&]() -> cldiam_status {
         const bool pull = pull_ok && (g->nnz - frozen_deg) < frozen_deg;
         CLD_TRY(zero_field(offsetof(Counters, front), 8));
-        CLD_K(K_REBUILD, s, k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), g->off, delta, pull, fv, fk, fp,
-                                                          cf, ctr.get()));
+        CLD_K(K_REBUILD, s, k_rebuild<<<gb, 256, 0, s>>>(n, key.get(), center.get(), cumulative ? D.get() : nullptr,
+                                                          g->off, delta, pull, fv, fk, fp, cf, ctr.get()));
         CLD_LAUNCH_CHECK();
         return CLDIAM_OK;
     };
@@ -215,8 +220,9 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
         st.centers_drawn += hc->selected;
 
         for (;;) {
-            uint32_t updated;
+            uint32_t updated, growth_steps = 0;
             do {
+                ++growth_steps;
                 ++stepid;
                 updated = 0;
                 if (nf > 0) {
@@ -225,8 +231,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                     CLD_TRY(zero_field(offsetof(Counters, nnext), 4));
                     const unsigned rg = (unsigned)std::min<uint64_t>((E + RC - 1) / RC, max_relax_grid);
                     CLD_K(K_RELAX, s, k_relax<<<rg, RT, 0, s>>>(fv, fk, fp, cf, nf, E, g->adj, center.get(),
-                                                                 key.get(), delta, stamp.get(), stepid, next.get(),
-                                                                 ctr.get()));
+                                                                 cumulative ? D.get() : nullptr, key.get(), delta,
+                                                                 stamp.get(), stepid, next.get(), ctr.get()));
                     CLD_LAUNCH_CHECK();
                     CLD_K(K_SNAPSHOT, s, k_snapshot<<<max_relax_grid, 256, 0, s>>>(next.get(), key.get(), g->off, delta,
                                                                                  fv2, fk2, fp2, cf2, ctr.get()));
@@ -249,7 +255,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                 }
                 st.steps++;
                 st.node_updates += updated;
-            } while (updated != 0 && 2 * covered < U);
+            } while (updated != 0 && 2 * covered < U && (step_cap == 0 || growth_steps < step_cap));
             if (2 * covered >= U) break;
             bool growable = false;
             if (delta < kDeltaMax && g->connected) {
@@ -277,7 +283,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
 
         // assign and contract
         CLD_TRY(zero_field(offsetof(Counters, frozen), 16));  // frozen + frozen_deg
-        CLD_K(K_FINALIZE, s, k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), ctr.get()));
+        CLD_K(K_FINALIZE, s, k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), cumulative ? nullptr : R.get(),
+                                                             D.get(), ctr.get()));
         CLD_K(K_FINALIZE, s, k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), g->off,
                                                                   ctr.get()));
         CLD_LAUNCH_CHECK();

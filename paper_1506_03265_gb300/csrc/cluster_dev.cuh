@@ -10,6 +10,9 @@
 // hold key 0, which no candidate can undercut, so the relaxation needs no
 // frozen test; they are relaxers with the virtual key (0, c_u).
 //
+// In the cumulative contract mode (Dcum != nullptr) a frozen node relaxes
+// with its own bound (D_u, c_u) instead, and only while D_u < Delta.
+//
 // Steps are synchronous: each frontier entry carries the key its node had
 // at the start of the step, so in-place atomicMin gives exactly the
 // start-of-step (Jacobi) semantics of the paper's "in parallel" step.  The
@@ -116,8 +119,9 @@ __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restric
 // (w, c_u) from its frozen neighbours -- the same candidates, read from the
 // side with fewer adjacency entries.
 __device__ __forceinline__ void dev_rebuild(uint32_t n, const unsigned long long* __restrict__ key,
-                                            const uint32_t* __restrict__ center, const uint64_t* __restrict__ off,
-                                            uint32_t delta, bool pull, uint32_t* __restrict__ fbase,
+                                            const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
+                                            const uint64_t* __restrict__ off, uint32_t delta, bool pull,
+                                            uint32_t* __restrict__ fbase,
                                             unsigned long long* __restrict__ fkey, uint32_t* __restrict__ fpre,
                                             uint32_t* __restrict__ cfirst, Counters* ctr, unsigned long long* scratch,
                                             uint32_t br, uint32_t nb) {
@@ -133,8 +137,9 @@ __device__ __forceinline__ void dev_rebuild(uint32_t n, const unsigned long long
             const uint32_t c = __ldcg(&center[v]);
             if (deg > 0) {
                 if (c != kNone) {
-                    push = !pull;
-                    k = c;  // (0, c_u)
+                    const uint32_t dd = Dcum ? __ldcg(&Dcum[v]) : 0u;  // (0, c_u), or (D_u, c_u) cumulative
+                    push = !pull && dd < delta;
+                    k = ((unsigned long long)dd << 32) | c;
                 } else {
                     k = __ldcg(&key[v]);
                     push = k != kInfKey && (uint32_t)(k >> 32) < delta;
@@ -225,8 +230,9 @@ template <int U>
 __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
                                           const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
                                           uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
-                                          const uint32_t* __restrict__ center, unsigned long long* __restrict__ key,
-                                          uint32_t delta, uint32_t* __restrict__ stamp, uint32_t stepid,
+                                          const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
+                                          unsigned long long* __restrict__ key, uint32_t delta,
+                                          uint32_t* __restrict__ stamp, uint32_t stepid,
                                           uint32_t* __restrict__ next, Counters* ctr, RelaxSmem& sm,
                                           uint32_t* nbuf, uint32_t br, uint32_t nb) {
     constexpr uint32_t kNB = 2 * U * 32;  // a chunk adds at most U x 32 nodes per warp
@@ -330,8 +336,11 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
                 } else if (ed[u].y <= delta) {
                     const uint32_t cu = __ldcg(&center[ed[u].x]);
                     if (cu != kNone) {
-                        target[u] = (uint32_t)ku;
-                        nk[u] = ((unsigned long long)ed[u].y << 32) | cu;
+                        const uint64_t cand = (uint64_t)(Dcum ? __ldcg(&Dcum[ed[u].x]) : 0u) + ed[u].y;
+                        if (cand <= delta) {
+                            target[u] = (uint32_t)ku;
+                            nk[u] = (cand << 32) | cu;
+                        }
                     }
                 }
             }
@@ -416,7 +425,8 @@ __device__ __forceinline__ void dev_growable(const uint32_t* __restrict__ row, c
     if (__any_sync(0xffffffffu, any) && lane_id() == 0) atomicExch(&ctr->growable, 1u);
 }
 
-// a7 (part 1): D_v = d_v + R[c_v] for the nodes covered in this stage (R as before the stage).
+// a7 (part 1): D_v = d_v + R[c_v] for the nodes covered in this stage (R as before the stage);
+// D_v = d_v in the cumulative contract mode (R null), whose d_v already bounds dist_G(c_v, v).
 __device__ __forceinline__ void dev_finalize_d(uint32_t n, const unsigned long long* __restrict__ key,
                                                const uint32_t* __restrict__ center, const uint32_t* __restrict__ R,
                                                uint32_t* __restrict__ D, Counters* ctr, uint32_t br, uint32_t nb) {
@@ -424,7 +434,7 @@ __device__ __forceinline__ void dev_finalize_d(uint32_t n, const unsigned long l
         if (__ldcg(&center[v]) != kNone) continue;
         const unsigned long long k = __ldcg(&key[v]);
         if (k == kInfKey) continue;
-        uint64_t dv = (k >> 32) + (uint64_t)__ldcg(&R[(uint32_t)k]);
+        uint64_t dv = (k >> 32) + (R ? (uint64_t)__ldcg(&R[(uint32_t)k]) : 0ull);  // cumulative mode: R null
         if (dv >= 0xFFFFFFFFull) {
             atomicExch(&ctr->overflow, 1u);
             dv = 0xFFFFFFFEull;

@@ -214,30 +214,6 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, bool pred, u
     return slot;
 }
 
-// Segmented minimum over a warp's lanes holding consecutive items of a
-// sorted sequence: lanes with equal keys form one run, so comparing the key
-// `o` lanes back suffices.  Returns, in each lane, the minimum of its run's
-// values from the run's first lane in this warp up to itself; the run's last
-// lane in the warp therefore holds the warp's contribution to the run.
-template <class K>
-__device__ __forceinline__ uint32_t warp_seg_min(K key, bool valid, uint32_t v) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        K ok = __shfl_up_sync(0xffffffffu, key, o);
-        uint32_t ov = __shfl_up_sync(0xffffffffu, v, o);
-        bool ovalid = __shfl_up_sync(0xffffffffu, valid, o);
-        if ((int)lane_id() >= o && ovalid && ok == key && ov < v) v = ov;
-    }
-    return v;
-}
-// true in the lane holding the last item of its run within the warp
-template <class K>
-__device__ __forceinline__ bool warp_run_tail(K key, bool valid) {
-    K nk = __shfl_down_sync(0xffffffffu, key, 1);
-    bool nvalid = __shfl_down_sync(0xffffffffu, valid, 1);
-    return valid && (lane_id() == 31 || !nvalid || nk != key);
-}
-
 // Block-wide reduction helpers (blockDim.x multiple of 32, <= 1024).
 template <class T, class Op>
 __device__ T block_reduce(T v, Op op, T identity) {

@@ -296,11 +296,12 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         void** p; bool* o; cudaStream_t s;
         ~InFree() { if (*o) dfree(*p, s); }
     };
-    CLD_TRY(to_device(src, m * 4, s, &dsrc, &osrc));
+    // the edge arrays are read once (by the emission kernel): pinned host arrays are read in place
+    CLD_TRY(to_device(src, m * 4, s, &dsrc, &osrc, true));
     InFree f1{&dsrc, &osrc, s};
-    CLD_TRY(to_device(dst, m * 4, s, &ddst, &odst));
+    CLD_TRY(to_device(dst, m * 4, s, &ddst, &odst, true));
     InFree f2{&ddst, &odst, s};
-    CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
+    CLD_TRY(to_device(w, m * 4, s, &dw, &ow, true));
     InFree f3{&dw, &ow, s};
 
     // items: packed words when the weight fits in the bits the two ids leave, else (key, weight) pairs

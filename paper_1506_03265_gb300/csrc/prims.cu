@@ -638,43 +638,49 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
     }
     __syncthreads();
     const uint32_t tbase = s_prefix + s_woff[w];
+    // Run minima: a head stores its run's key and its own value, then (after a block barrier, so the
+    // stores come first) every other item of a run folds its value in with atomicMin.  The one run
+    // that may continue into the next tile has its head fold in with atomicMin too (w_out holds
+    // 0xFFFFFFFF beforehand), as do items whose run began in an earlier tile.
+    const size_t tend = min(cnt, (size_t)(tile + 1) * UQ_TILE);
+    const K lastkey = (K)(keys[tend - 1] >> ks);
+    const bool crosses = tend < cnt && (K)(keys[tend] >> ks) == lastkey && lastkey < sentinel;
+    const auto row_of = [&](K kk) -> uint64_t {
+        return div_shift >= 0 ? ((uint64_t)kk >> div_shift) : (uint64_t)kk / div;
+    };
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
         const bool valid = key[i] < sentinel;
-        const uint32_t v = warp_seg_min(key[i], valid, val[i]);
-        const bool tail = warp_run_tail(key[i], valid);
-        // a run that starts and ends inside these 32 items is written by its last lane alone: plain
-        // store; a run piece that may continue in another warp or tile is folded in with atomicMin
-        const K up = __shfl_up_sync(0xffffffffu, key[i], 1);
-        const unsigned starts = __ballot_sync(0xffffffffu, l == 0 || up != key[i]);
-        const unsigned seg0 = 31u - __clz(starts & (0xffffffffu >> (31u - l)));
-        const bool whole_head = (__shfl_sync(0xffffffffu, head_bits, seg0) >> i) & 1u;
+        K before = __shfl_up_sync(0xffffffffu, key[i], 1);
+        if (l == 0) before = idx > 0 ? (K)(keys[idx - 1] >> ks) : sentinel;
+        const uint32_t f = (head_bits >> i) & 1u;
+        if (!valid || !f) continue;
+        const uint32_t r = tbase + ex[i];
+        if (crosses && key[i] == lastkey) atomicMin(&w_out[(size_t)r * cs], val[i]);
+        else w_out[(size_t)r * cs] = val[i];
+        const uint64_t q = row_of(key[i]);
+        if (row_out) row_out[r] = (uint32_t)q;
+        col_out[(size_t)r * cs] = (uint32_t)((uint64_t)key[i] - q * div);
+        if (off_out) {
+            const uint64_t q0 = idx == 0 ? 0ull : row_of(before) + 1ull;  // rows after the previous run's row
+            for (uint64_t qq = q0; qq <= q && qq <= nrows; ++qq) off_out[qq] = r;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < UQ_ITEMS; ++i) {
+        const size_t idx = base + (size_t)i * 32 + l;
+        const bool valid = key[i] < sentinel;
         K after = __shfl_down_sync(0xffffffffu, key[i], 1);
         if (l == 31) after = (idx + 1 < cnt) ? (K)(keys[idx + 1] >> ks) : sentinel;
-        K before = up;
-        if (l == 0) before = idx > 0 ? (K)(keys[idx - 1] >> ks) : sentinel;
         if (!valid) continue;
         const uint32_t f = (head_bits >> i) & 1u;
         const uint32_t r = tbase + ex[i] + f - 1u;
-        if (tail) {
-            if (whole_head && after != key[i]) w_out[(size_t)r * cs] = v;
-            else atomicMin(&w_out[(size_t)r * cs], v);
-        }
-        const auto row_of = [&](K kk) -> uint64_t {
-            return div_shift >= 0 ? ((uint64_t)kk >> div_shift) : (uint64_t)kk / div;
-        };
-        const uint64_t q = row_of(key[i]);
-        if (f) {
-            if (row_out) row_out[r] = (uint32_t)q;
-            col_out[(size_t)r * cs] = (uint32_t)((uint64_t)key[i] - q * div);
-            if (off_out) {
-                const uint64_t q0 = idx == 0 ? 0ull : row_of(before) + 1ull;  // rows after the previous run's row
-                for (uint64_t qq = q0; qq <= q && qq <= nrows; ++qq) off_out[qq] = r;
-            }
-        }
-        if (off_out && tail && !(after < sentinel))  // the last run: the remaining rows end at the total
-            for (uint64_t qq = q + 1; qq <= nrows; ++qq) off_out[qq] = (uint64_t)r + 1;
+        if (!f) atomicMin(&w_out[(size_t)r * cs], val[i]);
+        // the last run: the remaining rows end at the total
+        if (off_out && !(after < sentinel))
+            for (uint64_t qq = row_of(key[i]) + 1; qq <= nrows; ++qq) off_out[qq] = (uint64_t)r + 1;
     }
 }
 

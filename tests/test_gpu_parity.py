@@ -332,3 +332,36 @@ def test_device_inputs(cd):
     og = oracle.build_csr(e.n, e.src, e.dst, e.w)
     off, col, w, _ = g.copy()
     assert np.array_equal(off, og.off) and np.array_equal(col, og.col)
+
+
+def test_pinned_host_inputs(cd):
+    # pinned host edge arrays are read in place by the emission kernel (no staging copy)
+    torch = pytest.importorskip("torch")
+    e = inputs.rmat(12, 8, 1000, 6)
+    t = [torch.from_numpy(a.view(np.int32).copy()).pin_memory() for a in (e.src, e.dst, e.w)]
+    g = cd.build_csr(t[0], t[1], t[2], e.n)
+    og = oracle.build_csr(e.n, e.src, e.dst, e.w)
+    off, col, w, orig = g.copy()
+    assert np.array_equal(off, og.off) and np.array_equal(col, og.col) and np.array_equal(w, og.wt)
+    assert np.array_equal(orig, og.orig)
+    r = cd.run(t[0], t[1], t[2], e.n, 0.8, 5)
+    ores, _, _ = oracle.cldiam(og, 0.8, 5)
+    assert (r["k"], r["phi_approx"]) == (ores.k, ores.phi_approx)
+
+
+def test_initial_delta_experiment_small(cd):
+    # Section 5's initial-Delta experiment on a small two-weight mesh: both starts agree with the
+    # oracle, and starting at the diameter gives a much worse ratio than starting at the minimum weight
+    e = inputs.grid(128, 10, 7)
+    w = np.where(e.w == 1, 1_000_000, 1).astype(np.uint32)
+    g = cd.build_csr(e.src, e.dst, w, e.n)
+    og = oracle.build_csr(e.n, e.src, e.dst, w)
+    lb, _ = oracle.lower_bound(og, 0)
+    ratios = []
+    for mode, d0 in ((cd.DELTA0_MIN, 0), (cd.DELTA0_EXPLICIT, lb)):
+        r = cd.estimate(cd.quotient_build(cd.cluster(g, 0.5, 3, delta0_mode=mode, delta0=d0)))
+        ocl = oracle.cluster(og, 0.5, 3, oracle.delta0(og, oracle.DELTA0_MIN) if d0 == 0 else d0)
+        ores = oracle.estimate(oracle.quotient(og, ocl), ocl)
+        assert (r["k"], r["phi_approx"], r["steps"]) == (ores.k, ores.phi_approx, ocl.stats["steps"])
+        ratios.append(r["phi_approx"] / lb)
+    assert ratios[0] < 1.01 and ratios[1] > 2.0, ratios
