@@ -191,6 +191,18 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     uint32_t* cf = cfA.get();
     uint32_t* cf2 = cfB.get();
     const unsigned max_relax_grid = (unsigned)num_sms() * 8;
+    // relax CTAs loop over chunks: launch exactly the resident ones (shared memory limits them to a few per
+    // SM), so that no second, partial wave of CTAs runs after the first has finished its chunks
+    static int relax_per_sm[64];
+    int dev = 0;
+    CLD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || relax_per_sm[dev] == 0) {
+        int per_sm = 0;
+        CLD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_relax, RT, 0));
+        if (dev >= 0 && dev < 64) relax_per_sm[dev] = std::max(1, per_sm);
+        else relax_per_sm[0] = std::max(1, per_sm);
+    }
+    const unsigned relax_grid = (unsigned)num_sms() * (unsigned)relax_per_sm[(dev >= 0 && dev < 64) ? dev : 0];
     uint32_t nf = 0, E = 0;
 
     // list every relaxer (stage start, or after Delta doubled)
@@ -226,10 +238,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                 ++stepid;
                 updated = 0;
                 if (nf > 0) {
-                    CLD_TRY(zero_field(offsetof(Counters, newly_covered), 8));
-                    CLD_TRY(zero_field(offsetof(Counters, front), 8));
-                    CLD_TRY(zero_field(offsetof(Counters, nnext), 4));
-                    const unsigned rg = (unsigned)std::min<uint64_t>((E + RC - 1) / RC, max_relax_grid);
+                    CLD_TRY(zero_field(offsetof(Counters, newly_covered), 24));  // newly_covered, front, nnext
+                    const unsigned rg = (unsigned)std::min<uint64_t>((E + RC - 1) / RC, relax_grid);
                     CLD_K(K_RELAX, s, k_relax<<<rg, RT, 0, s>>>(fv, fk, fp, cf, nf, E, g->adj, center.get(),
                                                                  cumulative ? D.get() : nullptr, key.get(), delta,
                                                                  stamp.get(), stepid, next.get(), ctr.get()));

@@ -30,22 +30,28 @@
 // CTA there is no kernel boundary to drop stale L1 lines between phases.
 #pragma once
 
+#include <cstddef>
+
 #include "common.cuh"
 
 namespace cld {
 
 struct Counters {
     unsigned long long selected;       // centers drawn in this stage
-    unsigned long long newly_covered;  // nodes that got their first key this step
     unsigned long long edges_scanned;  // adjacency entries read by relax
     unsigned long long frozen;         // nodes frozen by finalize
     unsigned long long frozen_deg;     // their degree sum
+    // reset before every growing step (one contiguous block)
+    unsigned long long newly_covered;  // nodes that got their first key this step
     unsigned long long front;          // next frontier: (entries << 32) | adjacency entries
     uint32_t nnext;                    // changed nodes this step
+    uint32_t pad;
+    // others
     uint32_t growable;                 // some covered/frozen node touches an uncovered one
     uint32_t overflow;                 // a D_v reached 2^32 - 1
-    uint32_t pad;
 };
+static_assert(offsetof(Counters, pad) + 4 - offsetof(Counters, newly_covered) == 24,
+              "the per-step counters form one block");
 
 constexpr int RT = 256;                        // relax threads per CTA in the grid form
 constexpr int RU = 4;                          // adjacency entries per relax thread per chunk (grid form)
@@ -269,7 +275,7 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
             cp_async_8(&sm.key[b][j], &fkey[i0 + j]);
         }
     };
-    uint32_t chunk = br;
+    uint32_t chunk = br;  // chunks br, br + nb, ...
     if ((uint64_t)chunk * CL >= E) return;
     uint32_t i0, cnt;
     range_of(chunk, i0, cnt);
