@@ -264,11 +264,11 @@ cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, 
 cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
                                     uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
-// The same for packed items (row << col_bits | col) << wb | value, sorted on
-// their key bits; items whose key bits are all ones are skipped.
-cldiam_status unique_min_packed_u64(const uint64_t* items, int wb, size_t cnt, int col_bits, uint32_t* row_out,
-                                    uint32_t* col_out, uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
-                                    uint32_t* total_dev, cudaStream_t s);
+// The same for packed CSR items (row << vb | col) << (64 - 2 vb) | w, sorted on their (row, col) bits
+// (~0 marks a dropped item): row_out[r], adj_out[r] = (col, min w) per unique (row, col), the offsets
+// off_out[0..nrows] and the count in *total_dev, in one look-back pass.  adj_out needs no pre-fill.
+cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint32_t* row_out, uint2* adj_out,
+                                uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
 
 // CSR offsets off[0..n] of entries whose (sorted) row ids are row[0..nnz):
 // off[u] = index of the first entry with row >= u.  No atomics, no scan.

@@ -64,11 +64,6 @@ __global__ void k_emit_packed(const uint32_t* __restrict__ src, const uint32_t* 
     if (__any_sync(0xffffffffu, wd) && lane_id() == 0) atomicExch(wide, 1u);
 }
 
-__global__ void k_widen_offsets(const uint32_t* __restrict__ excl, uint32_t n, uint32_t total, uint64_t* __restrict__ off) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
-        off[i] = (i == n) ? (uint64_t)total : (uint64_t)excl[i];
-}
-
 __global__ void k_iota(uint32_t* __restrict__ a, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
 }
@@ -193,25 +188,58 @@ __global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t*
         }
 }
 
+// new offsets (widened from the 32-bit scan of the kept degrees) and, for each kept node orig[i], its
+// new id and the shift from its old adjacency positions to its new ones (positions are < 2^32, so
+// the shift is taken modulo 2^32); map of a dropped node keeps its 0xFFFFFFFF pre-fill
+__global__ void k_lcc_offsets(const uint32_t* __restrict__ excl, uint32_t n_out, uint32_t total,
+                              const uint32_t* __restrict__ orig, const uint64_t* __restrict__ off,
+                              uint64_t* __restrict__ noff, uint2* __restrict__ map) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_out; i += gridDim.x * blockDim.x) {
+        noff[i] = (i == n_out) ? (uint64_t)total : (uint64_t)excl[i];
+        if (i < n_out) {
+            const uint32_t u = orig[i];
+            map[u] = make_uint2(i, excl[i] - (uint32_t)off[u]);
+        }
+    }
+}
+
 // copy of the kept rows with new ids (monotone, so rows stay sorted), and the
-// weight statistics of the copy: sum over u < v and minimum
-__global__ void k_lcc_copy(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid,
-                           const uint64_t* __restrict__ off, const uint32_t* __restrict__ row,
-                           const uint2* __restrict__ adj, uint64_t nnz, const uint64_t* __restrict__ noff,
-                           uint32_t* __restrict__ nrow, uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
-                           uint32_t* __restrict__ wmin) {
+// weight statistics of the copy: sum over u < v and minimum.  Each thread
+// handles LU entries a grid stride apart with all their loads issued first.
+__global__ void __launch_bounds__(256) k_lcc_copy(const uint2* __restrict__ map, const uint32_t* __restrict__ newid,
+                                                  const uint32_t* __restrict__ row, const uint2* __restrict__ adj,
+                                                  uint64_t nnz, uint32_t* __restrict__ nrow, uint2* __restrict__ nadj,
+                                                  unsigned long long* __restrict__ wsum, uint32_t* __restrict__ wmin) {
+    constexpr int LU = 4;
     unsigned long long sum = 0;
     uint32_t mn = 0xFFFFFFFFu;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = row[i];
-        if (!keep[u]) continue;
-        uint32_t nu = newid[u];
-        uint64_t pos = noff[nu] + (i - off[u]);
-        uint2 e = adj[i];
-        nadj[pos] = make_uint2(newid[e.x], e.y);
-        nrow[pos] = nu;
-        if (u < e.x) sum += e.y;
-        mn = e.y < mn ? e.y : mn;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnz; b += stride * LU) {
+        uint32_t u[LU];
+        uint2 e[LU], mp[LU];
+        uint32_t nv[LU];
+#pragma unroll
+        for (int k = 0; k < LU; ++k) {
+            const uint64_t i = b + (uint64_t)k * stride;
+            u[k] = i < nnz ? row[i] : 0u;
+            e[k] = i < nnz ? adj[i] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < LU; ++k) {
+            const uint64_t i = b + (uint64_t)k * stride;
+            mp[k] = i < nnz ? map[u[k]] : make_uint2(0xFFFFFFFFu, 0u);
+            nv[k] = i < nnz ? newid[e[k].x] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < LU; ++k) {
+            if (mp[k].x == 0xFFFFFFFFu) continue;  // dropped row, or past the end
+            const uint64_t i = b + (uint64_t)k * stride;
+            const uint32_t pos = (uint32_t)i + mp[k].y;
+            nadj[pos] = make_uint2(nv[k], e[k].y);
+            nrow[pos] = mp[k].x;
+            if (u[k] < e[k].x) sum += e[k].y;
+            mn = e[k].y < mn ? e[k].y : mn;
+        }
     }
     sum = block_reduce(sum, [](unsigned long long a, unsigned long long b) { return a + b; }, 0ull);
     if (threadIdx.x == 0 && sum) atomicAdd(wsum, sum);
@@ -320,7 +348,6 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(deg.alloc((size_t)n + 1, s));
     CLD_TRY(degx.alloc((size_t)n + 1, s));
     CLD_TRY(off.alloc((size_t)n + 1, s));
-    CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));
     bool packed = wb >= 1;
     if (packed) {
         DBuf<uint64_t> items, items2;
@@ -340,12 +367,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             bool alt = false;
             CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s));
             // unique (row, col) runs with their lightest weight, in one look-back pass
-            CLD_TRY(unique_min_packed_u64(alt ? items2.get() : items.get(), wb, cnt, vb, row.get(), &adj.get()->x,
-                                          &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
+            CLD_TRY(unique_packed_csr(alt ? items2.get() : items.get(), cnt, vb, row.get(), adj.get(), off.get(), n,
+                                      scal.get() + 1, s));
         }
     }
     if (!packed) {
         // keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
+        CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));  // run minima fold in
         const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
         DBuf<uint64_t> keys, keys2;
         DBuf<uint32_t> vals, vals2;
@@ -457,13 +485,16 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(noff.alloc((size_t)n_out + 1, s));
         CLD_TRY(nadj.alloc(nnz_out ? nnz_out : 1, s));
         CLD_TRY(nrow.alloc(nnz_out ? nnz_out : 1, s));
-        CLD_K(K_CSR, s, k_widen_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
-                                                                          noff.get()));
+        DBuf<uint2> map;
+        CLD_TRY(map.alloc(n, s));
+        CLD_CUDA(cudaMemsetAsync(map.get(), 0xFF, (size_t)n * 8, s));
+        CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
+                                                                                    orig.get(), off.get(), noff.get(),
+                                                                                    map.get()));
         CLD_LAUNCH_CHECK();
         if (nnz) {
-            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(),
-                                                                         row.get(), adj.get(), nnz, noff.get(),
-                                                                         nrow.get(), nadj.get(), wsum.get(),
+            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(map.get(), newid.get(), row.get(), adj.get(),
+                                                                         nnz, nrow.get(), nadj.get(), wsum.get(),
                                                                          scal.get() + 6));
             CLD_LAUNCH_CHECK();
         }

@@ -339,18 +339,32 @@ __global__ void k_os_hist_scan(uint32_t* __restrict__ hist, int npass) {
     }
 }
 
-// KV: items carry a 32-bit value (vin/vout); otherwise keys only.
-template <class K, bool KV, int OS_ITEMS = OsCfg<K, KV>::ITEMS, int OS_TILE = OsCfg<K, KV>::TILE>
+// Digit (key >> shift) & 0xFF.  For 64-bit keys HI says shift >= 32 (uniform per pass), so the
+// digit comes from one 32-bit word, or from a funnel shift of the two when it may straddle them.
+template <class K, bool HI>
+__device__ __forceinline__ uint32_t os_digit(K k, uint32_t sh) {
+    if constexpr (sizeof(K) == 8) {
+        const uint32_t lo = (uint32_t)k, hi = (uint32_t)((uint64_t)k >> 32);
+        if constexpr (HI) return (hi >> sh) & 0xFFu;
+        else return __funnelshift_r(lo, hi, sh) & 0xFFu;
+    } else {
+        return ((uint32_t)k >> sh) & 0xFFu;
+    }
+}
+
+// KV: items carry a 32-bit value (vin/vout); otherwise keys only.  sh = shift mod 32 (HI: shift >= 32).
+template <class K, bool KV, bool HI, int OS_ITEMS = OsCfg<K, KV>::ITEMS, int OS_TILE = OsCfg<K, KV>::TILE>
 __global__ void __launch_bounds__(OS_THREADS, 4)
     k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-              uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ goff,
+              uint32_t* __restrict__ vout, size_t n, uint32_t sh, const uint32_t* __restrict__ goff,
               unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     K* s_key = reinterpret_cast<K*>(os_smem);
     uint32_t* s_val = reinterpret_cast<uint32_t*>(os_smem + sizeof(K) * OS_TILE);
+    // whist[w][d]: first the count of digit d among warp w's items, then the tile position of warp w's
+    // first d item; gdiff[d]: output position of the tile's first d item minus its tile position
     __shared__ uint32_t whist[OS_WARPS][OS_RADIX];
-    __shared__ uint32_t tstart[OS_RADIX];
-    __shared__ uint32_t gbase[OS_RADIX];
+    __shared__ uint32_t gdiff[OS_RADIX];
     __shared__ uint32_t wsum[OS_WARPS];
     __shared__ uint32_t s_tile;
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
@@ -359,59 +373,80 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
     __syncthreads();
     const uint32_t tile = s_tile;
     const size_t tbase = (size_t)tile * OS_TILE;
+    const uint32_t rem = (uint32_t)min((size_t)OS_TILE, n - tbase);  // items in this tile
+    const K* kt = kin + tbase;
+    const uint32_t* vt = KV ? vin + tbase : nullptr;
+    const uint32_t lbase = w * (OS_ITEMS * 32) + l;  // tile position of this thread's item 0 (warp-striped)
     const unsigned ltmask = lanemask_lt();
 
     K key[OS_ITEMS];
     uint32_t val[KV ? OS_ITEMS : 1];
+    uint32_t dig_pk[(OS_ITEMS + 3) / 4];   // digits, four per word
     uint32_t rank_pk[(OS_ITEMS + 1) / 2];  // warp-local ranks (< 32 * OS_ITEMS) as 16-bit halves; 0xFFFF = no item
     // issue every load of the tile before ranking, so they are in flight together
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
-        const size_t idx = tbase + (size_t)w * (OS_ITEMS * 32) + (size_t)i * 32 + l;
-        const bool valid = idx < n;
-        key[i] = valid ? kin[idx] : (K)0;
-        if constexpr (KV) val[i] = valid ? vin[idx] : 0u;
+        const uint32_t li = lbase + (uint32_t)i * 32;
+        key[i] = li < rem ? kt[li] : (K)0;
+        if constexpr (KV) val[i] = li < rem ? vt[li] : 0u;
     }
+    // stable warp-local ranks: peers with the same digit (match), counted in item order then lane order;
+    // every peer reads the running count (one broadcast word), the highest peer writes it back
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
-        const size_t idx = tbase + (size_t)w * (OS_ITEMS * 32) + (size_t)i * 32 + l;
-        const bool valid = idx < n;
-        const uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xFF) : 0x100u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned leader = __ffs(peers) - 1;
-        uint32_t b = 0;
-        if (valid && l == leader) {
-            b = whist[w][d];
-            whist[w][d] = b + (uint32_t)__popc(peers);
-        }
-        b = __shfl_sync(0xffffffffu, b, leader);
-        const uint32_t rk = valid ? b + (uint32_t)__popc(peers & ltmask) : 0xFFFFu;
+        const bool valid = lbase + (uint32_t)i * 32 < rem;
+        const uint32_t d = os_digit<K, HI>(key[i], sh);
+        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        const uint32_t cur = whist[w][d];
+        __syncwarp();
+        if (valid && (peers >> l) == 1u) whist[w][d] = cur + (uint32_t)__popc(peers);
+        const uint32_t rk = valid ? cur + (uint32_t)__popc(peers & ltmask) : 0xFFFFu;
         if (i % 2 == 0) rank_pk[i / 2] = rk;
         else rank_pk[i / 2] |= rk << 16;
+        if (i % 4 == 0) dig_pk[i / 4] = d;
+        else dig_pk[i / 4] |= d << (8 * (i % 4));
         __syncwarp();
     }
     __syncthreads();
 
-    // per digit (thread d): warp offsets within the tile, tile count, publication, look-back
+    // per digit (thread d): tile count, publication, tile-local scan, look-back
     const unsigned d = tid;
+    const uint32_t g0 = goff[d];
     uint32_t cnt = 0;
 #pragma unroll
-    for (int ww = 0; ww < OS_WARPS; ++ww) {
-        uint32_t t = whist[ww][d];
-        whist[ww][d] = cnt;
-        cnt += t;
-    }
+    for (int ww = 0; ww < OS_WARPS; ++ww) cnt += whist[ww][d];
     volatile unsigned long long* vst = status;
     if (tile == 0) vst[d] = OS_PRE | cnt;
     else vst[(size_t)tile * OS_RADIX + d] = OS_AGG | cnt;
-    // tile-local exclusive scan over digits
+    uint32_t tst;
     {
-        uint32_t incl = warp_incl_scan(cnt);
+        const uint32_t incl = warp_incl_scan(cnt);
         if (l == 31) wsum[w] = incl;
         __syncthreads();
         uint32_t off = 0;
         for (unsigned ww = 0; ww < w; ++ww) off += wsum[ww];
-        tstart[d] = off + incl - cnt;
+        tst = off + incl - cnt;
+    }
+    {
+        uint32_t run = tst;  // only thread d touches column d of whist here
+#pragma unroll
+        for (int ww = 0; ww < OS_WARPS; ++ww) {
+            const uint32_t cw = whist[ww][d];
+            whist[ww][d] = run;
+            run += cw;
+        }
+    }
+    __syncthreads();
+    // stage in digit order (tile positions suffice); the keys are dead before the look-back
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const uint32_t rk = (rank_pk[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
+        if (rk != 0xFFFFu) {
+            const uint32_t dd = (dig_pk[i / 4] >> (8 * (i % 4))) & 0xFFu;
+            const uint32_t pos = whist[w][dd] + rk;
+            s_key[pos] = key[i];
+            if constexpr (KV) s_val[pos] = val[i];
+        }
     }
     uint32_t excl = 0;
     if (tile > 0) {
@@ -445,28 +480,25 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         }
         vst[(size_t)tile * OS_RADIX + d] = OS_PRE | (excl + cnt);
     }
-    gbase[d] = goff[d] + excl;
+    gdiff[d] = g0 + excl - tst;  // modulo 2^32; positions are < 2^32
     __syncthreads();
-
-    // stage in digit order
+    // write out: consecutive threads take consecutive staged items, i.e. runs of equal digits
+    if (rem == (uint32_t)OS_TILE) {
 #pragma unroll
-    for (int i = 0; i < OS_ITEMS; ++i) {
-        const uint32_t rk = (rank_pk[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-        if (rk != 0xFFFFu) {
-            const uint32_t dd = (uint32_t)((key[i] >> shift) & 0xFF);
-            const uint32_t pos = tstart[dd] + whist[w][dd] + rk;
-            s_key[pos] = key[i];
-            if constexpr (KV) s_val[pos] = val[i];
+        for (int j = 0; j < OS_ITEMS; ++j) {
+            const uint32_t i = (uint32_t)j * OS_THREADS + tid;
+            const K k = s_key[i];
+            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh)] + i;
+            kout[pos] = k;
+            if constexpr (KV) vout[pos] = s_val[i];
         }
-    }
-    __syncthreads();
-    const uint32_t tcount = (uint32_t)min((size_t)OS_TILE, n - tbase);
-    for (uint32_t i = tid; i < tcount; i += OS_THREADS) {
-        const K k = s_key[i];
-        const uint32_t dd = (uint32_t)((k >> shift) & 0xFF);
-        const size_t pos = (size_t)gbase[dd] + (i - tstart[dd]);
-        kout[pos] = k;
-        if constexpr (KV) vout[pos] = s_val[i];
+    } else {
+        for (uint32_t i = tid; i < rem; i += OS_THREADS) {
+            const K k = s_key[i];
+            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh)] + i;
+            kout[pos] = k;
+            if constexpr (KV) vout[pos] = s_val[i];
+        }
     }
 }
 
@@ -486,8 +518,14 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[kv][dev]) {
-        if (kv) CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (kv) {
+            CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, true, false>, a, (int)smem));
+            CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, true, true>, a, (int)smem));
+        } else {
+            CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, false, false>, a, (int)smem));
+            CLD_CUDA(cudaFuncSetAttribute(k_os_pass<K, false, true>, a, (int)smem));
+        }
         if (dev >= 0 && dev < 64) attr_set[kv][dev] = true;
     }
     DBuf<uint32_t> hist, ctl;
@@ -508,16 +546,24 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
     bool alt = false;
     for (int p = 0; p < npass; ++p) {
         CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * OS_RADIX * 8, s));
-        if (kv) {
-            CLD_K(K_RADIX_SCATTER, s,
-                  k_os_pass<K, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, shift0 + 8 * p,
-                                                                      hist.get() + p * OS_RADIX, status.get(),
-                                                                      ctl.get() + p, ctl.get() + 2 * npass));
+        const int shift = shift0 + 8 * p;
+        const bool hi = sizeof(K) == 8 && shift >= 32;
+        const uint32_t sh = (uint32_t)shift & 31u;
+        const uint32_t* go = hist.get() + p * OS_RADIX;
+        uint32_t* tc = ctl.get() + p;
+        uint32_t* er = ctl.get() + 2 * npass;
+        if (kv && hi) {
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, go,
+                                                                                              status.get(), tc, er));
+        } else if (kv) {
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, false><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, go,
+                                                                                               status.get(), tc, er));
+        } else if (hi) {
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, false, true><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n,
+                                                                                               sh, go, status.get(), tc, er));
         } else {
-            CLD_K(K_RADIX_SCATTER, s,
-                  k_os_pass<K, false><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n, shift0 + 8 * p,
-                                                                       hist.get() + p * OS_RADIX, status.get(),
-                                                                       ctl.get() + p, ctl.get() + 2 * npass));
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, false, false><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n,
+                                                                                                sh, go, status.get(), tc, er));
         }
         CLD_LAUNCH_CHECK();
         // algorithmic bytes: every item (key and value) read once and written once
@@ -542,9 +588,7 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
 // run inside a warp, or one atomicMin per run piece per warp otherwise.
 // Output per unique key: row_out[r] = key / div (if row_out), col_out[r*cs] =
 // key % div, w_out[r*cs] = min value (w_out pre-filled with 0xFFFFFFFF).
-// Keys >= sentinel are ignored (they sort last).  Packed items (vals ==
-// nullptr, wb > 0) hold the value in their low wb bits and the key above it;
-// div_shift >= 0 replaces the division by a shift (div = 2^div_shift).
+// Keys >= sentinel are ignored (they sort last).
 // With off_out, the run heads also write the CSR offsets of rows
 // 0..nrows: off_out[q] = index of the first unique key with row >= q (a head
 // fills the rows after its predecessor's row up to its own; the last run
@@ -555,7 +599,7 @@ constexpr int UQ_TILE = UQ_THREADS * UQ_ITEMS;
 
 // heads of each tile (first pass)
 template <class K>
-__global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const K* __restrict__ keys, int ks, size_t cnt,
+__global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const K* __restrict__ keys, size_t cnt,
                                                               K sentinel, uint32_t* __restrict__ heads) {
     __shared__ uint32_t s_w[UQ_THREADS / 32];
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
@@ -564,14 +608,14 @@ __global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const K* __restrict
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
-        key[i] = idx < cnt ? (K)(keys[idx] >> ks) : sentinel;
+        key[i] = idx < cnt ? keys[idx] : sentinel;
     }
     uint32_t run = 0;
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
         K prev = __shfl_up_sync(0xffffffffu, key[i], 1);
-        if (l == 0) prev = (idx > 0 && idx < cnt) ? (K)(keys[idx - 1] >> ks) : sentinel;
+        if (l == 0) prev = (idx > 0 && idx < cnt) ? keys[idx - 1] : sentinel;
         run += (uint32_t)__popc(__ballot_sync(0xffffffffu, key[i] < sentinel && (idx == 0 || prev != key[i])));
     }
     if (l == 0) s_w[w] = run;
@@ -586,8 +630,8 @@ __global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const K* __restrict
 // second pass: tile t's heads get indices from first[t] on
 template <class K>
 __global__ void __launch_bounds__(UQ_THREADS, 4)
-    k_unique_write(const K* __restrict__ keys, const uint32_t* __restrict__ vals, int wb, size_t cnt, K sentinel,
-                   uint64_t div, int div_shift, uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out,
+    k_unique_write(const K* __restrict__ keys, const uint32_t* __restrict__ vals, size_t cnt, K sentinel,
+                   uint64_t div, uint32_t* __restrict__ row_out, uint32_t* __restrict__ col_out,
                    uint32_t* __restrict__ w_out, int cs, uint64_t* __restrict__ off_out, uint32_t nrows,
                    const uint32_t* __restrict__ first) {
     __shared__ uint32_t s_woff[UQ_THREADS / 32], s_prefix;
@@ -596,27 +640,19 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
     const size_t base = (size_t)tile * UQ_TILE + (size_t)w * (UQ_ITEMS * 32);
     K key[UQ_ITEMS];
     uint32_t val[UQ_ITEMS];
-    const K wmask = (K)((1ull << wb) - 1ull);
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
-        if (vals) {
-            key[i] = idx < cnt ? keys[idx] : sentinel;
-            val[i] = idx < cnt ? vals[idx] : 0xFFFFFFFFu;
-        } else {
-            const K it = idx < cnt ? keys[idx] : (K)0;
-            key[i] = idx < cnt ? (K)(it >> wb) : sentinel;
-            val[i] = idx < cnt ? (uint32_t)(it & wmask) : 0xFFFFFFFFu;
-        }
+        key[i] = idx < cnt ? keys[idx] : sentinel;
+        val[i] = idx < cnt ? vals[idx] : 0xFFFFFFFFu;
     }
-    const int ks = vals ? 0 : wb;  // key of a neighbouring item read from memory
     uint32_t head_bits = 0, run = 0;
     uint32_t ex[UQ_ITEMS];
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
         K prev = __shfl_up_sync(0xffffffffu, key[i], 1);
-        if (l == 0) prev = (idx > 0 && idx < cnt) ? (K)(keys[idx - 1] >> ks) : sentinel;
+        if (l == 0) prev = (idx > 0 && idx < cnt) ? keys[idx - 1] : sentinel;
         const bool f = key[i] < sentinel && (idx == 0 || prev != key[i]);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
         ex[i] = run + (uint32_t)__popc(bal & lanemask_lt());
@@ -643,17 +679,15 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
     // that may continue into the next tile has its head fold in with atomicMin too (w_out holds
     // 0xFFFFFFFF beforehand), as do items whose run began in an earlier tile.
     const size_t tend = min(cnt, (size_t)(tile + 1) * UQ_TILE);
-    const K lastkey = (K)(keys[tend - 1] >> ks);
-    const bool crosses = tend < cnt && (K)(keys[tend] >> ks) == lastkey && lastkey < sentinel;
-    const auto row_of = [&](K kk) -> uint64_t {
-        return div_shift >= 0 ? ((uint64_t)kk >> div_shift) : (uint64_t)kk / div;
-    };
+    const K lastkey = keys[tend - 1];
+    const bool crosses = tend < cnt && keys[tend] == lastkey && lastkey < sentinel;
+    const auto row_of = [&](K kk) -> uint64_t { return (uint64_t)kk / div; };
 #pragma unroll
     for (int i = 0; i < UQ_ITEMS; ++i) {
         const size_t idx = base + (size_t)i * 32 + l;
         const bool valid = key[i] < sentinel;
         K before = __shfl_up_sync(0xffffffffu, key[i], 1);
-        if (l == 0) before = idx > 0 ? (K)(keys[idx - 1] >> ks) : sentinel;
+        if (l == 0) before = idx > 0 ? keys[idx - 1] : sentinel;
         const uint32_t f = (head_bits >> i) & 1u;
         if (!valid || !f) continue;
         const uint32_t r = tbase + ex[i];
@@ -673,7 +707,7 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
         const size_t idx = base + (size_t)i * 32 + l;
         const bool valid = key[i] < sentinel;
         K after = __shfl_down_sync(0xffffffffu, key[i], 1);
-        if (l == 31) after = (idx + 1 < cnt) ? (K)(keys[idx + 1] >> ks) : sentinel;
+        if (l == 31) after = (idx + 1 < cnt) ? keys[idx + 1] : sentinel;
         if (!valid) continue;
         const uint32_t f = (head_bits >> i) & 1u;
         const uint32_t r = tbase + ex[i] + f - 1u;
@@ -685,8 +719,8 @@ __global__ void __launch_bounds__(UQ_THREADS, 4)
 }
 
 template <class K>
-static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, int wb, size_t cnt, K sentinel,
-                                       uint64_t div, int div_shift, uint32_t* row_out, uint32_t* col_out,
+static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size_t cnt, K sentinel,
+                                       uint64_t div, uint32_t* row_out, uint32_t* col_out,
                                        uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
                                        uint32_t* total_dev, cudaStream_t s) {
     if (cnt == 0) {
@@ -699,10 +733,10 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, int 
     DBuf<uint32_t> heads, first;
     CLD_TRY(heads.alloc(ntiles, s));
     CLD_TRY(first.alloc(ntiles, s));
-    CLD_K(K_CSR, s, k_unique_count<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals ? 0 : wb, cnt, sentinel, heads.get()));
+    CLD_K(K_CSR, s, k_unique_count<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, cnt, sentinel, heads.get()));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, total_dev, s));
-    CLD_K(K_CSR, s, k_unique_write<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, wb, cnt, sentinel, div, div_shift,
+    CLD_K(K_CSR, s, k_unique_write<K><<<ntiles, UQ_THREADS, 0, s>>>(keys, vals, cnt, sentinel, div,
                                                                      row_out, col_out, w_out, cs, off_out, nrows,
                                                                      first.get()));
     CLD_LAUNCH_CHECK();
@@ -713,23 +747,218 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, int 
     return CLDIAM_OK;
 }
 
+// ------------------------------------------------------------------ CSR de-duplication of packed items
+// Items (row << vb | col) << wb | w with wb = 64 - 2 vb, sorted on their (row, col) bits; ~0 marks a
+// dropped item (self-loop) and sorts last.  One pass: tile t flags its run heads, publishes its head
+// count and finds the heads of all earlier tiles by a warp-wide decoupled look-back over one status
+// word per tile, then writes row_out[r], adj_out[r] = (col, w) for its heads and the CSR offsets.
+// Run minima: a head stores its own weight, and after a block barrier every other item of a run
+// headed in the same tile folds its weight in with atomicMin; the items of the tile's last run that
+// lie in later tiles are read by the head's tile (a warp scanning forward) and folded in the same way,
+// so a tile never touches a run headed in an earlier one and adj_out needs no pre-fill.
+constexpr int UP_THREADS = 256;
+constexpr int UP_WARPS = UP_THREADS / 32;
+constexpr int UP_ITEMS = 8;
+constexpr int UP_TILE = UP_THREADS * UP_ITEMS;
+constexpr unsigned long long UP_AGG = 1ull << 32;  // status: tile's own head count
+constexpr unsigned long long UP_PRE = 2ull << 32;  // status: heads in tiles 0..t
+
+__global__ void __launch_bounds__(UP_THREADS)
+    k_unique_packed(const uint64_t* __restrict__ items, uint32_t cnt, int vb, uint32_t* __restrict__ row_out,
+                    uint2* __restrict__ adj_out, uint64_t* __restrict__ off_out, uint32_t nrows,
+                    unsigned long long* __restrict__ status, uint32_t* __restrict__ ctl, uint32_t* __restrict__ total) {
+    __shared__ uint32_t s_woff[UP_WARPS];  // heads per warp, then the global index of the warp's first head
+    __shared__ uint32_t s_tile, s_first, s_count;
+    const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
+    if (tid == 0) s_tile = atomicAdd(&ctl[0], 1u);  // tiles in start order: earlier tiles are running or done
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tbase = (uint64_t)tile * UP_TILE;
+    const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
+    const int wb = 64 - 2 * vb;
+    const uint64_t same_lim = 1ull << wb;  // two items with (a ^ b) below this share (row, col)
+    const uint64_t valid_lim = ~0ull << wb;  // items below this are not dropped
+    const uint32_t wmask = wb >= 32 ? 0xFFFFFFFFu : ((1u << wb) - 1u);
+    const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
+    const uint32_t rsh = 32u - (uint32_t)vb;  // row = high word >> rsh
+    const uint32_t wstart = w * (UP_ITEMS * 32);  // tile position of the warp's first item (warp-striped rows of 32)
+    const uint64_t* it = items + tbase;
+
+    uint64_t x[UP_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        const uint32_t li = wstart + (uint32_t)i * 32 + l;
+        x[i] = li < rem ? it[li] : ~0ull;
+    }
+    // the item before the warp's first one (none before position 0: ~0 differs from every valid item)
+    uint64_t carry = ~0ull;
+    if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
+    uint32_t head = 0, rstart = 0, lastv = 0;  // per item bits: run head; first item of its row; last valid item
+    uint32_t ex_pk[UP_ITEMS / 4];               // heads before the item within the warp (< 256), one byte each
+    uint32_t run = 0;
+    unsigned vbal_prev = 0;
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        // previous item: lane l - 1 of this row; for lane 0, lane 31 of the previous row (rotation carry)
+        const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
+        const uint64_t prev = l == 0 ? carry : rot;
+        carry = rot;
+        const bool valid = x[i] < valid_lim;
+        const bool f = valid && (prev ^ x[i]) >= same_lim;
+        const bool rs = f && (prev >= valid_lim || (uint32_t)(prev >> 32) >> rsh != (uint32_t)(x[i] >> 32) >> rsh);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const unsigned vbal = __ballot_sync(0xffffffffu, valid);
+        const uint32_t ex = run + (uint32_t)__popc(bal & lanemask_lt());
+        run += (uint32_t)__popc(bal);
+        if (i % 4 == 0) ex_pk[i / 4] = ex;
+        else ex_pk[i / 4] |= ex << (8 * (i % 4));
+        head |= (f ? 1u : 0u) << i;
+        rstart |= (rs ? 1u : 0u) << i;
+        // last valid item: its successor (lane l + 1, or lane 0 of the next row) is dropped or absent
+        if (i > 0 && l == 31 && ((vbal_prev >> 31) & 1u) && !(vbal & 1u)) lastv |= 1u << (i - 1);
+        if (valid && l < 31 && !((vbal >> (l + 1)) & 1u)) lastv |= 1u << i;
+        vbal_prev = vbal;
+    }
+    if (l == 31 && ((vbal_prev >> 31) & 1u)) {  // the warp's last item: look at the next one in memory
+        const uint64_t pos = tbase + wstart + UP_ITEMS * 32;  // position after the warp's last item
+        if (pos >= cnt || items[pos] >= valid_lim) lastv |= 1u << (UP_ITEMS - 1);
+    }
+    if (l == 0) s_woff[w] = run;
+    __syncthreads();
+
+    if (w == 0) {
+        const uint32_t v = l < UP_WARPS ? s_woff[l] : 0u;
+        const uint32_t incl = warp_incl_scan(v);
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, UP_WARPS - 1);
+        volatile unsigned long long* vst = status;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            if (l == 0) vst[0] = UP_PRE | tot;
+        } else {
+            if (l == 0) vst[tile] = UP_AGG | tot;
+            // lane j reads tile t - j; the window ends at the nearest inclusive prefix; wait (bounded)
+            // only on unpublished tiles before it
+            const long long t0 = clock64();
+            long long t = (long long)tile - 1;
+            bool done = false;
+            while (!done) {
+                const long long j = t - (long long)l;
+                unsigned long long sv = j >= 0 ? (unsigned long long)vst[j] : (unsigned long long)UP_PRE;
+                while (true) {
+                    const unsigned pre = __ballot_sync(0xffffffffu, (sv >> 32) == 2ull);
+                    const unsigned need = pre ? (0xFFFFFFFFu >> (31 - (__ffs(pre) - 1))) : 0xFFFFFFFFu;
+                    const unsigned unpub = __ballot_sync(0xffffffffu, (sv >> 32) == 0ull) & need;
+                    if (!unpub) {
+                        excl += warp_sum(((need >> l) & 1u) ? (uint32_t)sv : 0u);
+                        done = pre != 0;
+                        break;
+                    }
+                    if (__any_sync(0xffffffffu, clock64() - t0 > OS_WAIT_CYCLES)) {  // warp-uniform give-up
+                        if (l == 0) atomicExch(&ctl[1], 1u);
+                        done = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                    if ((sv >> 32) == 0ull) sv = vst[j];
+                }
+                t -= 32;
+            }
+            if (l == 0) vst[tile] = UP_PRE | (excl + tot);
+        }
+        if (l < UP_WARPS) s_woff[l] = excl + incl - v;
+        if (l == 0) {
+            s_first = excl;
+            s_count = tot;
+            if (tile == gridDim.x - 1) *total = excl + tot;
+        }
+    }
+    __syncthreads();
+    const uint32_t woff = s_woff[w], tfirst = s_first;
+
+    // heads: row, (col, own weight), offsets of the rows from the previous item's row + 1 up to theirs
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        if (!((head >> i) & 1u)) continue;
+        const uint32_t r = woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu);
+        const uint32_t row = (uint32_t)(x[i] >> 32) >> rsh;
+        row_out[r] = row;
+        adj_out[r] = make_uint2((uint32_t)(x[i] >> wb) & cmask, (uint32_t)x[i] & wmask);
+        if ((rstart >> i) & 1u) {
+            const uint64_t pos = tbase + wstart + (uint32_t)i * 32 + l;
+            const uint32_t q0 = pos == 0 ? 0u : (uint32_t)(items[pos - 1] >> 32) >> rsh;
+            for (uint32_t q = pos == 0 ? 0u : q0 + 1; q <= row; ++q) off_out[q] = r;
+        }
+    }
+    __syncthreads();
+    // other members of runs headed in this tile; the last valid item closes the offsets
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        const uint32_t li = wstart + (uint32_t)i * 32 + l;
+        if (li >= rem || x[i] >= valid_lim) continue;
+        const uint32_t f = (head >> i) & 1u;
+        const uint32_t before = woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu);  // heads before the item
+        const uint32_t r = before + f - 1u;
+        if (!f && before > tfirst) atomicMin(&adj_out[r].y, (uint32_t)x[i] & wmask);
+        if ((lastv >> i) & 1u) {
+            const uint32_t row = (uint32_t)(x[i] >> 32) >> rsh;
+            for (uint32_t q = row + 1; q <= nrows; ++q) off_out[q] = (uint64_t)r + 1;
+        }
+    }
+    // the tile's last run continuing into later tiles: scan forward while the key repeats
+    if (w == UP_WARPS - 1 && rem == (uint32_t)UP_TILE && s_count > 0 && tbase + UP_TILE < cnt) {
+        const uint64_t last = __shfl_sync(0xffffffffu, x[UP_ITEMS - 1], 31);
+        if (last < valid_lim) {
+            uint32_t mn = 0xFFFFFFFFu;
+            for (uint64_t p = tbase + UP_TILE;; p += 32) {
+                const uint64_t y = p + l < cnt ? items[p + l] : ~0ull;
+                const unsigned same = __ballot_sync(0xffffffffu, y < valid_lim && (y ^ last) < same_lim);
+                const unsigned take = ~same ? (unsigned)(__ffs(~same) - 1) : 32u;  // leading lanes of the run
+                if (l < take) mn = min(mn, (uint32_t)y & wmask);
+                if (take < 32) break;
+            }
+            mn = warp_min(mn);
+            if (l == 0 && mn != 0xFFFFFFFFu) atomicMin(&adj_out[tfirst + s_count - 1].y, mn);
+        }
+    }
+}
+
+cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint32_t* row_out, uint2* adj_out,
+                                uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
+    // every offset is written when some item is kept; zeros cover the case with none
+    CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));
+    if (cnt == 0) {
+        CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
+        return CLDIAM_OK;
+    }
+    if (cnt > 0xFFFFFFFFull - UP_TILE) return fail(CLDIAM_ERR_UNSUPPORTED, "too many items");
+    if (vb < 1 || vb > 32) return fail(CLDIAM_ERR_INVALID_ARG, "packed items need 1..32 id bits");
+    const uint32_t ntiles = (uint32_t)((cnt + UP_TILE - 1) / UP_TILE);
+    DBuf<unsigned long long> status;
+    DBuf<uint32_t> ctl;
+    CLD_TRY(status.alloc(ntiles, s));
+    CLD_TRY(ctl.alloc(2, s));
+    CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * 8, s));
+    CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, 8, s));
+    CLD_K(K_CSR, s, k_unique_packed<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, row_out, adj_out, off_out,
+                                                                  nrows, status.get(), ctl.get(), total_dev));
+    CLD_LAUNCH_CHECK();
+    uint32_t herr = 0;
+    CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(CLDIAM_ERR_TIMEOUT, "de-duplication look-back wait expired");
+    return CLDIAM_OK;
+}
+
 cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, size_t cnt, uint64_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
                                     uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
-    return unique_min_sorted<uint64_t>(keys, vals, 0, cnt, sentinel, div, -1, row_out, col_out, w_out, cs, off_out,
+    return unique_min_sorted<uint64_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, off_out,
                                        nrows, total_dev, s);
-}
-cldiam_status unique_min_packed_u64(const uint64_t* items, int wb, size_t cnt, int col_bits, uint32_t* row_out,
-                                    uint32_t* col_out, uint32_t* w_out, int cs, uint64_t* off_out, uint32_t nrows,
-                                    uint32_t* total_dev, cudaStream_t s) {
-    const uint64_t sentinel = (1ull << (2 * col_bits)) - 1ull;
-    return unique_min_sorted<uint64_t>(items, nullptr, wb, cnt, sentinel, 1ull << col_bits, col_bits, row_out,
-                                       col_out, w_out, cs, off_out, nrows, total_dev, s);
 }
 cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
                                     uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
-    return unique_min_sorted<uint32_t>(keys, vals, 0, cnt, sentinel, div, -1, row_out, col_out, w_out, cs, off_out,
+    return unique_min_sorted<uint32_t>(keys, vals, cnt, sentinel, div, row_out, col_out, w_out, cs, off_out,
                                        nrows, total_dev, s);
 }
 

@@ -92,6 +92,39 @@ def test_csr_wide_items(cd, n, wmax):
     check_csr(cd, n, src, dst, w, False)
 
 
+@pytest.mark.parametrize("case", ["long_runs", "loops_tail", "sparse_rows", "tile_edges"])
+@pytest.mark.parametrize("lcc", [True, False])
+def test_csr_dedup_tile_boundaries(cd, case, lcc):
+    # de-duplication runs 2048 sorted items per tile: runs of one (row, col) spanning several tiles,
+    # dropped self-loops filling whole tiles at the end, rows with no entries, item counts at tile edges
+    rng = np.random.default_rng(["long_runs", "loops_tail", "sparse_rows", "tile_edges"].index(case))
+    if case == "long_runs":
+        n = 300
+        src = np.concatenate([np.full(6000, 7), np.full(2100, 8), rng.integers(0, n, 3000)]).astype(np.uint32)
+        dst = np.concatenate([np.full(6000, 9), np.full(2100, 7), rng.integers(0, n, 3000)]).astype(np.uint32)
+        perm = rng.permutation(src.size)
+        src, dst = src[perm], dst[perm]
+    elif case == "loops_tail":
+        n = 500
+        a = rng.integers(0, n, 7000)
+        src = np.concatenate([a, rng.integers(0, n, 900)]).astype(np.uint32)
+        dst = np.concatenate([a, rng.integers(0, n, 900)]).astype(np.uint32)
+    elif case == "sparse_rows":
+        n = 200_000
+        src = rng.integers(0, n, 5000).astype(np.uint32)
+        dst = (src + rng.integers(1, 4, 5000)).astype(np.uint32) % n
+    else:
+        for m in (1023, 1024, 1025, 2048, 2049):
+            n = 64
+            src = rng.integers(0, n, m).astype(np.uint32)
+            dst = rng.integers(0, n, m).astype(np.uint32)
+            w = rng.integers(1, 1000, m).astype(np.uint32)
+            check_csr(cd, n, src, dst, w, lcc)
+        return
+    w = rng.integers(1, 1 << 20, src.size).astype(np.uint32)
+    check_csr(cd, n, src, dst, w, lcc)
+
+
 def test_csr_degenerate(cd):
     z = np.zeros(0, np.uint32)
     g = cd.build_csr(z, z, z, 1)
