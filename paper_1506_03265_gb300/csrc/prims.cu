@@ -283,43 +283,39 @@ constexpr unsigned long long OS_AGG = 1ull << 32;   // status: tile's own count
 constexpr unsigned long long OS_PRE = 2ull << 32;   // status: inclusive prefix over tiles 0..t
 constexpr long long OS_WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: a look-back that waits longer gives up
 
+// Digit histograms of every pass from one read of the keys: one private histogram per warp and pass
+// in shared memory (warps x npass x 256 words, dynamic), so shared atomics collide only within a warp.
 template <class K>
 __global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass, int shift0,
                                                  uint32_t* __restrict__ hist) {
-    // one private histogram per warp and pass: shared atomics collide only within a warp
-    __shared__ uint32_t h[8][4][OS_RADIX];  // warps x passes (<= 4 per launch) x digits
-    for (int i = threadIdx.x; i < 8 * 4 * OS_RADIX; i += blockDim.x) (&h[0][0][0])[i] = 0;
-    __syncthreads();
+    extern __shared__ uint32_t hs[];
     const unsigned w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < OS_WARPS * npass * OS_RADIX; i += blockDim.x) hs[i] = 0;
+    __syncthreads();
+    uint32_t* h = hs + (size_t)w * npass * OS_RADIX;
     constexpr int U = 8;  // keys loaded per thread before counting, to keep loads in flight
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (int p0 = 0; p0 < npass; p0 += 4) {
-        const int np = min(4, npass - p0);
-        for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += stride * U) {
-            K kk[U];
+    for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += stride * U) {
+        K kk[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const size_t i = base + (size_t)u * stride;
-                kk[u] = i < n ? keys[i] : (K)0;
-            }
+        for (int u = 0; u < U; ++u) {
+            const size_t i = base + (size_t)u * stride;
+            kk[u] = i < n ? keys[i] : (K)0;
+        }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (base + (size_t)u * stride >= n) break;
-                for (int p = 0; p < np; ++p)
-                    atomicAdd(&h[w][p][(uint32_t)((kk[u] >> (shift0 + 8 * (p0 + p))) & 0xFF)], 1u);
+        for (int u = 0; u < U; ++u) {
+            const bool valid = base + (size_t)u * stride < n;
+            for (int p = 0; p < npass; ++p) {
+                const uint32_t d = (uint32_t)((kk[u] >> (shift0 + 8 * p)) & 0xFF);
+                if (valid) atomicAdd(&h[p * OS_RADIX + d], 1u);
             }
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < np * OS_RADIX; i += blockDim.x) {
-            const int p = i / OS_RADIX, d = i % OS_RADIX;
-            uint32_t c = 0;
-            for (int ww = 0; ww < 8; ++ww) {
-                c += h[ww][p][d];
-                h[ww][p][d] = 0;
-            }
-            if (c) atomicAdd(&hist[(p0 + p) * OS_RADIX + d], c);
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * OS_RADIX; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int ww = 0; ww < OS_WARPS; ++ww) c += hs[(size_t)ww * npass * OS_RADIX + i];
+        if (c) atomicAdd(&hist[i], c);
     }
 }
 
@@ -390,13 +386,25 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         key[i] = li < rem ? kt[li] : (K)0;
         if constexpr (KV) val[i] = li < rem ? vt[li] : 0u;
     }
-    // stable warp-local ranks: peers with the same digit (match), counted in item order then lane order;
-    // every peer reads the running count (one broadcast word), the highest peer writes it back
+    // stable warp-local ranks: peers with the same digit, counted in item order then lane order; the peer
+    // mask is the AND of one ballot per digit bit (a fixed cost; a match instruction costs more the more
+    // distinct digits a warp holds, which is most of them for these keys); every peer reads the running
+    // count (one broadcast word), the highest peer writes it back
+    const bool full = rem == (uint32_t)OS_TILE;
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
         const bool valid = lbase + (uint32_t)i * 32 < rem;
         const uint32_t d = os_digit<K, HI>(key[i], sh);
-        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        unsigned peers = 0xFFFFFFFFu;
+        if (!full) {  // the last tile: items past the end form their own group
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            peers = valid ? vb : ~vb;
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
         const uint32_t cur = whist[w][d];
         __syncwarp();
         if (valid && (peers >> l) == 1u) whist[w][d] = cur + (uint32_t)__popc(peers);
@@ -515,6 +523,7 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
     const uint32_t ntiles = (uint32_t)((n + tile - 1) / tile);
     const size_t smem = (sizeof(K) + (kv ? sizeof(uint32_t) : 0)) * tile;
     static bool attr_set[2][64];
+    static bool hist_attr_set[64];
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[kv][dev]) {
@@ -535,7 +544,12 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
     CLD_TRY(status.alloc((size_t)ntiles * OS_RADIX, s));
     CLD_CUDA(cudaMemsetAsync(hist.get(), 0, (size_t)npass * OS_RADIX * 4, s));
     CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, (2 * npass + 2) * 4, s));
-    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, 0, s>>>(keys, n, npass, shift0, hist.get()));
+    const size_t hsm = (size_t)OS_WARPS * npass * OS_RADIX * 4;  // <= 64 KB (at most 8 passes)
+    if (dev < 0 || dev >= 64 || !hist_attr_set[dev]) {
+        CLD_CUDA(cudaFuncSetAttribute(k_os_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * OS_WARPS * OS_RADIX * 4));
+        if (dev >= 0 && dev < 64) hist_attr_set[dev] = true;
+    }
+    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, hsm, s>>>(keys, n, npass, shift0, hist.get()));
     CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist.get(), npass));
     CLD_LAUNCH_CHECK();
     prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
@@ -763,7 +777,7 @@ constexpr int UP_TILE = UP_THREADS * UP_ITEMS;
 constexpr unsigned long long UP_AGG = 1ull << 32;  // status: tile's own head count
 constexpr unsigned long long UP_PRE = 2ull << 32;  // status: heads in tiles 0..t
 
-__global__ void __launch_bounds__(UP_THREADS)
+__global__ void __launch_bounds__(UP_THREADS, 4)
     k_unique_packed(const uint64_t* __restrict__ items, uint32_t cnt, int vb, uint32_t* __restrict__ row_out,
                     uint2* __restrict__ adj_out, uint64_t* __restrict__ off_out, uint32_t nrows,
                     unsigned long long* __restrict__ status, uint32_t* __restrict__ ctl, uint32_t* __restrict__ total) {
@@ -836,20 +850,37 @@ __global__ void __launch_bounds__(UP_THREADS)
             if (l == 0) vst[0] = UP_PRE | tot;
         } else {
             if (l == 0) vst[tile] = UP_AGG | tot;
-            // lane j reads tile t - j; the window ends at the nearest inclusive prefix; wait (bounded)
-            // only on unpublished tiles before it
+            // a window of 4 x 32 earlier tiles per round trip: lane l reads tiles t - 4l - k (k < 4); the
+            // window ends at the nearest inclusive prefix; wait (bounded) only on unpublished tiles before it
+            constexpr int LK = 4;
             const long long t0 = clock64();
             long long t = (long long)tile - 1;
             bool done = false;
             while (!done) {
-                const long long j = t - (long long)l;
-                unsigned long long sv = j >= 0 ? (unsigned long long)vst[j] : (unsigned long long)UP_PRE;
+                unsigned long long sv[LK];
+#pragma unroll
+                for (int k = 0; k < LK; ++k) {
+                    const long long j = t - (long long)(LK * l + k);
+                    sv[k] = j >= 0 ? (unsigned long long)vst[j] : (unsigned long long)UP_PRE;
+                }
                 while (true) {
-                    const unsigned pre = __ballot_sync(0xffffffffu, (sv >> 32) == 2ull);
-                    const unsigned need = pre ? (0xFFFFFFFFu >> (31 - (__ffs(pre) - 1))) : 0xFFFFFFFFu;
-                    const unsigned unpub = __ballot_sync(0xffffffffu, (sv >> 32) == 0ull) & need;
-                    if (!unpub) {
-                        excl += warp_sum(((need >> l) & 1u) ? (uint32_t)sv : 0u);
+                    int kp = LK;  // this lane's first inclusive prefix
+#pragma unroll
+                    for (int k = LK - 1; k >= 0; --k)
+                        if ((sv[k] >> 32) == 2ull) kp = k;
+                    const unsigned pre = __ballot_sync(0xffffffffu, kp < LK);
+                    const unsigned lp = pre ? (unsigned)(__ffs(pre) - 1) : 32u;
+                    const int need = l < lp ? LK : (l == lp ? kp + 1 : 0);  // statuses this lane must add
+                    bool unpub = false;
+                    uint32_t part = 0;
+#pragma unroll
+                    for (int k = 0; k < LK; ++k)
+                        if (k < need) {
+                            unpub |= (sv[k] >> 32) == 0ull;
+                            part += (uint32_t)sv[k];
+                        }
+                    if (!__any_sync(0xffffffffu, unpub)) {
+                        excl += warp_sum(part);
                         done = pre != 0;
                         break;
                     }
@@ -859,9 +890,11 @@ __global__ void __launch_bounds__(UP_THREADS)
                         break;
                     }
                     __nanosleep(32);
-                    if ((sv >> 32) == 0ull) sv = vst[j];
+#pragma unroll
+                    for (int k = 0; k < LK; ++k)
+                        if (k < need && (sv[k] >> 32) == 0ull) sv[k] = vst[t - (long long)(LK * l + k)];
                 }
-                t -= 32;
+                t -= LK * 32;
             }
             if (l == 0) vst[tile] = UP_PRE | (excl + tot);
         }
