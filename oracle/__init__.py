@@ -80,6 +80,9 @@ def _lib_load():
                                              ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32, P, P,
                                              ctypes.POINTER(Stats), P, ctypes.c_uint64, P]
             lib.orc_cluster_opts.restype = ctypes.c_int
+            lib.orc_cluster2.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                         ctypes.c_int, ctypes.c_uint32, P, P, ctypes.POINTER(C2Stats)]
+            lib.orc_cluster2.restype = ctypes.c_int
             lib.orc_quotient.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, P, P, P, P]
             lib.orc_quotient.restype = ctypes.c_int64
             lib.orc_dijkstra.argtypes = [ctypes.c_uint32, P, P, P, P, ctypes.c_uint32, P]
@@ -193,6 +196,28 @@ def cluster(g: CSR, tau: float, seed: int, delta0_value: int, trace_cap: int = 1
         raise RuntimeError(f"orc_cluster failed: {rc}")
     stats = {f: getattr(st, f) for f, _ in Stats._fields_ if f != "pad"}
     return Clustering(center, D, stats, tr[:min(tl.value, trace_cap)].copy())
+
+
+class C2Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint32), ("steps", ctypes.c_uint32), ("centers_drawn", ctypes.c_uint64),
+                ("node_updates", ctypes.c_uint64), ("r_cl", ctypes.c_uint64)]
+
+
+def cluster2(g: CSR, tau: float, seed: int, delta0_value: int, contract_mode: int = CONTRACT_RESET,
+             step_cap: int = 0) -> Clustering:
+    """CLUSTER2(G, tau) of Algorithm 2 (Section 4): CLUSTER for R_CL, then log n iterations drawing new
+    centers with probability 2^i / n, PartialGrowth2 with Delta = 2 R_CL and Contract2 on an explicit
+    contracted edge list.  D_v is the length of the path the growth followed from c_v."""
+    lib = _lib_load()
+    center = np.empty(g.n, np.uint32)
+    D = np.empty(g.n, np.uint64)
+    st = C2Stats()
+    rc = lib.orc_cluster2(g.n, _ptr(g.off), _ptr(g.col), _ptr(g.wt), float(tau), seed, delta0_value,
+                          int(contract_mode), int(step_cap), _ptr(center), _ptr(D), ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"orc_cluster2 failed: {rc}")
+    stats = {f: getattr(st, f) for f, _ in C2Stats._fields_}
+    return Clustering(center, D, stats, np.zeros(0, TRACE_DTYPE))
 
 
 @dataclass

@@ -23,6 +23,9 @@
  *                       uncapped growth changes nothing, cap 1 bounds every growth to one
  *                       step, the cumulative mode keeps every D within the final Delta and
  *                       above the true distance, and its first stage equals the default's
+ *   orc_cluster2        pinned: a global-offset multi-source Dijkstra restatement of
+ *                       Algorithm 2 (same draws), plus coverage / path-length invariants
+ *                       and the R_CL = 0 case (all singletons)
  *   orc_quotient        pinned: independent dictionary recomputation + symmetry
  *   orc_apsp_max        pinned: scipy shortest_path
  *   orc_dijkstra        pinned: scipy dijkstra
@@ -469,6 +472,149 @@ int orc_cluster(uint32_t n, const uint64_t* off, const uint32_t* col, const uint
 {
     return orc_cluster_opts(n, off, col, wt, tau, seed, delta0, 0, 0, center_out, D_out, st, trace, trace_cap,
                             trace_len);
+}
+
+/* ---------------------------------------------------------------------------
+ * CLUSTER2(G, tau), Algorithm 2 (Section 4), with PartialGrowth2 and Contract2
+ * taken literally: the current graph G_i is an explicit list of undirected
+ * edges whose ends are clusters formed so far (named by their center) or
+ * nodes not yet covered.  Readings fixed here where the paper leaves room:
+ *  - R_CL = largest D_v of CLUSTER(G, tau) run with the same options (its radius);
+ *    Delta = 2 R_CL throughout.
+ *  - the for loop runs i = 1..L, L = the least i >= 1 with 2^i >= n (log n rounded
+ *    up), so the last iteration draws every node still uncovered.
+ *  - center draw in iteration i: an uncovered v is drawn iff
+ *    Philox(seed; ctr = (v, i, 1, 0)) word 0 < thr_i, thr_i = floor(2^i 2^32 / n)
+ *    (2^32 when 2^i >= n).
+ *  - growing steps as in CLUSTER (synchronous; (distance, center id) order;
+ *    a relaxation is kept when d_u + w <= Delta); centers keep (0, c).
+ *  - G_1 holds the edges of G of weight <= 2 R_CL: heavier ones are never used.
+ *  - Contract2 keeps an edge between two uncovered nodes, maps an edge with
+ *    exactly one covered end a (cluster c_a, distance d_a) to (c_a, b) with
+ *    weight d_a + w - 2 R_CL, and drops an edge with both ends covered.
+ *  - D_v = d_v + (i_v - i_c) 2 R_CL, v reached at distance d_v in G_{i_v} and its
+ *    center drawn in iteration i_c: by induction over the contractions, the
+ *    length of a path of G from c_v to v.
+ * Outputs center_out[v], D_out[v]; counters in *st.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t iterations, steps;
+    uint64_t centers_drawn;
+    uint64_t node_updates;
+    uint64_t r_cl;
+} orc_c2_stats;
+
+int orc_cluster2(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* wt, double tau,
+                 uint64_t seed, uint32_t delta0, int contract_mode, uint32_t step_cap, uint32_t* center_out,
+                 uint64_t* D_out, orc_c2_stats* st)
+{
+    memset(st, 0, sizeof *st);
+    orc_stats s1;
+    int rc = orc_cluster_opts(n, off, col, wt, tau, seed, delta0, contract_mode, step_cap, center_out, D_out, &s1,
+                              NULL, 0, NULL);
+    if (rc != 0) return rc;
+    uint64_t R = 0;
+    for (uint32_t v = 0; v < n; ++v) if (D_out[v] > R) R = D_out[v];
+    const uint64_t delta = 2 * R;
+    st->r_cl = R;
+
+    /* G_1: undirected edges (a, b, w), a < b, w <= Delta */
+    uint64_t m = 0;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t j = off[u]; j < off[u + 1]; ++j)
+            if (u < col[j] && wt[j] <= delta) ++m;
+    uint32_t* ea = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint32_t* eb = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint64_t* ew = (uint64_t*)malloc(sizeof(uint64_t) * (m ? m : 1));
+    uint8_t* cov = (uint8_t*)calloc(n, 1);        /* covered (a center or reached) */
+    uint32_t* ccov = (uint32_t*)malloc(sizeof(uint32_t) * n);  /* center of a covered node */
+    uint32_t* it_sel = (uint32_t*)calloc(n, sizeof(uint32_t)); /* iteration a center was drawn */
+    uint32_t* it_cov = (uint32_t*)calloc(n, sizeof(uint32_t)); /* iteration a node was covered */
+    uint64_t* dcov = (uint64_t*)calloc(n, sizeof(uint64_t));   /* its distance in that G_i */
+    uint64_t* kd = (uint64_t*)malloc(sizeof(uint64_t) * n);    /* state (d, c) of the nodes of G_i */
+    uint32_t* kc = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    uint64_t* sd = (uint64_t*)malloc(sizeof(uint64_t) * n);    /* its snapshot at a step start */
+    uint32_t* sc = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    uint8_t* upd = (uint8_t*)malloc(n);
+    if (!ea || !eb || !ew || !cov || !ccov || !it_sel || !it_cov || !dcov || !kd || !kc || !sd || !sc || !upd) {
+        rc = ORC_ERR_OOM;
+        goto done;
+    }
+    m = 0;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t j = off[u]; j < off[u + 1]; ++j)
+            if (u < col[j] && wt[j] <= delta) { ea[m] = u; eb[m] = col[j]; ew[m] = wt[j]; ++m; }
+
+    uint32_t L = 1;
+    while (((uint64_t)1 << L) < (uint64_t)n) ++L;
+    st->iterations = L;
+    for (uint32_t i = 1; i <= L; ++i) {
+        const uint64_t thr = (((uint64_t)1 << i) >= (uint64_t)n) ? 4294967296ull : ((uint64_t)1 << (32 + i)) / n;
+        /* new centers among the uncovered nodes */
+        for (uint32_t v = 0; v < n; ++v) {
+            if (cov[v]) continue;
+            uint32_t ctr[4] = {v, i, 1, 0}, out[4];
+            orc_philox4x32_10(seed, ctr, out);
+            if ((uint64_t)out[0] < thr) {
+                cov[v] = 1; ccov[v] = v; it_sel[v] = i; it_cov[v] = i; dcov[v] = 0;
+                st->centers_drawn++;
+            }
+        }
+        /* states of G_i's nodes: every center (0, c); uncovered nodes (inf, nil) */
+        for (uint32_t v = 0; v < n; ++v) {
+            if (cov[v] && ccov[v] == v) { kd[v] = 0; kc[v] = v; }
+            else { kd[v] = UINT64_MAX; kc[v] = ORC_NONE; }
+        }
+        /* PartialGrowth2: growing steps until no state is updated */
+        for (;;) {
+            memcpy(sd, kd, sizeof(uint64_t) * n);
+            memcpy(sc, kc, sizeof(uint32_t) * n);
+            memset(upd, 0, n);
+            for (uint64_t e = 0; e < m; ++e) {
+                for (int dir = 0; dir < 2; ++dir) {
+                    const uint32_t a = dir ? eb[e] : ea[e], b = dir ? ea[e] : eb[e];
+                    if (sd[a] == UINT64_MAX || cov[b]) continue;  /* b must be an uncovered node */
+                    const uint64_t cand = sd[a] + ew[e];
+                    if (cand > delta) continue;
+                    if (cand < kd[b] || (cand == kd[b] && sc[a] < kc[b])) { kd[b] = cand; kc[b] = sc[a]; upd[b] = 1; }
+                }
+            }
+            uint64_t u = 0;
+            for (uint32_t v = 0; v < n; ++v) u += upd[v];
+            st->steps++;
+            st->node_updates += u;
+            if (u == 0) break;
+        }
+        /* the reached nodes join their clusters */
+        for (uint32_t v = 0; v < n; ++v) {
+            if (cov[v] || kd[v] == UINT64_MAX) continue;
+            cov[v] = 2;  /* covered in this iteration (kept distinct until the contraction below) */
+            ccov[v] = kc[v]; it_cov[v] = i; dcov[v] = kd[v];
+        }
+        /* Contract2 */
+        uint64_t m2 = 0;
+        for (uint64_t e = 0; e < m; ++e) {
+            const uint32_t a = ea[e], b = eb[e];
+            const int ca = cov[a] != 0, cb = cov[b] != 0;
+            if (ca && cb) continue;
+            if (!ca && !cb) { ea[m2] = a; eb[m2] = b; ew[m2] = ew[e]; ++m2; continue; }
+            const uint32_t x = ca ? a : b, y = ca ? b : a;  /* x covered, y not */
+            const uint64_t dx = kd[x];                     /* 0 for a center, else its distance this iteration */
+            if (dx + ew[e] <= delta) { rc = ORC_ERR_DIVERGED; goto done; }  /* y would have been reached */
+            ea[m2] = ccov[x]; eb[m2] = y; ew[m2] = dx + ew[e] - delta; ++m2;
+        }
+        m = m2;
+        for (uint32_t v = 0; v < n; ++v) if (cov[v] == 2) cov[v] = 1;
+    }
+    for (uint32_t v = 0; v < n; ++v) {
+        if (!cov[v]) { rc = ORC_ERR_DIVERGED; goto done; }  /* the last iteration draws every uncovered node */
+        center_out[v] = ccov[v];
+        D_out[v] = dcov[v] + (uint64_t)(it_cov[v] - it_sel[ccov[v]]) * delta;
+    }
+done:
+    free(ea); free(eb); free(ew); free(cov); free(ccov); free(it_sel); free(it_cov); free(dcov);
+    free(kd); free(kc); free(sd); free(sc); free(upd);
+    return rc;
 }
 
 /* ---------------------------------------------------------------------------
