@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--plain-sample-every", type=int, default=10)
     ap.add_argument("--no-delta0-experiment", action="store_true", help="skip the initial-Delta experiment")
+    ap.add_argument("--no-cluster2", action="store_true", help="skip the CLUSTER2 (Algorithm 2) leg")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run one pipeline pass on the workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -494,6 +495,21 @@ def run_gpu(args):
     for _ in range(reps):
         _, ecc, rounds = cd.sssp_delta(g, s, want_dist=False)
     t_ds = (time.perf_counter() - t0) / reps
+    cl2 = None
+    if not args.no_cluster2:
+        # CLUSTER2 (Algorithm 2) + quotient + estimate on the same CSR: the provable variant of Section 4
+        r2 = cd.estimate(cd.quotient_build(cd.cluster2(g, wl.tau, wl.seed)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r2 = cd.estimate(cd.quotient_build(cd.cluster2(g, wl.tau, wl.seed)))
+        t_c2 = (time.perf_counter() - t0) / reps
+        cl2 = {"what": "CLUSTER2 (Algorithm 2: CLUSTER for R_CL, then log2 n iterations of PartialGrowth2 / "
+                       "Contract2) + quotient + estimate on the built CSR, wall clock",
+               "ms": round(t_c2 * 1e3, 3), "gteps": round(m_lcc / t_c2 / 1e9, 4),
+               "k": r2["k"], "radius": r2["radius"], "phi_gc": r2["phi_gc"], "phi_approx": r2["phi_approx"],
+               "iterations": r2["stages"], "growth_rounds": r2["steps"], "r_cl": r2["delta_end"] // 2,
+               "phi_approx_over_cluster": round(r2["phi_approx"] / r["phi_approx"], 4)}
     del g
 
     line = {
@@ -520,6 +536,8 @@ def run_gpu(args):
                           "ms": round(t_ds * 1e3, 3), "gteps": round(m_lcc / t_ds / 1e9, 4), "ecc": ecc,
                           "upper_bound": 2 * ecc, "rounds": rounds},
     }
+    if cl2:
+        line["cluster2"] = cl2
     if not args.no_delta0_experiment and rank == 0:
         line["initial_delta_experiment"] = delta0_leg(cd)
     if not args.no_batched:

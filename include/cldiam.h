@@ -57,7 +57,7 @@ typedef int32_t cldiam_status;
 #define CLDIAM_ERR_CUDA (-5)        /* a CUDA runtime call failed                    */
 #define CLDIAM_ERR_BUSY (-6)        /* result not ready yet (serving poll)           */
 #define CLDIAM_ERR_CANCELLED (-7)   /* request cancelled or server stopped           */
-#define CLDIAM_ERR_DIVERGED (-8)    /* CLUSTER exceeded its stage limit              */
+#define CLDIAM_ERR_DIVERGED (-8)    /* CLUSTER / CLUSTER2 growth exceeded its limits */
 #define CLDIAM_ERR_UNSUPPORTED (-9) /* valid request this build does not handle      */
 
 /* cldiam_build_csr flags */
@@ -166,6 +166,32 @@ cldiam_status cldiam_delta0(const cldiam_graph* g, int32_t mode, uint32_t* out);
  */
 cldiam_status cldiam_cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
                              cldiam_clustering** out);
+/*
+ * CLUSTER2(G, tau) of Algorithm 2 (Section 4), on the device: the clustering
+ * behind the O(log^3 n) approximation bound of Section 4 (CL-DIAM itself, as
+ * Section 5 describes it, uses cldiam_cluster).
+ *  First cldiam_cluster(g, tau, seed, opts); R_CL = the largest D_v of that
+ *  clustering.  Then iterations i = 1..L, L = the least i >= 1 with 2^i >= n:
+ *   - a node not yet covered is drawn as a new center iff
+ *     Philox4x32-10(key = seed, counter = (v, i, 1, 0)) word 0 < floor(2^i 2^32 / n)
+ *     (every such node when 2^i >= n);
+ *   - PartialGrowth2: growth with Delta = 2 R_CL until no state changes,
+ *     (distance, center id) tie-break, only edges of weight <= 2 R_CL;
+ *   - Contract2: the covered nodes merge into their clusters, an edge leaving a
+ *     cluster gets weight d_u + w - 2 R_CL.
+ *  D_v = d_v + (i_v - i_c) 2 R_CL for v reached in iteration i_v (distance d_v
+ *  in that iteration's contracted graph) by a center drawn in iteration i_c:
+ *  the length of the path the growth followed, >= dist_G(c_v, v).
+ *  The result feeds cldiam_quotient_build / cldiam_estimate like a
+ *  cldiam_cluster result (Phi_approx = Phi(G_C) + 2 max D_v).  Counters:
+ *  stages = L, steps = device growth rounds (asynchronous relaxation to the
+ *  same fixed point as the paper's synchronous steps), delta_end = 2 R_CL,
+ *  centers_drawn = centers drawn by the iterations.  Deterministic in
+ *  (graph, tau, seed, opts).
+ *  Errors: those of cldiam_cluster; UNSUPPORTED when L x 2 R_CL >= 2^32 - 1.
+ */
+cldiam_status cldiam_cluster2(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
+                              cldiam_clustering** out);
 /* Counters of the clustering (k, stages, steps, ... ; phi fields are 0). */
 cldiam_status cldiam_clustering_info(const cldiam_clustering* c, cldiam_result* out);
 /* center[n] (center node id), D[n], cid[n] (cluster id = rank of the center id); any may be NULL. */

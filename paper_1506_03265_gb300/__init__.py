@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
             "cldiam_graph_free": (None, [P]),
             "cldiam_delta0": (st, [P, ctypes.c_int32, P]),
             "cldiam_cluster": (st, [P, ctypes.c_double, ctypes.c_uint64, P, PP]),
+            "cldiam_cluster2": (st, [P, ctypes.c_double, ctypes.c_uint64, P, PP]),
             "cldiam_clustering_info": (st, [P, P]),
             "cldiam_clustering_copy": (st, [P, P, P, P]),
             "cldiam_clustering_free": (None, [P]),
@@ -385,6 +386,16 @@ def cluster(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, m
     o = make_opts(delta0_mode, delta0, max_fw_k, quotient_mode, contract_mode, step_cap)
     h = ctypes.c_void_p()
     _check(load().cldiam_cluster(g.handle, float(tau), seed, ctypes.byref(o), ctypes.byref(h)), "cldiam_cluster")
+    return Clustering(h.value, g)
+
+
+def cluster2(g: Graph, tau: float, seed: int, delta0_mode=DELTA0_AVG, delta0=0, max_fw_k=0,
+             quotient_mode=QUOTIENT_AUTO, contract_mode=CONTRACT_RESET, step_cap=0) -> Clustering:
+    """cldiam_cluster2: CLUSTER2(G, tau) of Algorithm 2 (CLUSTER for R_CL, then log n iterations of
+    PartialGrowth2 / Contract2); the options apply to the first CLUSTER run."""
+    o = make_opts(delta0_mode, delta0, max_fw_k, quotient_mode, contract_mode, step_cap)
+    h = ctypes.c_void_p()
+    _check(load().cldiam_cluster2(g.handle, float(tau), seed, ctypes.byref(o), ctypes.byref(h)), "cldiam_cluster2")
     return Clustering(h.value, g)
 
 

@@ -150,6 +150,11 @@ cldiam_status cldiam_cluster(cldiam_graph* g, double tau, uint64_t seed, const c
     return guarded([&] { return cluster(g, tau, seed, opts, out); });
 }
 
+cldiam_status cldiam_cluster2(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
+                              cldiam_clustering** out) {
+    return guarded([&] { return cluster2(g, tau, seed, opts, out); });
+}
+
 cldiam_status cldiam_clustering_info(const cldiam_clustering* c, cldiam_result* out) {
     if (!c || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL clustering or out");
     *out = c->stats;

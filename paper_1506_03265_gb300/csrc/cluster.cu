@@ -96,6 +96,27 @@ struct ClusterOwner {
 
 }  // namespace
 
+// a9: cluster id = rank of the center's node id among all centers; *k = number of clusters (synchronises)
+cldiam_status relabel_clusters(cldiam_graph* g, const uint32_t* center, uint32_t* cid, uint32_t* k) {
+    const cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    const unsigned gb = grid_for(n, 256);
+    DBuf<uint32_t> flag, rank, kdev;
+    CLD_TRY(flag.alloc(n, s));
+    CLD_TRY(rank.alloc(n, s));
+    CLD_TRY(kdev.alloc(1, s));
+    CLD_K(K_MISC, s, k_center_flags<<<gb, 256, 0, s>>>(n, center, flag.get()));
+    CLD_LAUNCH_CHECK();
+    CLD_TRY(scan_exclusive_u32(flag.get(), rank.get(), n, kdev.get(), s));
+    CLD_K(K_MISC, s, k_assign_cid<<<gb, 256, 0, s>>>(n, center, rank.get(), cid));
+    CLD_LAUNCH_CHECK();
+    uint32_t* hk = reinterpret_cast<uint32_t*>(static_cast<char*>(g->host.h) + 128);
+    CLD_CUDA(cudaMemcpyAsync(hk, kdev.get(), 4, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaStreamSynchronize(s));
+    *k = *hk;
+    return CLDIAM_OK;
+}
+
 void free_clustering(cldiam_clustering* c) {
     if (!c) return;
     cudaStream_t s = c->g ? c->g->stream : nullptr;
@@ -308,20 +329,8 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     CLD_K(K_FINALIZE, s, k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get()));
     CLD_LAUNCH_CHECK();
 
-    // relabel
-    DBuf<uint32_t> flag, rank, kdev;
-    CLD_TRY(flag.alloc(n, s));
-    CLD_TRY(rank.alloc(n, s));
-    CLD_TRY(kdev.alloc(1, s));
-    CLD_K(K_MISC, s, k_center_flags<<<gb, 256, 0, s>>>(n, center.get(), flag.get()));
-    CLD_LAUNCH_CHECK();
-    CLD_TRY(scan_exclusive_u32(flag.get(), rank.get(), n, kdev.get(), s));
-    CLD_K(K_MISC, s, k_assign_cid<<<gb, 256, 0, s>>>(n, center.get(), rank.get(), cid.get()));
-    CLD_LAUNCH_CHECK();
-    uint32_t* hk = reinterpret_cast<uint32_t*>(static_cast<char*>(g->host.h) + 128);
-    CLD_CUDA(cudaMemcpyAsync(hk, kdev.get(), 4, cudaMemcpyDeviceToHost, s));
-    CLD_TRY(sync_counters());
-    st.k = *hk;
+    CLD_TRY(relabel_clusters(g, center.get(), cid.get(), &st.k));
+    prof_flush();
     st.delta_end = delta;
 
     cl->center = center.detach();

@@ -61,6 +61,9 @@ void free_graph(cldiam_graph* g);
 
 cldiam_status delta0(const cldiam_graph* g, int mode, uint32_t explicit_value, uint32_t* out);
 cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* o, cldiam_clustering** out);
+cldiam_status cluster2(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* o, cldiam_clustering** out);
+// cid[v] = rank of center[v] among the centers; *k = their number (synchronises the graph's stream)
+cldiam_status relabel_clusters(cldiam_graph* g, const uint32_t* center, uint32_t* cid, uint32_t* k);
 void free_clustering(cldiam_clustering* c);
 
 cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out);
