@@ -249,9 +249,11 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
-// Stable LSD radix sort of 64-bit keys alone on key bits [shift0, shift0 + bits).
+// Stable LSD radix sort of 64-bit keys alone on key bits [shift0, shift0 + bits).  With err_dev the
+// call does not synchronise: a look-back wait that expired sets *err_dev (device word) instead of
+// returning TIMEOUT, for the caller to read with its next result.
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits,
-                                  bool* result_in_alt, cudaStream_t s);
+                                  bool* result_in_alt, cudaStream_t s, uint32_t* err_dev = nullptr);
 
 // Unique keys of a sorted sequence with the minimum value of each run:
 // row_out[r] = key / div (row_out may be null), col_out[r*cs] = key % div,

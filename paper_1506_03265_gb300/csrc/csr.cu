@@ -191,9 +191,10 @@ __global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t*
 // new offsets (widened from the 32-bit scan of the kept degrees) and, for each kept node orig[i], its
 // new id and the shift from its old adjacency positions to its new ones (positions are < 2^32, so
 // the shift is taken modulo 2^32); map of a dropped node keeps its 0xFFFFFFFF pre-fill
-__global__ void k_lcc_offsets(const uint32_t* __restrict__ excl, uint32_t n_out, uint32_t total,
-                              const uint32_t* __restrict__ orig, const uint64_t* __restrict__ off,
-                              uint64_t* __restrict__ noff, uint2* __restrict__ map) {
+__global__ void k_lcc_offsets(const uint32_t* __restrict__ excl, uint32_t n, const uint32_t* __restrict__ n_out_dev,
+                              const uint32_t* __restrict__ total_dev, const uint32_t* __restrict__ orig,
+                              const uint64_t* __restrict__ off, uint64_t* __restrict__ noff, uint2* __restrict__ map) {
+    const uint32_t n_out = *n_out_dev, total = *total_dev;  // n_out <= n
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_out; i += gridDim.x * blockDim.x) {
         noff[i] = (i == n_out) ? (uint64_t)total : (uint64_t)excl[i];
         if (i < n_out) {
@@ -262,7 +263,10 @@ __global__ void k_graph_stats(const uint32_t* __restrict__ row, const uint2* __r
     if (threadIdx.x == 0) atomicMin(wmin, mn);
 }
 
-__global__ void k_degree_max(const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ out) {
+// largest degree of rows 0..n-1 (n = *n_dev when given: a count still on the device, <= the bound n)
+__global__ void k_degree_max(const uint64_t* __restrict__ off, uint32_t n, const uint32_t* __restrict__ n_dev,
+                             uint32_t* __restrict__ out) {
+    if (n_dev) n = min(n, *n_dev);
     uint32_t m = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
         m = max(m, (uint32_t)(off[v + 1] - off[v]));
@@ -334,9 +338,11 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
 
     // items: packed words when the weight fits in the bits the two ids leave, else (key, weight) pairs
     const uint64_t cnt = 2 * m;
+    // device words read back by the host: [0] bad input, [1] unique entries, [2] wide weight, [3] sampled
+    // giant size, [4] LCC nodes, [5] LCC entries, [6] min weight, [7] max degree, [8] sort look-back error
     DBuf<uint32_t> scal;
-    CLD_TRY(scal.alloc(8, s));
-    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(uint32_t), s));
+    CLD_TRY(scal.alloc(9, s));
+    CLD_CUDA(cudaMemsetAsync(scal.get(), 0, 9 * sizeof(uint32_t), s));
     const int vb = std::max(1, bits_for((uint64_t)n - 1));
     const int wb = 64 - 2 * vb;  // weight bits of a packed item
 
@@ -365,7 +371,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         if (packed) {
             CLD_TRY(items2.alloc(cnt ? cnt : 1, s));
             bool alt = false;
-            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s));
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s, scal.get() + 8));
             // unique (row, col) runs with their lightest weight, in one look-back pass
             CLD_TRY(unique_packed_csr(alt ? items2.get() : items.get(), cnt, vb, row.get(), adj.get(), off.get(), n,
                                       scal.get() + 1, s));
@@ -397,13 +403,9 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(unique_min_sorted_u64(alt ? keys2.get() : keys.get(), alt ? vals2.get() : vals.get(), cnt, sentinel, n,
                                       row.get(), &adj.get()->x, &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
     }
-    CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaStreamSynchronize(s));
-    const uint32_t nnz = hbad[1];
-    // (the row offsets were written by the run heads)
-
-    uint32_t n_out = n;
-    uint64_t nnz_out = nnz;
+    // (the row offsets were written by the run heads; the entry count stays on the device until the
+    // host needs it, read together with the next result)
+    uint32_t nnz = 0;
     DBuf<uint32_t> orig;
     // weight statistics for the initial Delta (Algorithm 1 / Section 5): sum over u < v, minimum
     DBuf<unsigned long long> wsum;
@@ -411,7 +413,6 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_CUDA(cudaMemsetAsync(wsum.get(), 0, 8, s));
     CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
-    bool stats_done = false;
     if (flags & CLDIAM_CSR_LCC) {
         DBuf<uint32_t> parent, size, keep, newid;
         DBuf<unsigned long long> best;
@@ -420,22 +421,24 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
         CLD_LAUNCH_CHECK();
         // Afforest-style: link two neighbours per node, find the dominant tree by sampling,
-        // then link the remaining edges of the nodes outside it
+        // then link the remaining edges of the nodes outside it (all no-ops on a graph without edges)
         constexpr uint32_t kNeighbourRounds = 2;
+        for (uint32_t r = 0; r < kNeighbourRounds; ++r) {
+            CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, r, parent.get()));
+            CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
+        }
+        CLD_LAUNCH_CHECK();
+        constexpr uint32_t kSamples = 1024;
+        DBuf<uint32_t> samp;
+        CLD_TRY(samp.alloc(kSamples, s));
+        CLD_K(K_CC, s, k_cc_sample<<<4, 256, 0, s>>>(parent.get(), n, kSamples, samp.get()));
+        CLD_LAUNCH_CHECK();
+        std::vector<uint32_t> hs(kSamples);
+        CLD_CUDA(cudaMemcpyAsync(hs.data(), samp.get(), kSamples * 4, cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        nnz = hbad[1];
         if (nnz > 0) {
-            for (uint32_t r = 0; r < kNeighbourRounds; ++r) {
-                CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, r, parent.get()));
-                CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
-            }
-            CLD_LAUNCH_CHECK();
-            constexpr uint32_t kSamples = 1024;
-            DBuf<uint32_t> samp;
-            CLD_TRY(samp.alloc(kSamples, s));
-            CLD_K(K_CC, s, k_cc_sample<<<4, 256, 0, s>>>(parent.get(), n, kSamples, samp.get()));
-            CLD_LAUNCH_CHECK();
-            std::vector<uint32_t> hs(kSamples);
-            CLD_CUDA(cudaMemcpyAsync(hs.data(), samp.get(), kSamples * 4, cudaMemcpyDeviceToHost, s));
-            CLD_CUDA(cudaStreamSynchronize(s));
             std::sort(hs.begin(), hs.end());
             uint32_t giant = hs[0], best_run = 0;
             for (size_t i = 0; i < hs.size();) {
@@ -468,29 +471,25 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_K(K_CC, s, k_cc_keep<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n, best.get(), keep.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(scan_exclusive_u32(keep.get(), newid.get(), n, scal.get() + 4, s));
-        CLD_CUDA(cudaMemcpyAsync(hbad + 4, scal.get() + 4, 4, cudaMemcpyDeviceToHost, s));
-        CLD_CUDA(cudaStreamSynchronize(s));
-        n_out = hbad[4];
-        CLD_TRY(orig.alloc(n_out, s));
+        // the LCC's node and entry counts stay on the device: its arrays are sized by the bounds n and
+        // nnz, and the kernels read the counts from scal[4] / scal[5]
+        CLD_TRY(orig.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
         CLD_K(K_CSR, s, k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), n, deg.get(), orig.get()));
         CLD_LAUNCH_CHECK();
-        CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n_out, scal.get() + 5, s));
-        CLD_CUDA(cudaMemcpyAsync(hbad + 5, scal.get() + 5, 4, cudaMemcpyDeviceToHost, s));
-        CLD_CUDA(cudaStreamSynchronize(s));
-        nnz_out = hbad[5];
+        CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n, scal.get() + 5, s));  // zeros past the kept nodes
         DBuf<uint64_t> noff;
         DBuf<uint2> nadj;
         DBuf<uint32_t> nrow;
-        CLD_TRY(noff.alloc((size_t)n_out + 1, s));
-        CLD_TRY(nadj.alloc(nnz_out ? nnz_out : 1, s));
-        CLD_TRY(nrow.alloc(nnz_out ? nnz_out : 1, s));
+        CLD_TRY(noff.alloc((size_t)n + 1, s));
+        CLD_TRY(nadj.alloc(nnz ? nnz : 1, s));
+        CLD_TRY(nrow.alloc(nnz ? nnz : 1, s));
         DBuf<uint2> map;
         CLD_TRY(map.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(map.get(), 0xFF, (size_t)n * 8, s));
-        CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n_out + 1, 256), 256, 0, s>>>(degx.get(), n_out, (uint32_t)nnz_out,
-                                                                                    orig.get(), off.get(), noff.get(),
-                                                                                    map.get()));
+        CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, scal.get() + 4,
+                                                                                scal.get() + 5, orig.get(), off.get(),
+                                                                                noff.get(), map.get()));
         CLD_LAUNCH_CHECK();
         if (nnz) {
             CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(map.get(), newid.get(), row.get(), adj.get(),
@@ -498,33 +497,43 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                                                          scal.get() + 6));
             CLD_LAUNCH_CHECK();
         }
-        stats_done = true;
         g->off = noff.detach();
         g->adj = nadj.detach();
         g->row = nrow.detach();
+        CLD_K(K_CSR, s, k_degree_max<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, scal.get() + 4, scal.get() + 7));
+        CLD_LAUNCH_CHECK();
     } else {
+        CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        nnz = hbad[1];
         CLD_TRY(orig.alloc(n, s));
         CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(orig.get(), n));
         CLD_LAUNCH_CHECK();
         g->off = off.detach();
         g->adj = adj.detach();
         g->row = row.detach();
-    }
-    g->orig = orig.detach();
-    g->n = n_out;
-    g->nnz = nnz_out;
-    g->connected = (flags & CLDIAM_CSR_LCC) != 0;
-
-    if (g->nnz && !stats_done) {
-        CLD_K(K_CSR, s, k_graph_stats<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, wsum.get(), scal.get() + 6));
+        if (nnz) {
+            CLD_K(K_CSR, s, k_graph_stats<<<grid_for(nnz, 256), 256, 0, s>>>(g->row, g->adj, nnz, wsum.get(),
+                                                                             scal.get() + 6));
+            CLD_LAUNCH_CHECK();
+        }
+        CLD_K(K_CSR, s, k_degree_max<<<grid_for(n, 256), 256, 0, s>>>(g->off, n, nullptr, scal.get() + 7));
         CLD_LAUNCH_CHECK();
     }
-    CLD_K(K_CSR, s, k_degree_max<<<grid_for(g->n, 256), 256, 0, s>>>(g->off, g->n, scal.get() + 7));
-    CLD_LAUNCH_CHECK();
+    g->orig = orig.detach();
+    g->connected = (flags & CLDIAM_CSR_LCC) != 0;
     uint64_t* hsum = reinterpret_cast<uint64_t*>(static_cast<char*>(g->host.h) + 64);
     CLD_CUDA(cudaMemcpyAsync(hsum, wsum.get(), 8, cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaMemcpyAsync(hbad + 6, scal.get() + 6, 8, cudaMemcpyDeviceToHost, s));
+    CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, 8 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
+    if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired");
+    if (flags & CLDIAM_CSR_LCC) {
+        g->n = hbad[4];
+        g->nnz = hbad[5];
+    } else {
+        g->n = n;
+        g->nnz = nnz;
+    }
     g->wsum_upper = *hsum;
     g->wmin = hbad[6];
     g->max_deg = hbad[7];

@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
 // LSD sort of n items on key bits [shift0, shift0 + bits); vals == nullptr sorts keys only.
 template <class K>
 static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, size_t n, int shift0,
-                                     int bits, bool* in_alt, cudaStream_t s) {
+                                     int bits, bool* in_alt, cudaStream_t s, uint32_t* err_dev = nullptr) {
     *in_alt = false;
     if (n <= 1 || bits <= 0) return CLDIAM_OK;
     if (n > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "radix sort limited to 2^32 - 1 items");
@@ -565,7 +565,7 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         const uint32_t sh = (uint32_t)shift & 31u;
         const uint32_t* go = hist.get() + p * OS_RADIX;
         uint32_t* tc = ctl.get() + p;
-        uint32_t* er = ctl.get() + 2 * npass;
+        uint32_t* er = err_dev ? err_dev : ctl.get() + 2 * npass;
         if (kv && hi) {
             CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, go,
                                                                                               status.get(), tc, er));
@@ -586,11 +586,12 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         uint32_t* tv = vi; vi = vo; vo = tv;
         alt = !alt;
     }
+    *in_alt = alt;
+    if (err_dev) return CLDIAM_OK;  // the caller reads the look-back error word with its next result
     uint32_t herr = 0;
     CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 2 * npass, 4, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     if (herr) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired");
-    *in_alt = alt;
     return CLDIAM_OK;
 }
 
@@ -763,9 +764,11 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size
 
 // ------------------------------------------------------------------ CSR de-duplication of packed items
 // Items (row << vb | col) << wb | w with wb = 64 - 2 vb, sorted on their (row, col) bits; ~0 marks a
-// dropped item (self-loop) and sorts last.  One pass: tile t flags its run heads, publishes its head
-// count and finds the heads of all earlier tiles by a warp-wide decoupled look-back over one status
-// word per tile, then writes row_out[r], adj_out[r] = (col, w) for its heads and the CSR offsets.
+// dropped item (self-loop) and sorts last.  Two passes over tiles of 2,048 items: the first counts each
+// tile's run heads, an exclusive scan gives each tile its first head index, and the second flags the
+// heads again and writes row_out[r], adj_out[r] = (col, w) for them and the CSR offsets.  (A one-pass
+// form with a decoupled look-back over the tile counts was slower: its tiles wait on each other while
+// the extra read of the two-pass form streams at full bandwidth.)
 // Run minima: a head stores its own weight, and after a block barrier every other item of a run
 // headed in the same tile folds its weight in with atomicMin; the items of the tile's last run that
 // lie in later tiles are read by the head's tile (a warp scanning forward) and folded in the same way,
@@ -774,19 +777,57 @@ constexpr int UP_THREADS = 256;
 constexpr int UP_WARPS = UP_THREADS / 32;
 constexpr int UP_ITEMS = 8;
 constexpr int UP_TILE = UP_THREADS * UP_ITEMS;
-constexpr unsigned long long UP_AGG = 1ull << 32;  // status: tile's own head count
-constexpr unsigned long long UP_PRE = 2ull << 32;  // status: heads in tiles 0..t
 
+// Head flag of a packed item: kept and not sharing (row, col) with its predecessor (~0 before position 0).
+__device__ __forceinline__ bool up_head(uint64_t prev, uint64_t x, uint64_t same_lim, uint64_t valid_lim) {
+    return x < valid_lim && (prev ^ x) >= same_lim;
+}
+
+// First pass of the two-pass form: run heads per tile.
+__global__ void __launch_bounds__(UP_THREADS) k_unique_packed_count(const uint64_t* __restrict__ items, uint32_t cnt,
+                                                                    int vb, uint32_t* __restrict__ heads) {
+    __shared__ uint32_t s_w[UP_WARPS];
+    const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
+    const uint64_t tbase = (uint64_t)blockIdx.x * UP_TILE;
+    const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
+    const int wb = 64 - 2 * vb;
+    const uint64_t same_lim = 1ull << wb, valid_lim = ~0ull << wb;
+    const uint32_t wstart = w * (UP_ITEMS * 32);
+    const uint64_t* it = items + tbase;
+    uint64_t x[UP_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        const uint32_t li = wstart + (uint32_t)i * 32 + l;
+        x[i] = li < rem ? it[li] : ~0ull;
+    }
+    uint64_t carry = ~0ull;
+    if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; ++i) {
+        const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
+        const uint64_t prev = l == 0 ? carry : rot;
+        carry = rot;
+        run += (uint32_t)__popc(__ballot_sync(0xffffffffu, up_head(prev, x[i], same_lim, valid_lim)));
+    }
+    if (l == 0) s_w[w] = run;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int ww = 0; ww < UP_WARPS; ++ww) t += s_w[ww];
+        heads[blockIdx.x] = t;
+    }
+}
+
+// Second pass: the tile's first head index is first[tile], the exclusive scan of the first pass.
 __global__ void __launch_bounds__(UP_THREADS, 4)
     k_unique_packed(const uint64_t* __restrict__ items, uint32_t cnt, int vb, uint32_t* __restrict__ row_out,
                     uint2* __restrict__ adj_out, uint64_t* __restrict__ off_out, uint32_t nrows,
-                    unsigned long long* __restrict__ status, uint32_t* __restrict__ ctl, uint32_t* __restrict__ total) {
+                    uint32_t* __restrict__ total, const uint32_t* __restrict__ first) {
     __shared__ uint32_t s_woff[UP_WARPS];  // heads per warp, then the global index of the warp's first head
-    __shared__ uint32_t s_tile, s_first, s_count;
+    __shared__ uint32_t s_first, s_count;
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
-    if (tid == 0) s_tile = atomicAdd(&ctl[0], 1u);  // tiles in start order: earlier tiles are running or done
-    __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = blockIdx.x;
     const uint64_t tbase = (uint64_t)tile * UP_TILE;
     const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
     const int wb = 64 - 2 * vb;
@@ -818,7 +859,7 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
         const uint64_t prev = l == 0 ? carry : rot;
         carry = rot;
         const bool valid = x[i] < valid_lim;
-        const bool f = valid && (prev ^ x[i]) >= same_lim;
+        const bool f = up_head(prev, x[i], same_lim, valid_lim);
         const bool rs = f && (prev >= valid_lim || (uint32_t)(prev >> 32) >> rsh != (uint32_t)(x[i] >> 32) >> rsh);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
         const unsigned vbal = __ballot_sync(0xffffffffu, valid);
@@ -844,60 +885,7 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
         const uint32_t v = l < UP_WARPS ? s_woff[l] : 0u;
         const uint32_t incl = warp_incl_scan(v);
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, UP_WARPS - 1);
-        volatile unsigned long long* vst = status;
-        uint32_t excl = 0;
-        if (tile == 0) {
-            if (l == 0) vst[0] = UP_PRE | tot;
-        } else {
-            if (l == 0) vst[tile] = UP_AGG | tot;
-            // a window of 4 x 32 earlier tiles per round trip: lane l reads tiles t - 4l - k (k < 4); the
-            // window ends at the nearest inclusive prefix; wait (bounded) only on unpublished tiles before it
-            constexpr int LK = 4;
-            const long long t0 = clock64();
-            long long t = (long long)tile - 1;
-            bool done = false;
-            while (!done) {
-                unsigned long long sv[LK];
-#pragma unroll
-                for (int k = 0; k < LK; ++k) {
-                    const long long j = t - (long long)(LK * l + k);
-                    sv[k] = j >= 0 ? (unsigned long long)vst[j] : (unsigned long long)UP_PRE;
-                }
-                while (true) {
-                    int kp = LK;  // this lane's first inclusive prefix
-#pragma unroll
-                    for (int k = LK - 1; k >= 0; --k)
-                        if ((sv[k] >> 32) == 2ull) kp = k;
-                    const unsigned pre = __ballot_sync(0xffffffffu, kp < LK);
-                    const unsigned lp = pre ? (unsigned)(__ffs(pre) - 1) : 32u;
-                    const int need = l < lp ? LK : (l == lp ? kp + 1 : 0);  // statuses this lane must add
-                    bool unpub = false;
-                    uint32_t part = 0;
-#pragma unroll
-                    for (int k = 0; k < LK; ++k)
-                        if (k < need) {
-                            unpub |= (sv[k] >> 32) == 0ull;
-                            part += (uint32_t)sv[k];
-                        }
-                    if (!__any_sync(0xffffffffu, unpub)) {
-                        excl += warp_sum(part);
-                        done = pre != 0;
-                        break;
-                    }
-                    if (__any_sync(0xffffffffu, clock64() - t0 > OS_WAIT_CYCLES)) {  // warp-uniform give-up
-                        if (l == 0) atomicExch(&ctl[1], 1u);
-                        done = true;
-                        break;
-                    }
-                    __nanosleep(32);
-#pragma unroll
-                    for (int k = 0; k < LK; ++k)
-                        if (k < need && (sv[k] >> 32) == 0ull) sv[k] = vst[t - (long long)(LK * l + k)];
-                }
-                t -= LK * 32;
-            }
-            if (l == 0) vst[tile] = UP_PRE | (excl + tot);
-        }
+        const uint32_t excl = first[tile];
         if (l < UP_WARPS) s_woff[l] = excl + incl - v;
         if (l == 0) {
             s_first = excl;
@@ -966,19 +954,15 @@ cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint3
     if (cnt > 0xFFFFFFFFull - UP_TILE) return fail(CLDIAM_ERR_UNSUPPORTED, "too many items");
     if (vb < 1 || vb > 32) return fail(CLDIAM_ERR_INVALID_ARG, "packed items need 1..32 id bits");
     const uint32_t ntiles = (uint32_t)((cnt + UP_TILE - 1) / UP_TILE);
-    DBuf<unsigned long long> status;
-    DBuf<uint32_t> ctl;
-    CLD_TRY(status.alloc(ntiles, s));
-    CLD_TRY(ctl.alloc(2, s));
-    CLD_CUDA(cudaMemsetAsync(status.get(), 0, (size_t)ntiles * 8, s));
-    CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, 8, s));
-    CLD_K(K_CSR, s, k_unique_packed<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, row_out, adj_out, off_out,
-                                                                  nrows, status.get(), ctl.get(), total_dev));
+    DBuf<uint32_t> heads, first;
+    CLD_TRY(heads.alloc(ntiles, s));
+    CLD_TRY(first.alloc(ntiles, s));
+    CLD_K(K_CSR, s, k_unique_packed_count<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, heads.get()));
     CLD_LAUNCH_CHECK();
-    uint32_t herr = 0;
-    CLD_CUDA(cudaMemcpyAsync(&herr, ctl.get() + 1, 4, cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaStreamSynchronize(s));
-    if (herr) return fail(CLDIAM_ERR_TIMEOUT, "de-duplication look-back wait expired");
+    CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, nullptr, s));
+    CLD_K(K_CSR, s, k_unique_packed<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, row_out, adj_out, off_out,
+                                                                  nrows, total_dev, first.get()));
+    CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
 
@@ -1000,8 +984,8 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
     return radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, 0, bits, in_alt, s);
 }
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits, bool* in_alt,
-                                  cudaStream_t s) {
-    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s);
+                                  cudaStream_t s, uint32_t* err_dev) {
+    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s, err_dev);
 }
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* in_alt, cudaStream_t s) {
