@@ -251,9 +251,11 @@ cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* key
                                    size_t n, int bits, bool* result_in_alt, cudaStream_t s);
 // Stable LSD radix sort of 64-bit keys alone on key bits [shift0, shift0 + bits).  With err_dev the
 // call does not synchronise: a look-back wait that expired sets *err_dev (device word) instead of
-// returning TIMEOUT, for the caller to read with its next result.
+// returning TIMEOUT, for the caller to read with its next result.  With first_in the n input keys are
+// read from there (never written) and keys / keys_alt serve only as the ping-pong buffers.
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits,
-                                  bool* result_in_alt, cudaStream_t s, uint32_t* err_dev = nullptr);
+                                  bool* result_in_alt, cudaStream_t s, uint32_t* err_dev = nullptr,
+                                  const uint64_t* first_in = nullptr);
 
 // Unique keys of a sorted sequence with the minimum value of each run:
 // row_out[r] = key / div (row_out may be null), col_out[r*cs] = key % div,
@@ -266,11 +268,11 @@ cldiam_status unique_min_sorted_u64(const uint64_t* keys, const uint32_t* vals, 
 cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, size_t cnt, uint32_t sentinel,
                                     uint64_t div, uint32_t* row_out, uint32_t* col_out, uint32_t* w_out, int cs,
                                     uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
-// The same for packed CSR items (row << vb | col) << (64 - 2 vb) | w, sorted on their (row, col) bits
-// (~0 marks a dropped item): row_out[r], adj_out[r] = (col, min w) per unique (row, col), the offsets
-// off_out[0..nrows] and the count in *total_dev, in one look-back pass.  adj_out needs no pre-fill.
-cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint32_t* row_out, uint2* adj_out,
-                                uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s);
+// De-duplication of packed edge items (a << vb | b) << (64 - 2 vb) | w sorted on their (a, b) bits (~0 marks
+// a dropped item): out[r] = the r-th distinct (a, b) item with its smallest weight; *total_dev = their
+// number.
+cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64_t* out, uint32_t* total_dev,
+                               cudaStream_t s);
 
 // CSR offsets off[0..n] of entries whose (sorted) row ids are row[0..nnz):
 // off[u] = index of the first entry with row >= u.  No atomics, no scan.

@@ -2,12 +2,14 @@
 // merge parallel edges to their minimum weight, symmetrise, sort rows by
 // column, optionally keep the largest connected component.
 //
-// Pipeline: every undirected edge becomes two directed items.  When
-// 2 * bits(n - 1) + bits(max w) <= 64 an item is one packed word
-// (row << b | col) << wb | w, sorted on its (row, col) bits only; otherwise
-// it is a key row * n + col with the weight beside it.  Run heads of the
-// sorted sequence give the unique entries, and the minimum over each run the
-// lightest parallel edge.  Components come from min-label
+// Pipeline: when 2 * bits(n - 1) + bits(max w) <= 64 every undirected edge is
+// one packed word (min << b | max) << wb | w, sorted on its (min, max) bits;
+// run heads give the distinct edges and the minimum over a run the lightest
+// parallel edge.  The distinct edges sorted again on max alone (stable, so
+// by (max, min)) give each row's entries below the diagonal; row x of the
+// CSR is those, then its entries above the diagonal from the first order.
+// Otherwise every edge becomes two directed (row * n + col, weight) pairs,
+// sorted and de-duplicated the same way.  Components come from min-label
 // hooking with pointer jumping: every tree points to a smaller id of its
 // component, so roots are component minima and the labelling is
 // deterministic.
@@ -40,28 +42,79 @@ __global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t
     }
 }
 
-// both directions of every edge as packed items (row << vb | col) << wb | w; a self-loop becomes ~0
-// (skipped, sorts last).  Also the input check (ids < n, weights >= 1 -> *bad) and whether a weight
-// needs more than wb bits (*wide: the caller falls back to (key, weight) pairs).
-__global__ void k_emit_packed(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
-                              const uint32_t* __restrict__ w, uint64_t m, uint32_t n, int vb, int wb,
-                              uint64_t* __restrict__ items, uint32_t* __restrict__ bad, uint32_t* __restrict__ wide) {
+// one item per edge, (min(u,v) << vb | max(u,v)) << wb | w, a self-loop as ~0 (dropped, sorts last); also
+// the input check (ids < n, weights >= 1 -> *bad) and whether a weight needs more than wb bits (*wide: the
+// caller falls back to (key, weight) pairs)
+__global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                             const uint32_t* __restrict__ w, uint64_t m, uint32_t n, int vb, int wb,
+                             uint64_t* __restrict__ items, uint32_t* __restrict__ bad, uint32_t* __restrict__ wide) {
     bool b = false, wd = false;
     const uint64_t wlim = wb >= 32 ? ~0ull : (1ull << wb);
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t u = src[e], v = dst[e], ww = w[e];
         b |= u >= n || v >= n || ww == 0;
         wd |= ww >= wlim;
-        uint64_t i0 = ~0ull, i1 = ~0ull;
-        if (u != v) {
-            i0 = (((u << vb) | v) << wb) | ww;
-            i1 = (((v << vb) | u) << wb) | ww;
-        }
-        reinterpret_cast<uint4*>(items)[e] =
-            make_uint4((uint32_t)i0, (uint32_t)(i0 >> 32), (uint32_t)i1, (uint32_t)(i1 >> 32));
+        const uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
+        items[e] = u != v ? (((lo << vb) | hi) << wb) | ww : ~0ull;
     }
     if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
     if (__any_sync(0xffffffffu, wd) && lane_id() == 0) atomicExch(wide, 1u);
+}
+
+// Distinct edges in two orders: U by (a, b) and T by (b, a) (a < b).  Row x of the symmetric CSR is its
+// lower entries (the a of T's run b = x, ascending) followed by its upper entries (the b of U's run
+// a = x, ascending).  Run boundaries give each row's two counts.
+__global__ void k_canon_runs(const uint64_t* __restrict__ U, const uint64_t* __restrict__ T, uint32_t mu, int vb,
+                             int wb, uint32_t* __restrict__ ustart, uint32_t* __restrict__ uend,
+                             uint32_t* __restrict__ tstart, uint32_t* __restrict__ tend) {
+    const int ash = 64 - vb;
+    const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
+        const uint32_t a = (uint32_t)(U[i] >> ash);
+        if (i == 0 || (uint32_t)(U[i - 1] >> ash) != a) ustart[a] = i;
+        if (i + 1 == mu || (uint32_t)(U[i + 1] >> ash) != a) uend[a] = i + 1;
+        const uint32_t b = (uint32_t)(T[i] >> wb) & cmask;
+        if (i == 0 || ((uint32_t)(T[i - 1] >> wb) & cmask) != b) tstart[b] = i;
+        if (i + 1 == mu || ((uint32_t)(T[i + 1] >> wb) & cmask) != b) tend[b] = i + 1;
+    }
+}
+
+// row degrees; also the directed entry count 2 mu into *nnz
+__global__ void k_canon_deg(uint32_t n, const uint32_t* __restrict__ ustart, const uint32_t* __restrict__ uend,
+                            const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend,
+                            uint64_t* __restrict__ deg, uint32_t mu, uint32_t* __restrict__ nnz) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nnz = 2 * mu;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        deg[x] = (uint64_t)(uend[x] - ustart[x]) + (tend[x] - tstart[x]);
+}
+
+// (a position outside its row's part means inconsistent runs: recorded in *err, the write skipped)
+__global__ void k_canon_scatter(const uint64_t* __restrict__ U, const uint64_t* __restrict__ T, uint32_t mu, int vb,
+                                int wb, const uint32_t* __restrict__ ustart, const uint32_t* __restrict__ tstart,
+                                const uint32_t* __restrict__ tend, const uint64_t* __restrict__ off,
+                                uint32_t* __restrict__ row, uint2* __restrict__ adj, uint32_t* __restrict__ err) {
+    const int ash = 64 - vb;
+    const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
+    const uint32_t wmask = wb >= 32 ? 0xFFFFFFFFu : ((1u << wb) - 1u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
+        const uint64_t u = U[i], t = T[i];
+        const uint32_t a = (uint32_t)(u >> ash), b = (uint32_t)(u >> wb) & cmask;
+        const uint64_t pu = off[a] + (tend[a] - tstart[a]) + (i - ustart[a]);  // after row a's lower entries
+        if (i >= ustart[a] && pu < off[a + 1]) {
+            adj[pu] = make_uint2(b, (uint32_t)u & wmask);
+            row[pu] = a;
+        } else {
+            atomicExch(err, 1u);
+        }
+        const uint32_t ta = (uint32_t)(t >> ash), tb = (uint32_t)(t >> wb) & cmask;
+        const uint64_t pt = off[tb] + (i - tstart[tb]);
+        if (i >= tstart[tb] && i < tend[tb]) {
+            adj[pt] = make_uint2(ta, (uint32_t)t & wmask);
+            row[pt] = tb;
+        } else {
+            atomicExch(err, 1u);
+        }
+    }
 }
 
 __global__ void k_iota(uint32_t* __restrict__ a, uint32_t n) {
@@ -84,12 +137,13 @@ __device__ __forceinline__ void cc_link(uint32_t u, uint32_t v, uint32_t* parent
     }
 }
 
-// first pass: link every node with its r-th neighbour
+// first pass: link every node with its r-th neighbour (ids >= n, which a consistent CSR never holds, are
+// skipped rather than followed)
 __global__ void k_cc_link_nth(const uint64_t* __restrict__ off, const uint2* __restrict__ adj, uint32_t n, uint32_t r,
                               uint32_t* __restrict__ parent) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const uint64_t b = off[v];
-        if (b + r < off[v + 1]) cc_link(v, adj[b + r].x, parent);
+        if (b + r < off[v + 1] && adj[b + r].x < n) cc_link(v, adj[b + r].x, parent);
     }
 }
 
@@ -102,7 +156,8 @@ __global__ void k_cc_link_rest(const uint64_t* __restrict__ off, const uint2* __
         uint32_t r = parent[v];
         while (parent[r] != r) r = parent[r];
         if (r == giant) continue;
-        for (uint64_t j = off[v] + skip; j < off[v + 1]; ++j) cc_link(v, adj[j].x, parent);
+        for (uint64_t j = off[v] + skip; j < off[v + 1]; ++j)
+            if (adj[j].x < n) cc_link(v, adj[j].x, parent);
     }
 }
 
@@ -356,12 +411,14 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_TRY(off.alloc((size_t)n + 1, s));
     bool packed = wb >= 1;
     if (packed) {
-        DBuf<uint64_t> items, items2;
-        CLD_TRY(items.alloc(cnt ? cnt : 1, s));
+        // one item per edge, sorted on (a, b) and de-duplicated (U); the same distinct edges sorted on b alone
+        // (stable, so by (b, a): T) give every row's entries below the diagonal; rows are assembled from both
+        DBuf<uint64_t> items, items2, uniq;
+        CLD_TRY(items.alloc(m ? m : 1, s));
         if (m > 0) {
-            CLD_K(K_CSR, s, k_emit_packed<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
-                                                                          (const uint32_t*)dw, m, n, vb, wb,
-                                                                          items.get(), scal.get(), scal.get() + 2));
+            CLD_K(K_CSR, s, k_emit_canon<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
+                                                                         (const uint32_t*)dw, m, n, vb, wb, items.get(),
+                                                                         scal.get(), scal.get() + 2));
             CLD_LAUNCH_CHECK();
         }
         CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -369,12 +426,38 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         if (hbad[0]) return fail(CLDIAM_ERR_INVALID_ARG, "edge with node id >= n or weight 0");
         packed = hbad[2] == 0;
         if (packed) {
-            CLD_TRY(items2.alloc(cnt ? cnt : 1, s));
+            CLD_TRY(items2.alloc(m ? m : 1, s));
+            CLD_TRY(uniq.alloc(m ? m : 1, s));
             bool alt = false;
-            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), cnt, wb, 2 * vb, &alt, s, scal.get() + 8));
-            // unique (row, col) runs with their lightest weight, in one look-back pass
-            CLD_TRY(unique_packed_csr(alt ? items2.get() : items.get(), cnt, vb, row.get(), adj.get(), off.get(), n,
-                                      scal.get() + 1, s));
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), m, wb, 2 * vb, &alt, s, scal.get() + 8));
+            CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s));
+            CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            CLD_CUDA(cudaStreamSynchronize(s));
+            const uint32_t mu = hbad[1];  // distinct undirected edges
+            bool alt2 = false;
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), mu, wb, vb, &alt2, s, scal.get() + 8, uniq.get()));
+            const uint64_t* T = alt2 ? items2.get() : items.get();
+            DBuf<uint32_t> runs;
+            DBuf<uint64_t> degs;
+            CLD_TRY(runs.alloc(4 * (size_t)n, s));
+            CLD_TRY(degs.alloc(n, s));
+            CLD_CUDA(cudaMemsetAsync(runs.get(), 0, 4 * (size_t)n * 4, s));
+            uint32_t* ustart = runs.get();
+            uint32_t* uend = ustart + n;
+            uint32_t* tstart = uend + n;
+            uint32_t* tend = tstart + n;
+            if (mu > 0)
+                CLD_K(K_CSR, s, k_canon_runs<<<grid_for(mu, 256), 256, 0, s>>>(uniq.get(), T, mu, vb, wb, ustart, uend,
+                                                                              tstart, tend));
+            CLD_K(K_CSR, s, k_canon_deg<<<grid_for(n, 256), 256, 0, s>>>(n, ustart, uend, tstart, tend, degs.get(), mu,
+                                                                        scal.get() + 1));
+            CLD_LAUNCH_CHECK();
+            CLD_TRY(scan_exclusive_u64(degs.get(), off.get(), n, off.get() + n, s));
+            if (mu > 0)
+                CLD_K(K_CSR, s, k_canon_scatter<<<grid_for(mu, 256), 256, 0, s>>>(uniq.get(), T, mu, vb, wb, ustart,
+                                                                                 tstart, tend, off.get(), row.get(),
+                                                                                 adj.get(), scal.get() + 8));
+            CLD_LAUNCH_CHECK();
         }
     }
     if (!packed) {
@@ -436,7 +519,10 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         std::vector<uint32_t> hs(kSamples);
         CLD_CUDA(cudaMemcpyAsync(hs.data(), samp.get(), kSamples * 4, cudaMemcpyDeviceToHost, s));
         CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaMemcpyAsync(hbad + 8, scal.get() + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CLD_CUDA(cudaStreamSynchronize(s));
+        // a failed sort or assembly leaves the CSR unusable: stop before anything indexes by its entries
+        if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired or CSR assembly inconsistent");
         nnz = hbad[1];
         if (nnz > 0) {
             std::sort(hs.begin(), hs.end());
@@ -526,7 +612,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_CUDA(cudaMemcpyAsync(hsum, wsum.get(), 8, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, 8 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
-    if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired");
+    if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired or CSR assembly inconsistent");
     if (flags & CLDIAM_CSR_LCC) {
         g->n = hbad[4];
         g->nnz = hbad[5];

@@ -286,7 +286,7 @@ constexpr long long OS_WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: a look-bac
 // Digit histograms of every pass from one read of the keys: one private histogram per warp and pass
 // in shared memory (warps x npass x 256 words, dynamic), so shared atomics collide only within a warp.
 template <class K>
-__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass, int shift0,
+__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, size_t n, int npass, int shift0, int bits,
                                                  uint32_t* __restrict__ hist) {
     extern __shared__ uint32_t hs[];
     const unsigned w = threadIdx.x >> 5;
@@ -306,7 +306,9 @@ __global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, siz
         for (int u = 0; u < U; ++u) {
             const bool valid = base + (size_t)u * stride < n;
             for (int p = 0; p < npass; ++p) {
-                const uint32_t d = (uint32_t)((kk[u] >> (shift0 + 8 * p)) & 0xFF);
+                // the last digit holds only the key bits left (bits above the key are not sorted on)
+                const uint32_t dm = bits - 8 * p >= 8 ? 0xFFu : ((1u << (bits - 8 * p)) - 1u);
+                const uint32_t d = (uint32_t)(kk[u] >> (shift0 + 8 * p)) & dm;
                 if (valid) atomicAdd(&h[p * OS_RADIX + d], 1u);
             }
         }
@@ -335,16 +337,17 @@ __global__ void k_os_hist_scan(uint32_t* __restrict__ hist, int npass) {
     }
 }
 
-// Digit (key >> shift) & 0xFF.  For 64-bit keys HI says shift >= 32 (uniform per pass), so the
-// digit comes from one 32-bit word, or from a funnel shift of the two when it may straddle them.
+// Digit (key >> shift) & dm (dm = 0xFF, or fewer bits in the last pass of a key whose width is not a
+// multiple of 8).  For 64-bit keys HI says shift >= 32 (uniform per pass), so the digit comes from one
+// 32-bit word, or from a funnel shift of the two when it may straddle them.
 template <class K, bool HI>
-__device__ __forceinline__ uint32_t os_digit(K k, uint32_t sh) {
+__device__ __forceinline__ uint32_t os_digit(K k, uint32_t sh, uint32_t dm) {
     if constexpr (sizeof(K) == 8) {
         const uint32_t lo = (uint32_t)k, hi = (uint32_t)((uint64_t)k >> 32);
-        if constexpr (HI) return (hi >> sh) & 0xFFu;
-        else return __funnelshift_r(lo, hi, sh) & 0xFFu;
+        if constexpr (HI) return (hi >> sh) & dm;
+        else return __funnelshift_r(lo, hi, sh) & dm;
     } else {
-        return ((uint32_t)k >> sh) & 0xFFu;
+        return ((uint32_t)k >> sh) & dm;
     }
 }
 
@@ -352,7 +355,7 @@ __device__ __forceinline__ uint32_t os_digit(K k, uint32_t sh) {
 template <class K, bool KV, bool HI, int OS_ITEMS = OsCfg<K, KV>::ITEMS, int OS_TILE = OsCfg<K, KV>::TILE>
 __global__ void __launch_bounds__(OS_THREADS, 4)
     k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-              uint32_t* __restrict__ vout, size_t n, uint32_t sh, const uint32_t* __restrict__ goff,
+              uint32_t* __restrict__ vout, size_t n, uint32_t sh, uint32_t dm, const uint32_t* __restrict__ goff,
               unsigned long long* __restrict__ status, uint32_t* __restrict__ tile_ctr, uint32_t* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     K* s_key = reinterpret_cast<K*>(os_smem);
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
         const bool valid = lbase + (uint32_t)i * 32 < rem;
-        const uint32_t d = os_digit<K, HI>(key[i], sh);
+        const uint32_t d = os_digit<K, HI>(key[i], sh, dm);
         unsigned peers = 0xFFFFFFFFu;
         if (!full) {  // the last tile: items past the end form their own group
             const unsigned vb = __ballot_sync(0xffffffffu, valid);
@@ -496,14 +499,14 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         for (int j = 0; j < OS_ITEMS; ++j) {
             const uint32_t i = (uint32_t)j * OS_THREADS + tid;
             const K k = s_key[i];
-            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh)] + i;
+            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh, dm)] + i;
             kout[pos] = k;
             if constexpr (KV) vout[pos] = s_val[i];
         }
     } else {
         for (uint32_t i = tid; i < rem; i += OS_THREADS) {
             const K k = s_key[i];
-            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh)] + i;
+            const uint32_t pos = gdiff[os_digit<K, HI>(k, sh, dm)] + i;
             kout[pos] = k;
             if constexpr (KV) vout[pos] = s_val[i];
         }
@@ -513,9 +516,13 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
 // LSD sort of n items on key bits [shift0, shift0 + bits); vals == nullptr sorts keys only.
 template <class K>
 static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, size_t n, int shift0,
-                                     int bits, bool* in_alt, cudaStream_t s, uint32_t* err_dev = nullptr) {
+                                     int bits, bool* in_alt, cudaStream_t s, uint32_t* err_dev = nullptr,
+                                     const K* first_in = nullptr) {
     *in_alt = false;
-    if (n <= 1 || bits <= 0) return CLDIAM_OK;
+    if (n <= 1 || bits <= 0) {
+        if (first_in && n) CLD_CUDA(cudaMemcpyAsync(keys, first_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
+        return CLDIAM_OK;
+    }
     if (n > 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "radix sort limited to 2^32 - 1 items");
     const bool kv = vals != nullptr;
     const int npass = (bits + 7) / 8;
@@ -549,11 +556,13 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         CLD_CUDA(cudaFuncSetAttribute(k_os_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * OS_WARPS * OS_RADIX * 4));
         if (dev >= 0 && dev < 64) hist_attr_set[dev] = true;
     }
-    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, hsm, s>>>(keys, n, npass, shift0, hist.get()));
+    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, hsm, s>>>(first_in ? first_in : keys, n, npass, shift0, bits,
+                                                                              hist.get()));
     CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist.get(), npass));
     CLD_LAUNCH_CHECK();
     prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
-    K* ki = keys;
+    // first_in (keys only): the first pass reads it and writes keys_alt, so first_in is never written
+    const K* ki = first_in ? first_in : keys;
     uint32_t* vi = vals;
     K* ko = keys_alt;
     uint32_t* vo = vals_alt;
@@ -563,26 +572,29 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         const int shift = shift0 + 8 * p;
         const bool hi = sizeof(K) == 8 && shift >= 32;
         const uint32_t sh = (uint32_t)shift & 31u;
+        const uint32_t dm = bits - 8 * p >= 8 ? 0xFFu : ((1u << (bits - 8 * p)) - 1u);  // key bits only
         const uint32_t* go = hist.get() + p * OS_RADIX;
         uint32_t* tc = ctl.get() + p;
         uint32_t* er = err_dev ? err_dev : ctl.get() + 2 * npass;
         if (kv && hi) {
-            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, go,
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, true><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, dm, go,
                                                                                               status.get(), tc, er));
         } else if (kv) {
-            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, false><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, go,
+            CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, true, false><<<ntiles, OS_THREADS, smem, s>>>(ki, vi, ko, vo, n, sh, dm, go,
                                                                                                status.get(), tc, er));
         } else if (hi) {
             CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, false, true><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n,
-                                                                                               sh, go, status.get(), tc, er));
+                                                                                               sh, dm, go, status.get(), tc, er));
         } else {
             CLD_K(K_RADIX_SCATTER, s, k_os_pass<K, false, false><<<ntiles, OS_THREADS, smem, s>>>(ki, nullptr, ko, nullptr, n,
-                                                                                                sh, go, status.get(), tc, er));
+                                                                                                sh, dm, go, status.get(), tc, er));
         }
         CLD_LAUNCH_CHECK();
         // algorithmic bytes: every item (key and value) read once and written once
         prof_add_bytes(K_RADIX_SCATTER, 2.0 * (double)n * (sizeof(K) + (kv ? sizeof(uint32_t) : 0)));
-        K* tk = ki; ki = ko; ko = tk;
+        const K* done_in = ki;
+        ki = ko;
+        ko = (first_in && p == 0) ? keys : const_cast<K*>(done_in);  // first_in is never written
         uint32_t* tv = vi; vi = vo; vo = tv;
         alt = !alt;
     }
@@ -762,17 +774,12 @@ static cldiam_status unique_min_sorted(const K* keys, const uint32_t* vals, size
     return CLDIAM_OK;
 }
 
-// ------------------------------------------------------------------ CSR de-duplication of packed items
-// Items (row << vb | col) << wb | w with wb = 64 - 2 vb, sorted on their (row, col) bits; ~0 marks a
-// dropped item (self-loop) and sorts last.  Two passes over tiles of 2,048 items: the first counts each
-// tile's run heads, an exclusive scan gives each tile its first head index, and the second flags the
-// heads again and writes row_out[r], adj_out[r] = (col, w) for them and the CSR offsets.  (A one-pass
-// form with a decoupled look-back over the tile counts was slower: its tiles wait on each other while
-// the extra read of the two-pass form streams at full bandwidth.)
-// Run minima: a head stores its own weight, and after a block barrier every other item of a run
-// headed in the same tile folds its weight in with atomicMin; the items of the tile's last run that
-// lie in later tiles are read by the head's tile (a warp scanning forward) and folded in the same way,
-// so a tile never touches a run headed in an earlier one and adj_out needs no pre-fill.
+// ------------------------------------------------------------------ de-duplication of packed edge items
+// Items (a << vb | b) << wb | w with wb = 64 - 2 vb, sorted on their (a, b) bits; ~0 marks a dropped item
+// (self-loop) and sorts last.  Two passes over tiles of 2,048 items: the first counts each tile's run
+// heads, an exclusive scan gives each tile its first head index, and the second flags the heads again
+// and writes them out.  (A one-pass form with a decoupled look-back over the tile counts was slower: its
+// tiles wait on each other while the extra read of the two-pass form streams at full bandwidth.)
 constexpr int UP_THREADS = 256;
 constexpr int UP_WARPS = UP_THREADS / 32;
 constexpr int UP_ITEMS = 8;
@@ -819,68 +826,48 @@ __global__ void __launch_bounds__(UP_THREADS) k_unique_packed_count(const uint64
     }
 }
 
-// Second pass: the tile's first head index is first[tile], the exclusive scan of the first pass.
+// De-duplication that keeps packed items: out[r] = the r-th distinct (row, col) with its smallest weight.
+// Items of one run differ only in their weight bits, so the run minimum is the 64-bit minimum of the items:
+// heads store their item, the other members of runs headed in the tile fold theirs in with atomicMin after
+// a block barrier, and the tile's last run is followed into later tiles by one warp.
 __global__ void __launch_bounds__(UP_THREADS, 4)
-    k_unique_packed(const uint64_t* __restrict__ items, uint32_t cnt, int vb, uint32_t* __restrict__ row_out,
-                    uint2* __restrict__ adj_out, uint64_t* __restrict__ off_out, uint32_t nrows,
-                    uint32_t* __restrict__ total, const uint32_t* __restrict__ first) {
-    __shared__ uint32_t s_woff[UP_WARPS];  // heads per warp, then the global index of the warp's first head
+    k_unique_items(const uint64_t* __restrict__ items, uint32_t cnt, int vb, unsigned long long* __restrict__ out,
+                   uint32_t* __restrict__ total, const uint32_t* __restrict__ first) {
+    __shared__ uint32_t s_woff[UP_WARPS];
     __shared__ uint32_t s_first, s_count;
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
     const uint32_t tile = blockIdx.x;
     const uint64_t tbase = (uint64_t)tile * UP_TILE;
     const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
     const int wb = 64 - 2 * vb;
-    const uint64_t same_lim = 1ull << wb;  // two items with (a ^ b) below this share (row, col)
-    const uint64_t valid_lim = ~0ull << wb;  // items below this are not dropped
-    const uint32_t wmask = wb >= 32 ? 0xFFFFFFFFu : ((1u << wb) - 1u);
-    const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
-    const uint32_t rsh = 32u - (uint32_t)vb;  // row = high word >> rsh
-    const uint32_t wstart = w * (UP_ITEMS * 32);  // tile position of the warp's first item (warp-striped rows of 32)
+    const uint64_t same_lim = 1ull << wb, valid_lim = ~0ull << wb;
+    const uint32_t wstart = w * (UP_ITEMS * 32);
     const uint64_t* it = items + tbase;
-
     uint64_t x[UP_ITEMS];
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i) {
         const uint32_t li = wstart + (uint32_t)i * 32 + l;
         x[i] = li < rem ? it[li] : ~0ull;
     }
-    // the item before the warp's first one (none before position 0: ~0 differs from every valid item)
     uint64_t carry = ~0ull;
     if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
-    uint32_t head = 0, rstart = 0, lastv = 0;  // per item bits: run head; first item of its row; last valid item
-    uint32_t ex_pk[UP_ITEMS / 4];               // heads before the item within the warp (< 256), one byte each
-    uint32_t run = 0;
-    unsigned vbal_prev = 0;
+    uint32_t head = 0, run = 0;
+    uint32_t ex_pk[UP_ITEMS / 4];
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i) {
-        // previous item: lane l - 1 of this row; for lane 0, lane 31 of the previous row (rotation carry)
         const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
         const uint64_t prev = l == 0 ? carry : rot;
         carry = rot;
-        const bool valid = x[i] < valid_lim;
         const bool f = up_head(prev, x[i], same_lim, valid_lim);
-        const bool rs = f && (prev >= valid_lim || (uint32_t)(prev >> 32) >> rsh != (uint32_t)(x[i] >> 32) >> rsh);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const unsigned vbal = __ballot_sync(0xffffffffu, valid);
         const uint32_t ex = run + (uint32_t)__popc(bal & lanemask_lt());
         run += (uint32_t)__popc(bal);
         if (i % 4 == 0) ex_pk[i / 4] = ex;
         else ex_pk[i / 4] |= ex << (8 * (i % 4));
         head |= (f ? 1u : 0u) << i;
-        rstart |= (rs ? 1u : 0u) << i;
-        // last valid item: its successor (lane l + 1, or lane 0 of the next row) is dropped or absent
-        if (i > 0 && l == 31 && ((vbal_prev >> 31) & 1u) && !(vbal & 1u)) lastv |= 1u << (i - 1);
-        if (valid && l < 31 && !((vbal >> (l + 1)) & 1u)) lastv |= 1u << i;
-        vbal_prev = vbal;
-    }
-    if (l == 31 && ((vbal_prev >> 31) & 1u)) {  // the warp's last item: look at the next one in memory
-        const uint64_t pos = tbase + wstart + UP_ITEMS * 32;  // position after the warp's last item
-        if (pos >= cnt || items[pos] >= valid_lim) lastv |= 1u << (UP_ITEMS - 1);
     }
     if (l == 0) s_woff[w] = run;
     __syncthreads();
-
     if (w == 0) {
         const uint32_t v = l < UP_WARPS ? s_woff[l] : 0u;
         const uint32_t incl = warp_incl_scan(v);
@@ -895,58 +882,37 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
     }
     __syncthreads();
     const uint32_t woff = s_woff[w], tfirst = s_first;
-
-    // heads: row, (col, own weight), offsets of the rows from the previous item's row + 1 up to theirs
 #pragma unroll
-    for (int i = 0; i < UP_ITEMS; ++i) {
-        if (!((head >> i) & 1u)) continue;
-        const uint32_t r = woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu);
-        const uint32_t row = (uint32_t)(x[i] >> 32) >> rsh;
-        row_out[r] = row;
-        adj_out[r] = make_uint2((uint32_t)(x[i] >> wb) & cmask, (uint32_t)x[i] & wmask);
-        if ((rstart >> i) & 1u) {
-            const uint64_t pos = tbase + wstart + (uint32_t)i * 32 + l;
-            const uint32_t q0 = pos == 0 ? 0u : (uint32_t)(items[pos - 1] >> 32) >> rsh;
-            for (uint32_t q = pos == 0 ? 0u : q0 + 1; q <= row; ++q) off_out[q] = r;
-        }
-    }
+    for (int i = 0; i < UP_ITEMS; ++i)
+        if ((head >> i) & 1u) out[woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu)] = x[i];
     __syncthreads();
-    // other members of runs headed in this tile; the last valid item closes the offsets
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i) {
         const uint32_t li = wstart + (uint32_t)i * 32 + l;
-        if (li >= rem || x[i] >= valid_lim) continue;
-        const uint32_t f = (head >> i) & 1u;
+        if (li >= rem || x[i] >= valid_lim || ((head >> i) & 1u)) continue;
         const uint32_t before = woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu);  // heads before the item
-        const uint32_t r = before + f - 1u;
-        if (!f && before > tfirst) atomicMin(&adj_out[r].y, (uint32_t)x[i] & wmask);
-        if ((lastv >> i) & 1u) {
-            const uint32_t row = (uint32_t)(x[i] >> 32) >> rsh;
-            for (uint32_t q = row + 1; q <= nrows; ++q) off_out[q] = (uint64_t)r + 1;
-        }
+        if (before > tfirst) atomicMin(&out[before - 1], (unsigned long long)x[i]);
     }
     // the tile's last run continuing into later tiles: scan forward while the key repeats
     if (w == UP_WARPS - 1 && rem == (uint32_t)UP_TILE && s_count > 0 && tbase + UP_TILE < cnt) {
         const uint64_t last = __shfl_sync(0xffffffffu, x[UP_ITEMS - 1], 31);
         if (last < valid_lim) {
-            uint32_t mn = 0xFFFFFFFFu;
+            unsigned long long mn = ~0ull;
             for (uint64_t p = tbase + UP_TILE;; p += 32) {
                 const uint64_t y = p + l < cnt ? items[p + l] : ~0ull;
                 const unsigned same = __ballot_sync(0xffffffffu, y < valid_lim && (y ^ last) < same_lim);
-                const unsigned take = ~same ? (unsigned)(__ffs(~same) - 1) : 32u;  // leading lanes of the run
-                if (l < take) mn = min(mn, (uint32_t)y & wmask);
+                const unsigned take = ~same ? (unsigned)(__ffs(~same) - 1) : 32u;
+                if (l < take) mn = min(mn, (unsigned long long)y);
                 if (take < 32) break;
             }
             mn = warp_min(mn);
-            if (l == 0 && mn != 0xFFFFFFFFu) atomicMin(&adj_out[tfirst + s_count - 1].y, mn);
+            if (l == 0 && mn != ~0ull) atomicMin(&out[tfirst + s_count - 1], mn);
         }
     }
 }
 
-cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint32_t* row_out, uint2* adj_out,
-                                uint64_t* off_out, uint32_t nrows, uint32_t* total_dev, cudaStream_t s) {
-    // every offset is written when some item is kept; zeros cover the case with none
-    CLD_CUDA(cudaMemsetAsync(off_out, 0, ((size_t)nrows + 1) * 8, s));
+cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64_t* out, uint32_t* total_dev,
+                               cudaStream_t s) {
     if (cnt == 0) {
         CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
         return CLDIAM_OK;
@@ -960,8 +926,9 @@ cldiam_status unique_packed_csr(const uint64_t* items, size_t cnt, int vb, uint3
     CLD_K(K_CSR, s, k_unique_packed_count<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, heads.get()));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, nullptr, s));
-    CLD_K(K_CSR, s, k_unique_packed<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, row_out, adj_out, off_out,
-                                                                  nrows, total_dev, first.get()));
+    CLD_K(K_CSR, s, k_unique_items<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb,
+                                                                 reinterpret_cast<unsigned long long*>(out), total_dev,
+                                                                 first.get()));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
@@ -984,8 +951,8 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
     return radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, 0, bits, in_alt, s);
 }
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits, bool* in_alt,
-                                  cudaStream_t s, uint32_t* err_dev) {
-    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s, err_dev);
+                                  cudaStream_t s, uint32_t* err_dev, const uint64_t* first_in) {
+    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s, err_dev, first_in);
 }
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* in_alt, cudaStream_t s) {
