@@ -64,26 +64,44 @@ __global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* _
 // Distinct edges in two orders: U by (a, b) and T by (b, a) (a < b).  Row x of the symmetric CSR is its
 // lower entries (the a of T's run b = x, ascending) followed by its upper entries (the b of U's run
 // a = x, ascending).  Run boundaries give each row's two counts.
+// (also the directed entry count 2 mu into *nnz)
 __global__ void k_canon_runs(const uint64_t* __restrict__ U, const uint64_t* __restrict__ T, uint32_t mu, int vb,
                              int wb, uint32_t* __restrict__ ustart, uint32_t* __restrict__ uend,
-                             uint32_t* __restrict__ tstart, uint32_t* __restrict__ tend) {
+                             uint32_t* __restrict__ tstart, uint32_t* __restrict__ tend, uint32_t* __restrict__ nnz) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nnz = 2 * mu;
     const int ash = 64 - vb;
     const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
-        const uint32_t a = (uint32_t)(U[i] >> ash);
-        if (i == 0 || (uint32_t)(U[i - 1] >> ash) != a) ustart[a] = i;
-        if (i + 1 == mu || (uint32_t)(U[i + 1] >> ash) != a) uend[a] = i + 1;
-        const uint32_t b = (uint32_t)(T[i] >> wb) & cmask;
-        if (i == 0 || ((uint32_t)(T[i - 1] >> wb) & cmask) != b) tstart[b] = i;
-        if (i + 1 == mu || ((uint32_t)(T[i + 1] >> wb) & cmask) != b) tend[b] = i + 1;
+    constexpr uint32_t kNo = 0xFFFFFFFFu;  // no neighbour (ids are below n <= 2^32 - 1)
+    const unsigned l = lane_id();
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count; neighbours' row ids come by shuffle, the warp's two edge lanes load theirs
+    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < mu; i0 += stride) {
+        const uint32_t i = i0 + l;
+        const bool ok = i < mu;
+        const uint32_t a = ok ? (uint32_t)(U[i] >> ash) : kNo;
+        const uint32_t b = ok ? (uint32_t)(T[i] >> wb) & cmask : kNo;
+        uint32_t ap = __shfl_up_sync(0xffffffffu, a, 1), an = __shfl_down_sync(0xffffffffu, a, 1);
+        uint32_t bp = __shfl_up_sync(0xffffffffu, b, 1), bn = __shfl_down_sync(0xffffffffu, b, 1);
+        if (l == 0) {
+            ap = ok && i > 0 ? (uint32_t)(U[i - 1] >> ash) : kNo;
+            bp = ok && i > 0 ? (uint32_t)(T[i - 1] >> wb) & cmask : kNo;
+        }
+        if (l == 31) {
+            an = i + 1 < mu ? (uint32_t)(U[i + 1] >> ash) : kNo;
+            bn = i + 1 < mu ? (uint32_t)(T[i + 1] >> wb) & cmask : kNo;
+        }
+        if (!ok) continue;
+        if (ap != a) ustart[a] = i;
+        if (an != a) uend[a] = i + 1;
+        if (bp != b) tstart[b] = i;
+        if (bn != b) tend[b] = i + 1;
     }
 }
 
-// row degrees; also the directed entry count 2 mu into *nnz
+// row degrees
 __global__ void k_canon_deg(uint32_t n, const uint32_t* __restrict__ ustart, const uint32_t* __restrict__ uend,
                             const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend,
-                            uint64_t* __restrict__ deg, uint32_t mu, uint32_t* __restrict__ nnz) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nnz = 2 * mu;
+                            uint64_t* __restrict__ deg) {
     for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
         deg[x] = (uint64_t)(uend[x] - ustart[x]) + (tend[x] - tstart[x]);
 }
@@ -137,27 +155,54 @@ __device__ __forceinline__ void cc_link(uint32_t u, uint32_t v, uint32_t* parent
     }
 }
 
-// first pass: link every node with its r-th neighbour (ids >= n, which a consistent CSR never holds, are
+// A node's neighbours in CSR order, from the CSR ...
+struct CsrAdj {
+    const uint64_t* off;
+    const uint2* adj;
+    __device__ uint32_t deg(uint32_t v) const { return (uint32_t)(off[v + 1] - off[v]); }
+    __device__ uint32_t nbr(uint32_t v, uint32_t r) const { return adj[off[v] + r].x; }
+};
+// ... or from the two orders of the distinct edges (a, b), a < b: first the lower neighbours (the a of
+// v's run in T, sorted by (b, a)), then the upper ones (the b of v's run in U, sorted by (a, b))
+struct ListAdj {
+    const uint64_t* U;
+    const uint64_t* T;
+    const uint32_t *ustart, *uend, *tstart, *tend;
+    int ash, wb;
+    uint32_t cmask;
+    __device__ uint32_t lo(uint32_t v) const { return tend[v] - tstart[v]; }
+    __device__ uint32_t deg(uint32_t v) const { return lo(v) + (uend[v] - ustart[v]); }
+    __device__ uint32_t nbr(uint32_t v, uint32_t r) const {
+        const uint32_t l = lo(v);
+        return r < l ? (uint32_t)(T[tstart[v] + r] >> ash) : (uint32_t)(U[ustart[v] + (r - l)] >> wb) & cmask;
+    }
+};
+
+// first pass: link every node with its r-th neighbour (ids >= n, which a consistent graph never holds, are
 // skipped rather than followed)
-__global__ void k_cc_link_nth(const uint64_t* __restrict__ off, const uint2* __restrict__ adj, uint32_t n, uint32_t r,
-                              uint32_t* __restrict__ parent) {
+template <class A>
+__global__ void k_cc_link_nth(A g, uint32_t n, uint32_t r, uint32_t* __restrict__ parent) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint64_t b = off[v];
-        if (b + r < off[v + 1] && adj[b + r].x < n) cc_link(v, adj[b + r].x, parent);
+        if (r >= g.deg(v)) continue;
+        const uint32_t c = g.nbr(v, r);
+        if (c < n) cc_link(v, c, parent);
     }
 }
 
 // final pass: nodes outside the dominant tree link all their remaining
 // neighbours (an edge with both ends in the dominant tree adds nothing; an
 // edge with one end outside is linked from that end)
-__global__ void k_cc_link_rest(const uint64_t* __restrict__ off, const uint2* __restrict__ adj, uint32_t n,
-                               uint32_t skip, uint32_t giant, uint32_t* __restrict__ parent) {
+template <class A>
+__global__ void k_cc_link_rest(A g, uint32_t n, uint32_t skip, uint32_t giant, uint32_t* __restrict__ parent) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t r = parent[v];
         while (parent[r] != r) r = parent[r];
         if (r == giant) continue;
-        for (uint64_t j = off[v] + skip; j < off[v + 1]; ++j)
-            if (adj[j].x < n) cc_link(v, adj[j].x, parent);
+        const uint32_t d = g.deg(v);
+        for (uint32_t j = skip; j < d; ++j) {
+            const uint32_t c = g.nbr(v, j);
+            if (c < n) cc_link(v, c, parent);
+        }
     }
 }
 
@@ -233,12 +278,12 @@ __global__ void k_cc_keep(const uint32_t* __restrict__ parent, uint32_t n, const
         keep[v] = parent[v] == root ? 1u : 0u;
 }
 
-__global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid,
-                              const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ ndeg,
-                              uint32_t* __restrict__ orig) {
+template <class A>
+__global__ void k_lcc_degrees(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newid, A g, uint32_t n,
+                              uint32_t* __restrict__ ndeg, uint32_t* __restrict__ orig) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
         if (keep[v]) {
-            ndeg[newid[v]] = (uint32_t)(off[v + 1] - off[v]);
+            ndeg[newid[v]] = g.deg(v);
             orig[newid[v]] = v;
         }
 }
@@ -252,7 +297,7 @@ __global__ void k_lcc_offsets(const uint32_t* __restrict__ excl, uint32_t n, con
     const uint32_t n_out = *n_out_dev, total = *total_dev;  // n_out <= n
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_out; i += gridDim.x * blockDim.x) {
         noff[i] = (i == n_out) ? (uint64_t)total : (uint64_t)excl[i];
-        if (i < n_out) {
+        if (map && i < n_out) {
             const uint32_t u = orig[i];
             map[u] = make_uint2(i, excl[i] - (uint32_t)off[u]);
         }
@@ -300,6 +345,51 @@ __global__ void __launch_bounds__(256) k_lcc_copy(const uint2* __restrict__ map,
     sum = block_reduce(sum, [](unsigned long long a, unsigned long long b) { return a + b; }, 0ull);
     if (threadIdx.x == 0 && sum) atomicAdd(wsum, sum);
     mn = block_reduce(mn, [](uint32_t a, uint32_t b) { return a < b ? a : b; }, 0xFFFFFFFFu);
+    if (threadIdx.x == 0 && mn != 0xFFFFFFFFu) atomicMin(wmin, mn);
+}
+
+// The LCC's CSR straight from the two orders of the distinct edges: an edge (a, b) of a kept component
+// goes to row newid[a] after its lower entries (from U) and to row newid[b] (from T); new ids are
+// monotone, so rows stay sorted.  Weight statistics as k_lcc_copy (each undirected edge once: from U).
+// A position outside its row's part is recorded in *err and the write skipped.
+__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint32_t* __restrict__ keep,
+                               const uint32_t* __restrict__ newid, const uint64_t* __restrict__ noff,
+                               uint32_t* __restrict__ nrow, uint2* __restrict__ nadj,
+                               unsigned long long* __restrict__ wsum, uint32_t* __restrict__ wmin,
+                               uint32_t* __restrict__ err) {
+    const uint32_t wmask = g.wb >= 32 ? 0xFFFFFFFFu : ((1u << g.wb) - 1u);
+    unsigned long long sum = 0;
+    uint32_t mn = 0xFFFFFFFFu;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
+        const uint64_t u = g.U[i], t = g.T[i];
+        const uint32_t a = (uint32_t)(u >> g.ash), b = (uint32_t)(u >> g.wb) & g.cmask, w = (uint32_t)u & wmask;
+        if (keep[a]) {
+            const uint32_t na = newid[a];
+            const uint64_t pos = noff[na] + g.lo(a) + (i - g.ustart[a]);
+            if (i >= g.ustart[a] && i < g.uend[a] && pos < noff[na + 1]) {
+                nadj[pos] = make_uint2(newid[b], w);
+                nrow[pos] = na;
+            } else {
+                atomicExch(err, 1u);
+            }
+            sum += w;
+            mn = w < mn ? w : mn;
+        }
+        const uint32_t ta = (uint32_t)(t >> g.ash), tb = (uint32_t)(t >> g.wb) & g.cmask;
+        if (keep[tb]) {
+            const uint32_t nb = newid[tb];
+            const uint64_t pos = noff[nb] + (i - g.tstart[tb]);
+            if (i >= g.tstart[tb] && i < g.tend[tb]) {
+                nadj[pos] = make_uint2(newid[ta], (uint32_t)t & wmask);
+                nrow[pos] = nb;
+            } else {
+                atomicExch(err, 1u);
+            }
+        }
+    }
+    sum = block_reduce(sum, [](unsigned long long x, unsigned long long y) { return x + y; }, 0ull);
+    if (threadIdx.x == 0 && sum) atomicAdd(wsum, sum);
+    mn = block_reduce(mn, [](uint32_t x, uint32_t y) { return x < y ? x : y; }, 0xFFFFFFFFu);
     if (threadIdx.x == 0 && mn != 0xFFFFFFFFu) atomicMin(wmin, mn);
 }
 
@@ -404,16 +494,26 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     DBuf<uint32_t> row, deg, degx;
     DBuf<uint64_t> off;
     DBuf<uint2> adj;
-    CLD_TRY(row.alloc(cnt ? cnt : 1, s));
-    CLD_TRY(adj.alloc(cnt ? cnt : 1, s));
+    // the whole graph's row / adj arrays are allocated only where they are built (the packed path with the
+    // LCC goes from the edge lists straight to the LCC's CSR)
+    const auto alloc_full = [&]() -> cldiam_status {
+        CLD_TRY(row.alloc(cnt ? cnt : 1, s));
+        CLD_TRY(adj.alloc(cnt ? cnt : 1, s));
+        return CLDIAM_OK;
+    };
     CLD_TRY(deg.alloc((size_t)n + 1, s));
     CLD_TRY(degx.alloc((size_t)n + 1, s));
     CLD_TRY(off.alloc((size_t)n + 1, s));
+    const bool lcc = (flags & CLDIAM_CSR_LCC) != 0;
     bool packed = wb >= 1;
+    // packed path: the distinct edges in two orders and their run bounds (the adjacency in list form)
+    DBuf<uint64_t> items, items2, uniq;
+    DBuf<uint32_t> runs;
+    ListAdj la{};
+    uint32_t mu = 0;
     if (packed) {
         // one item per edge, sorted on (a, b) and de-duplicated (U); the same distinct edges sorted on b alone
-        // (stable, so by (b, a): T) give every row's entries below the diagonal; rows are assembled from both
-        DBuf<uint64_t> items, items2, uniq;
+        // (stable, so by (b, a): T) give every row's entries below the diagonal
         CLD_TRY(items.alloc(m ? m : 1, s));
         if (m > 0) {
             CLD_K(K_CSR, s, k_emit_canon<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
@@ -433,35 +533,49 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s));
             CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CLD_CUDA(cudaStreamSynchronize(s));
-            const uint32_t mu = hbad[1];  // distinct undirected edges
+            mu = hbad[1];  // distinct undirected edges
             bool alt2 = false;
             CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), mu, wb, vb, &alt2, s, scal.get() + 8, uniq.get()));
-            const uint64_t* T = alt2 ? items2.get() : items.get();
-            DBuf<uint32_t> runs;
-            DBuf<uint64_t> degs;
             CLD_TRY(runs.alloc(4 * (size_t)n, s));
-            CLD_TRY(degs.alloc(n, s));
             CLD_CUDA(cudaMemsetAsync(runs.get(), 0, 4 * (size_t)n * 4, s));
-            uint32_t* ustart = runs.get();
-            uint32_t* uend = ustart + n;
-            uint32_t* tstart = uend + n;
-            uint32_t* tend = tstart + n;
-            if (mu > 0)
-                CLD_K(K_CSR, s, k_canon_runs<<<grid_for(mu, 256), 256, 0, s>>>(uniq.get(), T, mu, vb, wb, ustart, uend,
-                                                                              tstart, tend));
-            CLD_K(K_CSR, s, k_canon_deg<<<grid_for(n, 256), 256, 0, s>>>(n, ustart, uend, tstart, tend, degs.get(), mu,
-                                                                        scal.get() + 1));
-            CLD_LAUNCH_CHECK();
-            CLD_TRY(scan_exclusive_u64(degs.get(), off.get(), n, off.get() + n, s));
-            if (mu > 0)
-                CLD_K(K_CSR, s, k_canon_scatter<<<grid_for(mu, 256), 256, 0, s>>>(uniq.get(), T, mu, vb, wb, ustart,
-                                                                                 tstart, tend, off.get(), row.get(),
-                                                                                 adj.get(), scal.get() + 8));
-            CLD_LAUNCH_CHECK();
+            la.U = uniq.get();
+            la.T = alt2 ? items2.get() : items.get();
+            la.ustart = runs.get();
+            la.uend = runs.get() + n;
+            la.tstart = runs.get() + 2 * (size_t)n;
+            la.tend = runs.get() + 3 * (size_t)n;
+            la.ash = 64 - vb;
+            la.wb = wb;
+            la.cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
+            uint32_t* r0 = runs.get();
+            if (mu > 0) {
+                CLD_K(K_CSR, s, k_canon_runs<<<grid_for(mu, 256), 256, 0, s>>>(la.U, la.T, mu, vb, wb, r0, r0 + n,
+                                                                              r0 + 2 * (size_t)n, r0 + 3 * (size_t)n,
+                                                                              scal.get() + 1));
+                CLD_LAUNCH_CHECK();
+            }
+            if (!lcc) {
+                // the whole graph's CSR: row x = its lower entries, then its upper entries
+                CLD_TRY(alloc_full());
+                DBuf<uint64_t> degs;
+                CLD_TRY(degs.alloc(n, s));
+                CLD_K(K_CSR, s, k_canon_deg<<<grid_for(n, 256), 256, 0, s>>>(n, la.ustart, la.uend, la.tstart, la.tend,
+                                                                            degs.get()));
+                CLD_LAUNCH_CHECK();
+                CLD_TRY(scan_exclusive_u64(degs.get(), off.get(), n, off.get() + n, s));
+                if (mu > 0) {
+                    CLD_K(K_CSR, s, k_canon_scatter<<<grid_for(mu, 256), 256, 0, s>>>(la.U, la.T, mu, vb, wb, la.ustart,
+                                                                                     la.tstart, la.tend, off.get(),
+                                                                                     row.get(), adj.get(),
+                                                                                     scal.get() + 8));
+                    CLD_LAUNCH_CHECK();
+                }
+            }
         }
     }
     if (!packed) {
         // keys u*n + v (u != v) are at most n^2 - 2; n^2 - 1 marks a dropped self-loop
+        CLD_TRY(alloc_full());
         CLD_CUDA(cudaMemsetAsync(adj.get(), 0xFF, (size_t)(cnt ? cnt : 1) * 8, s));  // run minima fold in
         const uint64_t sentinel = (uint64_t)n * (uint64_t)n - 1;
         DBuf<uint64_t> keys, keys2;
@@ -486,8 +600,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(unique_min_sorted_u64(alt ? keys2.get() : keys.get(), alt ? vals2.get() : vals.get(), cnt, sentinel, n,
                                       row.get(), &adj.get()->x, &adj.get()->y, 2, off.get(), n, scal.get() + 1, s));
     }
-    // (the row offsets were written by the run heads; the entry count stays on the device until the
-    // host needs it, read together with the next result)
+    // (the entry count stays on the device until the host needs it, read together with the next result)
     uint32_t nnz = 0;
     DBuf<uint32_t> orig;
     // weight statistics for the initial Delta (Algorithm 1 / Section 5): sum over u < v, minimum
@@ -496,18 +609,20 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     CLD_CUDA(cudaMemsetAsync(wsum.get(), 0, 8, s));
     CLD_CUDA(cudaMemsetAsync(scal.get() + 6, 0xFF, 4, s));
     CLD_CUDA(cudaMemsetAsync(scal.get() + 7, 0, 4, s));
-    if (flags & CLDIAM_CSR_LCC) {
+    if (lcc) {
         DBuf<uint32_t> parent, size, keep, newid;
         DBuf<unsigned long long> best;
         CLD_TRY(parent.alloc(n, s));
         CLD_TRY(best.alloc(1, s));
         CLD_K(K_MISC, s, k_iota<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
         CLD_LAUNCH_CHECK();
+        const CsrAdj ca{off.get(), adj.get()};
         // Afforest-style: link two neighbours per node, find the dominant tree by sampling,
         // then link the remaining edges of the nodes outside it (all no-ops on a graph without edges)
         constexpr uint32_t kNeighbourRounds = 2;
         for (uint32_t r = 0; r < kNeighbourRounds; ++r) {
-            CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, r, parent.get()));
+            if (packed) CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(la, n, r, parent.get()));
+            else CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(ca, n, r, parent.get()));
             CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
         }
         CLD_LAUNCH_CHECK();
@@ -521,7 +636,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CLD_CUDA(cudaMemcpyAsync(hbad + 8, scal.get() + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CLD_CUDA(cudaStreamSynchronize(s));
-        // a failed sort or assembly leaves the CSR unusable: stop before anything indexes by its entries
+        // a failed sort leaves the graph unusable: stop before anything indexes by its entries
         if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired or CSR assembly inconsistent");
         nnz = hbad[1];
         if (nnz > 0) {
@@ -533,8 +648,12 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                 if (j - i > best_run) { best_run = (uint32_t)(j - i); giant = hs[i]; }
                 i = j;
             }
-            CLD_K(K_CC, s, k_cc_link_rest<<<grid_for(n, 256), 256, 0, s>>>(off.get(), adj.get(), n, kNeighbourRounds,
-                                                                            giant, parent.get()));
+            if (packed)
+                CLD_K(K_CC, s, k_cc_link_rest<<<grid_for(n, 256), 256, 0, s>>>(la, n, kNeighbourRounds, giant,
+                                                                                parent.get()));
+            else
+                CLD_K(K_CC, s, k_cc_link_rest<<<grid_for(n, 256), 256, 0, s>>>(ca, n, kNeighbourRounds, giant,
+                                                                                parent.get()));
             CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
             CLD_LAUNCH_CHECK();
             CLD_CUDA(cudaMemsetAsync(scal.get() + 3, 0, 4, s));
@@ -561,7 +680,12 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         // nnz, and the kernels read the counts from scal[4] / scal[5]
         CLD_TRY(orig.alloc(n, s));
         CLD_CUDA(cudaMemsetAsync(deg.get(), 0, ((size_t)n + 1) * 4, s));
-        CLD_K(K_CSR, s, k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), off.get(), n, deg.get(), orig.get()));
+        if (packed)
+            CLD_K(K_CSR, s, k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), la, n, deg.get(),
+                                                                          orig.get()));
+        else
+            CLD_K(K_CSR, s, k_lcc_degrees<<<grid_for(n, 256), 256, 0, s>>>(keep.get(), newid.get(), ca, n, deg.get(),
+                                                                          orig.get()));
         CLD_LAUNCH_CHECK();
         CLD_TRY(scan_exclusive_u32(deg.get(), degx.get(), n, scal.get() + 5, s));  // zeros past the kept nodes
         DBuf<uint64_t> noff;
@@ -570,18 +694,33 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(noff.alloc((size_t)n + 1, s));
         CLD_TRY(nadj.alloc(nnz ? nnz : 1, s));
         CLD_TRY(nrow.alloc(nnz ? nnz : 1, s));
-        DBuf<uint2> map;
-        CLD_TRY(map.alloc(n, s));
-        CLD_CUDA(cudaMemsetAsync(map.get(), 0xFF, (size_t)n * 8, s));
-        CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, scal.get() + 4,
-                                                                                scal.get() + 5, orig.get(), off.get(),
-                                                                                noff.get(), map.get()));
-        CLD_LAUNCH_CHECK();
-        if (nnz) {
-            CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(map.get(), newid.get(), row.get(), adj.get(),
-                                                                         nnz, nrow.get(), nadj.get(), wsum.get(),
-                                                                         scal.get() + 6));
+        if (packed) {
+            // the LCC's CSR straight from the lists: the whole graph's CSR is never built
+            CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, scal.get() + 4,
+                                                                                    scal.get() + 5, orig.get(),
+                                                                                    nullptr, noff.get(), nullptr));
             CLD_LAUNCH_CHECK();
+            if (mu > 0) {
+                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, keep.get(), newid.get(),
+                                                                                noff.get(), nrow.get(), nadj.get(),
+                                                                                wsum.get(), scal.get() + 6,
+                                                                                scal.get() + 8));
+                CLD_LAUNCH_CHECK();
+            }
+        } else {
+            DBuf<uint2> map;
+            CLD_TRY(map.alloc(n, s));
+            CLD_CUDA(cudaMemsetAsync(map.get(), 0xFF, (size_t)n * 8, s));
+            CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, scal.get() + 4,
+                                                                                    scal.get() + 5, orig.get(),
+                                                                                    off.get(), noff.get(), map.get()));
+            CLD_LAUNCH_CHECK();
+            if (nnz) {
+                CLD_K(K_CSR, s, k_lcc_copy<<<grid_for(nnz, 256), 256, 0, s>>>(map.get(), newid.get(), row.get(),
+                                                                             adj.get(), nnz, nrow.get(), nadj.get(),
+                                                                             wsum.get(), scal.get() + 6));
+                CLD_LAUNCH_CHECK();
+            }
         }
         g->off = noff.detach();
         g->adj = nadj.detach();
@@ -607,13 +746,13 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_LAUNCH_CHECK();
     }
     g->orig = orig.detach();
-    g->connected = (flags & CLDIAM_CSR_LCC) != 0;
+    g->connected = lcc;
     uint64_t* hsum = reinterpret_cast<uint64_t*>(static_cast<char*>(g->host.h) + 64);
     CLD_CUDA(cudaMemcpyAsync(hsum, wsum.get(), 8, cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, 8 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
     if (hbad[8]) return fail(CLDIAM_ERR_TIMEOUT, "radix sort look-back wait expired or CSR assembly inconsistent");
-    if (flags & CLDIAM_CSR_LCC) {
+    if (lcc) {
         g->n = hbad[4];
         g->nnz = hbad[5];
     } else {
