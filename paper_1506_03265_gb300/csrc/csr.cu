@@ -348,12 +348,28 @@ __global__ void __launch_bounds__(256) k_lcc_copy(const uint2* __restrict__ map,
     if (threadIdx.x == 0 && mn != 0xFFFFFFFFu) atomicMin(wmin, mn);
 }
 
-// The LCC's CSR straight from the two orders of the distinct edges: an edge (a, b) of a kept component
+// New offsets of the LCC from the scan of its degrees, and per kept node u = orig[i] one word of four:
+// (i, the position shift of u's upper entries from their index in U, the shift of its lower entries from
+// their index in T, 0), positions and shifts taken modulo 2^32 (positions are < 2^32); dropped nodes keep
+// the all-ones pre-fill
+__global__ void k_lcc_offsets_lists(const uint32_t* __restrict__ excl, const uint32_t* __restrict__ n_out_dev,
+                                    const uint32_t* __restrict__ total_dev, const uint32_t* __restrict__ orig, ListAdj g,
+                                    uint64_t* __restrict__ noff, uint4* __restrict__ info) {
+    const uint32_t n_out = *n_out_dev, total = *total_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n_out; i += gridDim.x * blockDim.x) {
+        noff[i] = (i == n_out) ? (uint64_t)total : (uint64_t)excl[i];
+        if (i < n_out) {
+            const uint32_t u = orig[i];
+            info[u] = make_uint4(i, excl[i] + g.lo(u) - g.ustart[u], excl[i] - g.tstart[u], 0u);
+        }
+    }
+}
+
+// The LCC's CSR straight from the two orders of the distinct edges: an edge (a, b) of the kept component
 // goes to row newid[a] after its lower entries (from U) and to row newid[b] (from T); new ids are
 // monotone, so rows stay sorted.  Weight statistics as k_lcc_copy (each undirected edge once: from U).
-// A position outside its row's part is recorded in *err and the write skipped.
-__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint32_t* __restrict__ keep,
-                               const uint32_t* __restrict__ newid, const uint64_t* __restrict__ noff,
+// A position past the output (inconsistent input) is recorded in *err and the write skipped.
+__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info, uint64_t cap,
                                uint32_t* __restrict__ nrow, uint2* __restrict__ nadj,
                                unsigned long long* __restrict__ wsum, uint32_t* __restrict__ wmin,
                                uint32_t* __restrict__ err) {
@@ -363,12 +379,12 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint32_t* __restric
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
         const uint64_t u = g.U[i], t = g.T[i];
         const uint32_t a = (uint32_t)(u >> g.ash), b = (uint32_t)(u >> g.wb) & g.cmask, w = (uint32_t)u & wmask;
-        if (keep[a]) {
-            const uint32_t na = newid[a];
-            const uint64_t pos = noff[na] + g.lo(a) + (i - g.ustart[a]);
-            if (i >= g.ustart[a] && i < g.uend[a] && pos < noff[na + 1]) {
-                nadj[pos] = make_uint2(newid[b], w);
-                nrow[pos] = na;
+        const uint4 ia = info[a];
+        if (ia.x != 0xFFFFFFFFu) {  // kept (then b is kept too)
+            const uint32_t pos = ia.y + i;
+            if (pos < cap) {
+                nadj[pos] = make_uint2(info[b].x, w);
+                nrow[pos] = ia.x;
             } else {
                 atomicExch(err, 1u);
             }
@@ -376,12 +392,12 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint32_t* __restric
             mn = w < mn ? w : mn;
         }
         const uint32_t ta = (uint32_t)(t >> g.ash), tb = (uint32_t)(t >> g.wb) & g.cmask;
-        if (keep[tb]) {
-            const uint32_t nb = newid[tb];
-            const uint64_t pos = noff[nb] + (i - g.tstart[tb]);
-            if (i >= g.tstart[tb] && i < g.tend[tb]) {
-                nadj[pos] = make_uint2(newid[ta], (uint32_t)t & wmask);
-                nrow[pos] = nb;
+        const uint4 ib = info[tb];
+        if (ib.x != 0xFFFFFFFFu) {
+            const uint32_t pos = ib.z + i;
+            if (pos < cap) {
+                nadj[pos] = make_uint2(info[ta].x, (uint32_t)t & wmask);
+                nrow[pos] = ib.x;
             } else {
                 atomicExch(err, 1u);
             }
@@ -696,15 +712,16 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_TRY(nrow.alloc(nnz ? nnz : 1, s));
         if (packed) {
             // the LCC's CSR straight from the lists: the whole graph's CSR is never built
-            CLD_K(K_CSR, s, k_lcc_offsets<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(degx.get(), n, scal.get() + 4,
-                                                                                    scal.get() + 5, orig.get(),
-                                                                                    nullptr, noff.get(), nullptr));
+            DBuf<uint4> info;
+            CLD_TRY(info.alloc(n, s));
+            CLD_CUDA(cudaMemsetAsync(info.get(), 0xFF, (size_t)n * 16, s));
+            CLD_K(K_CSR, s, k_lcc_offsets_lists<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(
+                                degx.get(), scal.get() + 4, scal.get() + 5, orig.get(), la, noff.get(), info.get()));
             CLD_LAUNCH_CHECK();
             if (mu > 0) {
-                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, keep.get(), newid.get(),
-                                                                                noff.get(), nrow.get(), nadj.get(),
-                                                                                wsum.get(), scal.get() + 6,
-                                                                                scal.get() + 8));
+                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, info.get(), nnz ? nnz : 1,
+                                                                                nrow.get(), nadj.get(), wsum.get(),
+                                                                                scal.get() + 6, scal.get() + 8));
                 CLD_LAUNCH_CHECK();
             }
         } else {
