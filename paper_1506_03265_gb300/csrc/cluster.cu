@@ -79,12 +79,19 @@ __global__ void k_assign_cid(uint32_t n, const uint32_t* __restrict__ center, co
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) cid[v] = rank[center[v]];
 }
 
-__global__ void k_fill_u32(uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = x;
+// node state before the first stage: no center, D = R = 0, no stamp, no key
+__global__ void k_cluster_init(uint32_t n, uint32_t* __restrict__ center, uint32_t* __restrict__ D,
+                               uint32_t* __restrict__ R, uint32_t* __restrict__ stamp,
+                               unsigned long long* __restrict__ key) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        center[i] = kNone;
+        D[i] = 0;
+        R[i] = 0;
+        stamp[i] = 0;
+        key[i] = kInfKey;
+    }
 }
-__global__ void k_fill_u64(unsigned long long* __restrict__ a, uint32_t n, unsigned long long x) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = x;
-}
+
 
 struct ClusterOwner {
     cldiam_clustering* c;
@@ -178,11 +185,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     static_assert(sizeof(Counters) <= 128, "counter block must fit the pinned area");
 
     const unsigned gb = grid_for(n, 256);
-    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(center.get(), n, kNone));
-    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(D.get(), n, 0u));
-    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(R.get(), n, 0u));
-    CLD_K(K_MISC, s, k_fill_u32<<<gb, 256, 0, s>>>(stamp.get(), n, 0u));
-    CLD_K(K_MISC, s, k_fill_u64<<<gb, 256, 0, s>>>(key.get(), n, kInfKey));
+    CLD_K(K_MISC, s, k_cluster_init<<<gb, 256, 0, s>>>(n, center.get(), D.get(), R.get(), stamp.get(), key.get()));
     CLD_LAUNCH_CHECK();
     CLD_CUDA(cudaMemsetAsync(ctr.get(), 0, sizeof(Counters), s));
 
