@@ -178,16 +178,15 @@ struct ListAdj {
     }
 };
 
-// first pass: link every node with its first `rounds` neighbours (ids >= n, which a consistent graph never
-// holds, are skipped rather than followed)
+// first passes: link every node with its r-th neighbour (ids >= n, which a consistent graph never holds,
+// are skipped rather than followed).  One launch per r with pointer jumping in between: linking several
+// neighbours in one pass builds long parent chains on meshes, which every later link then walks.
 template <class A>
-__global__ void k_cc_link_first(A g, uint32_t n, uint32_t rounds, uint32_t* __restrict__ parent) {
+__global__ void k_cc_link_nth(A g, uint32_t n, uint32_t r, uint32_t* __restrict__ parent) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint32_t d = min(rounds, g.deg(v));
-        for (uint32_t r = 0; r < d; ++r) {
-            const uint32_t c = g.nbr(v, r);
-            if (c < n) cc_link(v, c, parent);
-        }
+        if (r >= g.deg(v)) continue;
+        const uint32_t c = g.nbr(v, r);
+        if (c < n) cc_link(v, c, parent);
     }
 }
 
@@ -638,9 +637,11 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         // Afforest-style: link two neighbours per node, find the dominant tree by sampling,
         // then link the remaining edges of the nodes outside it (all no-ops on a graph without edges)
         constexpr uint32_t kNeighbourRounds = 2;
-        if (packed) CLD_K(K_CC, s, k_cc_link_first<<<grid_for(n, 256), 256, 0, s>>>(la, n, kNeighbourRounds, parent.get()));
-        else CLD_K(K_CC, s, k_cc_link_first<<<grid_for(n, 256), 256, 0, s>>>(ca, n, kNeighbourRounds, parent.get()));
-        CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
+        for (uint32_t r = 0; r < kNeighbourRounds; ++r) {
+            if (packed) CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(la, n, r, parent.get()));
+            else CLD_K(K_CC, s, k_cc_link_nth<<<grid_for(n, 256), 256, 0, s>>>(ca, n, r, parent.get()));
+            CLD_K(K_CC, s, k_cc_compress<<<grid_for(n, 256), 256, 0, s>>>(parent.get(), n));
+        }
         CLD_LAUNCH_CHECK();
         constexpr uint32_t kSamples = 1024;
         DBuf<uint32_t> samp;
