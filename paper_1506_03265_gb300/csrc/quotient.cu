@@ -80,7 +80,9 @@ __global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __
             s = 0xFFFFFFFEull;
         }
         uint32_t* m = &M[(size_t)min(a, b) * k + max(a, b)];
-        if ((uint32_t)s < __ldcg(m)) atomicMin(m, (uint32_t)s);
+        // entries only decrease, so a stale copy in this SM's L1 is never below the current value: reading
+        // through L1 can let a useless atomicMin through but never hold back one that lowers the entry
+        if ((uint32_t)s < __ldca(m)) atomicMin(m, (uint32_t)s);
     }
     if (__any_sync(0xffffffffu, ovf) && lane_id() == 0) atomicExch(overflow, 1u);
 }
