@@ -1,5 +1,5 @@
 // Device-wide primitives: prefix sums, reductions and a stable LSD radix sort
-// (8-bit digits, warp match-based ranking).  These realise the sorting and
+// (8-bit digits, warp-level ranking from bit ballots).  These realise the sorting and
 // (segmented) prefix-sum building blocks that the paper's MR implementation
 // relies on (Fact 1, Section 2), here within one GPU.
 #include <cstdio>
@@ -266,7 +266,7 @@ cldiam_status reduce_sum_u32_to_u64(const uint32_t* in, size_t n, uint64_t* out,
 // ------------------------------------------------------------------ radix sort
 // Onesweep-style LSD radix sort (8-bit digits).  One read of the keys builds
 // the digit histograms of every pass; each pass is then a single kernel in
-// which tile t ranks its items (warp match-based, stable), publishes its
+// which tile t ranks its items (warp-level, stable), publishes its
 // per-digit counts, and obtains the counts of all earlier tiles by decoupled
 // look-back over a per-(tile, digit) status word, so no per-pass histogram
 // read or separate scan is needed.  Items are staged in shared memory in

@@ -233,7 +233,7 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
     K* sk = alt ? keys2.get() : keys.get();
     uint32_t* sv = alt ? vals2.get() : vals.get();
 
-    // unique cluster pairs with their lightest weight, in one look-back pass
+    // unique cluster pairs with their lightest weight (run heads, scan, write)
     DBuf<uint32_t> col, w;
     DBuf<uint64_t> off;
     CLD_TRY(col.alloc(cnt ? cnt : 1, s));
