@@ -20,7 +20,7 @@ def declared():
 
 def test_header_declares_the_boundary():
     names = declared()
-    for must in ["cldiam_build_csr", "cldiam_cluster", "cldiam_quotient_build", "cldiam_estimate",
+    for must in ["cldiam_build_csr", "cldiam_cluster", "cldiam_cluster2", "cldiam_quotient_build", "cldiam_estimate",
                  "cldiam_sssp_delta", "cldiam_apsp_max"]:
         assert must in names
 
