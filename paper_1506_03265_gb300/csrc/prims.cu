@@ -351,6 +351,65 @@ __device__ __forceinline__ uint32_t os_digit(K k, uint32_t sh, uint32_t dm) {
     }
 }
 
+// Narrows peers to the lanes whose digit bits B..7 equal this lane's.  plo holds digit bits 0..3 at the
+// top bit of its bytes 0..3 (bit j at bit 8j + 7), phi bits 4..7 likewise, so a byte permute of the pair
+// {phi, plo} whose selector nibbles are 8 + b (sign-replicate mode, source byte b) spreads digit bit b over
+// the whole word m; the ballot of m != 0 is the lanes with bit b set, and m picks it or its complement.
+template <int B>
+__device__ __forceinline__ unsigned os_peers(uint32_t plo, uint32_t phi, unsigned peers) {
+    uint32_t m;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(m) : "r"(plo), "r"(phi), "n"(0x1111 * (8 + B)));
+    const unsigned bb = __ballot_sync(0xffffffffu, m != 0u);
+    peers &= ~(bb ^ m);
+    if constexpr (B < 7) return os_peers<B + 1>(plo, phi, peers);
+    else return peers;
+}
+
+// Loads one tile's items, every load issued before ranking so they are in flight together, and ranks them.
+// FULL: every thread holds all OS_ITEMS items, so the per-item bounds tests go (and with them the spills
+// that the generic form needs at 64 registers).  Stable warp-local ranks: peers with the same digit,
+// counted in item order then lane order; the peer mask is the AND of one ballot per digit bit (a fixed
+// cost; a match instruction costs more the more distinct digits a warp holds, which is most of them for
+// these keys); every peer reads the running count (one broadcast word) and writes back the same new count
+// (in the last tile only the highest valid peer does).
+template <class K, bool KV, bool HI, int OS_ITEMS, bool FULL>
+__device__ __forceinline__ void os_load_rank(const K* __restrict__ kt, const uint32_t* __restrict__ vt, uint32_t rem,
+                                             uint32_t lbase, unsigned l, unsigned ltmask, uint32_t sh, uint32_t dm,
+                                             uint32_t* __restrict__ wh, K (&key)[OS_ITEMS],
+                                             uint32_t (&val)[KV ? OS_ITEMS : 1],
+                                             uint32_t (&rank_pk)[(OS_ITEMS + 1) / 2]) {
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const uint32_t li = lbase + (uint32_t)i * 32;
+        if constexpr (FULL) {
+            key[i] = kt[li];
+            if constexpr (KV) val[i] = vt[li];
+        } else {
+            key[i] = li < rem ? kt[li] : (K)0;
+            if constexpr (KV) val[i] = li < rem ? vt[li] : 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; ++i) {
+        const bool valid = FULL || lbase + (uint32_t)i * 32 < rem;
+        const uint32_t d = os_digit<K, HI>(key[i], sh, dm);
+        unsigned peers = 0xFFFFFFFFu;
+        if constexpr (!FULL) {  // the last tile: items past the end form their own group
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            peers = valid ? vb : ~vb;
+        }
+        peers = os_peers<0>((d & 0xFu) * 0x10204080u, (d & 0xF0u) * 0x01020408u, peers);
+        const uint32_t cur = wh[d];
+        __syncwarp();
+        if constexpr (FULL) wh[d] = cur + (uint32_t)__popc(peers);  // every peer stores the same value
+        else if (valid && (peers >> l) == 1u) wh[d] = cur + (uint32_t)__popc(peers);
+        const uint32_t rk = valid ? cur + (uint32_t)__popc(peers & ltmask) : 0xFFFFu;
+        if (i % 2 == 0) rank_pk[i / 2] = rk;
+        else rank_pk[i / 2] |= rk << 16;
+        __syncwarp();
+    }
+}
+
 // KV: items carry a 32-bit value (vin/vout); otherwise keys only.  sh = shift mod 32 (HI: shift >= 32).
 template <class K, bool KV, bool HI, int OS_ITEMS = OsCfg<K, KV>::ITEMS, int OS_TILE = OsCfg<K, KV>::TILE>
 __global__ void __launch_bounds__(OS_THREADS, 4)
@@ -380,44 +439,12 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
 
     K key[OS_ITEMS];
     uint32_t val[KV ? OS_ITEMS : 1];
-    uint32_t dig_pk[(OS_ITEMS + 3) / 4];   // digits, four per word
     uint32_t rank_pk[(OS_ITEMS + 1) / 2];  // warp-local ranks (< 32 * OS_ITEMS) as 16-bit halves; 0xFFFF = no item
-    // issue every load of the tile before ranking, so they are in flight together
-#pragma unroll
-    for (int i = 0; i < OS_ITEMS; ++i) {
-        const uint32_t li = lbase + (uint32_t)i * 32;
-        key[i] = li < rem ? kt[li] : (K)0;
-        if constexpr (KV) val[i] = li < rem ? vt[li] : 0u;
-    }
-    // stable warp-local ranks: peers with the same digit, counted in item order then lane order; the peer
-    // mask is the AND of one ballot per digit bit (a fixed cost; a match instruction costs more the more
-    // distinct digits a warp holds, which is most of them for these keys); every peer reads the running
-    // count (one broadcast word), the highest peer writes it back
-    const bool full = rem == (uint32_t)OS_TILE;
-#pragma unroll
-    for (int i = 0; i < OS_ITEMS; ++i) {
-        const bool valid = lbase + (uint32_t)i * 32 < rem;
-        const uint32_t d = os_digit<K, HI>(key[i], sh, dm);
-        unsigned peers = 0xFFFFFFFFu;
-        if (!full) {  // the last tile: items past the end form their own group
-            const unsigned vb = __ballot_sync(0xffffffffu, valid);
-            peers = valid ? vb : ~vb;
-        }
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bb : ~bb;
-        }
-        const uint32_t cur = whist[w][d];
-        __syncwarp();
-        if (valid && (peers >> l) == 1u) whist[w][d] = cur + (uint32_t)__popc(peers);
-        const uint32_t rk = valid ? cur + (uint32_t)__popc(peers & ltmask) : 0xFFFFu;
-        if (i % 2 == 0) rank_pk[i / 2] = rk;
-        else rank_pk[i / 2] |= rk << 16;
-        if (i % 4 == 0) dig_pk[i / 4] = d;
-        else dig_pk[i / 4] |= d << (8 * (i % 4));
-        __syncwarp();
-    }
+    // full tiles (all but the last) take the form without bounds tests
+    if (rem == (uint32_t)OS_TILE)
+        os_load_rank<K, KV, HI, OS_ITEMS, true>(kt, vt, rem, lbase, l, ltmask, sh, dm, whist[w], key, val, rank_pk);
+    else
+        os_load_rank<K, KV, HI, OS_ITEMS, false>(kt, vt, rem, lbase, l, ltmask, sh, dm, whist[w], key, val, rank_pk);
     __syncthreads();
 
     // per digit (thread d): tile count, publication, tile-local scan, look-back
@@ -448,12 +475,13 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
         }
     }
     __syncthreads();
-    // stage in digit order (tile positions suffice); the keys are dead before the look-back
+    // stage in digit order (tile positions suffice; digits recomputed from the keys); the keys are dead
+    // before the look-back
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; ++i) {
         const uint32_t rk = (rank_pk[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-        if (rk != 0xFFFFu) {
-            const uint32_t dd = (dig_pk[i / 4] >> (8 * (i % 4))) & 0xFFu;
+        if (rem == (uint32_t)OS_TILE || rk != 0xFFFFu) {
+            const uint32_t dd = os_digit<K, HI>(key[i], sh, dm);
             const uint32_t pos = whist[w][dd] + rk;
             s_key[pos] = key[i];
             if constexpr (KV) s_val[pos] = val[i];
