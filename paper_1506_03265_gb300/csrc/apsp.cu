@@ -491,10 +491,13 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
         if (bad) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
     }
     // sparse quotient (fewer than k^2 / 8 entries): batched SSSP, S sources per CTA with
-    // k x S distances (and one word of change bits per node) in shared memory, S = 8 while it fits
+    // k x S distances (and one word of change bits per node) in shared memory.  S = 8 below 2,048
+    // nodes; above, S = 4: its half-size distance block lets two 1,024-thread CTAs share an SM (they
+    // use <= 32 registers), where S = 8 fits one (R-MAT 24, k = 4,069: 3.0 -> 2.1 ms; road mesh 4096^2,
+    // k = 4,357: 4.0 -> 3.4 ms)
     constexpr size_t kSmem = 220 * 1024;
     const bool sparse = (double)nnz * 8.0 < (double)k * k;
-    if (sparse && (size_t)k * (8 * 4 + 8) <= kSmem) {
+    if (sparse && (size_t)k * (8 * 4 + 8) <= kSmem && k < 2048) {
         CLD_TRY(launch_wl<8>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
     } else if (sparse && (size_t)k * (4 * 4 + 8) <= kSmem) {
         CLD_TRY(launch_wl<4>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));

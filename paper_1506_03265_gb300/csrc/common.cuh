@@ -252,10 +252,13 @@ cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* key
 // Stable LSD radix sort of 64-bit keys alone on key bits [shift0, shift0 + bits).  With err_dev the
 // call does not synchronise: a look-back wait that expired sets *err_dev (device word) instead of
 // returning TIMEOUT, for the caller to read with its next result.  With first_in the n input keys are
-// read from there (never written) and keys / keys_alt serve only as the ping-pong buffers.
+// read from there (never written) and keys / keys_alt serve only as the ping-pong buffers.  With hist_in
+// the digit counts of every pass (ceil(bits / 8) x 256 words, in pass order, digits as the sort takes
+// them) were accumulated by the producer of the keys: the sort scans them in place instead of reading
+// the keys once more to count.
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits,
                                   bool* result_in_alt, cudaStream_t s, uint32_t* err_dev = nullptr,
-                                  const uint64_t* first_in = nullptr);
+                                  const uint64_t* first_in = nullptr, uint32_t* hist_in = nullptr);
 
 // Unique keys of a sorted sequence with the minimum value of each run:
 // row_out[r] = key / div (row_out may be null), col_out[r*cs] = key % div,

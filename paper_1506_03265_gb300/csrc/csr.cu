@@ -45,9 +45,19 @@ __global__ void k_emit_directed(const uint32_t* __restrict__ src, const uint32_t
 // one item per edge, (min(u,v) << vb | max(u,v)) << wb | w, a self-loop as ~0 (dropped, sorts last); also
 // the input check (ids < n, weights >= 1 -> *bad) and whether a weight needs more than wb bits (*wide: the
 // caller falls back to (key, weight) pairs)
+// The same pass counts the digits of every pass of the sort that follows (8-bit digits of the item's
+// 2 vb (a, b) bits, the last one masked to the bits left) into per-warp shared histograms
+// (warps x npass x 256 words of dynamic shared memory), flushed into hist (npass x 256) at the end: the
+// sort then needs no read of its own to count them.
 __global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                              const uint32_t* __restrict__ w, uint64_t m, uint32_t n, int vb, int wb,
-                             uint64_t* __restrict__ items, uint32_t* __restrict__ bad, uint32_t* __restrict__ wide) {
+                             uint64_t* __restrict__ items, uint32_t* __restrict__ bad, uint32_t* __restrict__ wide,
+                             uint32_t* __restrict__ hist) {
+    extern __shared__ uint32_t eh[];
+    const int npass = (2 * vb + 7) / 8;
+    for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * npass * 256; i += blockDim.x) eh[i] = 0;
+    __syncthreads();
+    uint32_t* h = eh + (threadIdx.x >> 5) * npass * 256;
     bool b = false, wd = false;
     const uint64_t wlim = wb >= 32 ? ~0ull : (1ull << wb);
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
@@ -55,10 +65,22 @@ __global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* _
         b |= u >= n || v >= n || ww == 0;
         wd |= ww >= wlim;
         const uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
-        items[e] = u != v ? (((lo << vb) | hi) << wb) | ww : ~0ull;
+        const uint64_t it = u != v ? (((lo << vb) | hi) << wb) | ww : ~0ull;
+        items[e] = it;
+        for (int p = 0; p < npass; ++p) {
+            const int left = 2 * vb - 8 * p;
+            const uint32_t dm = left >= 8 ? 0xFFu : ((1u << left) - 1u);
+            atomicAdd(&h[p * 256 + ((uint32_t)(it >> (wb + 8 * p)) & dm)], 1u);
+        }
     }
     if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
     if (__any_sync(0xffffffffu, wd) && lane_id() == 0) atomicExch(wide, 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) c += eh[ww * npass * 256 + i];
+        if (c) atomicAdd(&hist[i], c);
+    }
 }
 
 // Distinct edges in two orders: U by (a, b) and T by (b, a) (a < b).  Row x of the symmetric CSR is its
@@ -525,6 +547,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     bool packed = wb >= 1;
     // packed path: the distinct edges in two orders and their run bounds (the adjacency in list form)
     DBuf<uint64_t> items, items2, uniq;
+    DBuf<uint32_t> hist1;  // digit counts of the first sort, accumulated by the emission
     DBuf<uint32_t> runs;
     ListAdj la{};
     uint32_t mu = 0;
@@ -532,10 +555,21 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         // one item per edge, sorted on (a, b) and de-duplicated (U); the same distinct edges sorted on b alone
         // (stable, so by (b, a): T) give every row's entries below the diagonal
         CLD_TRY(items.alloc(m ? m : 1, s));
+        const int npass1 = (2 * vb + 7) / 8;
+        CLD_TRY(hist1.alloc((size_t)npass1 * 256, s));
+        CLD_CUDA(cudaMemsetAsync(hist1.get(), 0, (size_t)npass1 * 256 * 4, s));
         if (m > 0) {
-            CLD_K(K_CSR, s, k_emit_canon<<<grid_for(m, 256), 256, 0, s>>>((const uint32_t*)dsrc, (const uint32_t*)ddst,
-                                                                         (const uint32_t*)dw, m, n, vb, wb, items.get(),
-                                                                         scal.get(), scal.get() + 2));
+            const size_t esm = (size_t)8 * npass1 * 256 * 4;  // 8 warps; <= 64 KB
+            static bool emit_attr[64];
+            int dev = 0;
+            CLD_CUDA(cudaGetDevice(&dev));
+            if (dev < 0 || dev >= 64 || !emit_attr[dev]) {
+                CLD_CUDA(cudaFuncSetAttribute(k_emit_canon, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+                if (dev >= 0 && dev < 64) emit_attr[dev] = true;
+            }
+            CLD_K(K_CSR, s, k_emit_canon<<<grid_for(m, 256, 4), 256, esm, s>>>(
+                                (const uint32_t*)dsrc, (const uint32_t*)ddst, (const uint32_t*)dw, m, n, vb, wb, items.get(),
+                                scal.get(), scal.get() + 2, hist1.get()));
             CLD_LAUNCH_CHECK();
         }
         CLD_CUDA(cudaMemcpyAsync(hbad, scal.get(), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -546,7 +580,8 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             CLD_TRY(items2.alloc(m ? m : 1, s));
             CLD_TRY(uniq.alloc(m ? m : 1, s));
             bool alt = false;
-            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), m, wb, 2 * vb, &alt, s, scal.get() + 8));
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), m, wb, 2 * vb, &alt, s, scal.get() + 8, nullptr,
+                                        hist1.get()));
             CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s));
             CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CLD_CUDA(cudaStreamSynchronize(s));

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4)
 template <class K>
 static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, size_t n, int shift0,
                                      int bits, bool* in_alt, cudaStream_t s, uint32_t* err_dev = nullptr,
-                                     const K* first_in = nullptr) {
+                                     const K* first_in = nullptr, uint32_t* hist_in = nullptr) {
     *in_alt = false;
     if (n <= 1 || bits <= 0) {
         if (first_in && n) CLD_CUDA(cudaMemcpyAsync(keys, first_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
@@ -572,23 +572,28 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         }
         if (dev >= 0 && dev < 64) attr_set[kv][dev] = true;
     }
-    DBuf<uint32_t> hist, ctl;
+    DBuf<uint32_t> hist_own, ctl;
     DBuf<unsigned long long> status;
-    CLD_TRY(hist.alloc((size_t)npass * OS_RADIX, s));
     CLD_TRY(ctl.alloc(2 * npass + 2, s));
     CLD_TRY(status.alloc((size_t)ntiles * OS_RADIX, s));
-    CLD_CUDA(cudaMemsetAsync(hist.get(), 0, (size_t)npass * OS_RADIX * 4, s));
     CLD_CUDA(cudaMemsetAsync(ctl.get(), 0, (2 * npass + 2) * 4, s));
-    const size_t hsm = (size_t)OS_WARPS * npass * OS_RADIX * 4;  // <= 64 KB (at most 8 passes)
-    if (dev < 0 || dev >= 64 || !hist_attr_set[dev]) {
-        CLD_CUDA(cudaFuncSetAttribute(k_os_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * OS_WARPS * OS_RADIX * 4));
-        if (dev >= 0 && dev < 64) hist_attr_set[dev] = true;
+    uint32_t* hist = hist_in;
+    if (!hist) {
+        CLD_TRY(hist_own.alloc((size_t)npass * OS_RADIX, s));
+        hist = hist_own.get();
+        CLD_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * OS_RADIX * 4, s));
+        const size_t hsm = (size_t)OS_WARPS * npass * OS_RADIX * 4;  // <= 64 KB (at most 8 passes)
+        if (dev < 0 || dev >= 64 || !hist_attr_set[dev]) {
+            CLD_CUDA(cudaFuncSetAttribute(k_os_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          8 * OS_WARPS * OS_RADIX * 4));
+            if (dev >= 0 && dev < 64) hist_attr_set[dev] = true;
+        }
+        CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, hsm, s>>>(first_in ? first_in : keys, n, npass,
+                                                                                  shift0, bits, hist));
+        prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
     }
-    CLD_K(K_RADIX_HIST, s, k_os_hist<K><<<grid_for(n, 256, 4), 256, hsm, s>>>(first_in ? first_in : keys, n, npass, shift0, bits,
-                                                                              hist.get()));
-    CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist.get(), npass));
+    CLD_K(K_RADIX_HIST, s, k_os_hist_scan<<<1, OS_RADIX, 0, s>>>(hist, npass));
     CLD_LAUNCH_CHECK();
-    prof_add_bytes(K_RADIX_HIST, (double)n * sizeof(K));
     // first_in (keys only): the first pass reads it and writes keys_alt, so first_in is never written
     const K* ki = first_in ? first_in : keys;
     uint32_t* vi = vals;
@@ -601,7 +606,7 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
         const bool hi = sizeof(K) == 8 && shift >= 32;
         const uint32_t sh = (uint32_t)shift & 31u;
         const uint32_t dm = bits - 8 * p >= 8 ? 0xFFu : ((1u << (bits - 8 * p)) - 1u);  // key bits only
-        const uint32_t* go = hist.get() + p * OS_RADIX;
+        const uint32_t* go = hist + p * OS_RADIX;
         uint32_t* tc = ctl.get() + p;
         uint32_t* er = err_dev ? err_dev : ctl.get() + 2 * npass;
         if (kv && hi) {
@@ -979,8 +984,9 @@ cldiam_status radix_sort_pairs_u64(uint64_t* keys, uint32_t* vals, uint64_t* key
     return radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, 0, bits, in_alt, s);
 }
 cldiam_status radix_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int shift0, int bits, bool* in_alt,
-                                  cudaStream_t s, uint32_t* err_dev, const uint64_t* first_in) {
-    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s, err_dev, first_in);
+                                  cudaStream_t s, uint32_t* err_dev, const uint64_t* first_in, uint32_t* hist_in) {
+    return radix_sort_impl<uint64_t>(keys, nullptr, keys_alt, nullptr, n, shift0, bits, in_alt, s, err_dev, first_in,
+                                     hist_in);
 }
 cldiam_status radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                    size_t n, int bits, bool* in_alt, cudaStream_t s) {
