@@ -60,17 +60,34 @@ __global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* _
     uint32_t* h = eh + (threadIdx.x >> 5) * npass * 256;
     bool b = false, wd = false;
     const uint64_t wlim = wb >= 32 ? ~0ull : (1ull << wb);
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t u = src[e], v = dst[e], ww = w[e];
-        b |= u >= n || v >= n || ww == 0;
-        wd |= ww >= wlim;
-        const uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
-        const uint64_t it = u != v ? (((lo << vb) | hi) << wb) | ww : ~0ull;
-        items[e] = it;
-        for (int p = 0; p < npass; ++p) {
-            const int left = 2 * vb - 8 * p;
-            const uint32_t dm = left >= 8 ? 0xFFu : ((1u << left) - 1u);
-            atomicAdd(&h[p * 256 + ((uint32_t)(it >> (wb + 8 * p)) & dm)], 1u);
+    // EU edges per thread and iteration, their loads issued before the counting (which would otherwise
+    // hold back the next loads: fewer CTAs fit per SM with the histograms)
+    constexpr int EU = 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < m; base += stride * EU) {
+        uint32_t su[EU], sv[EU], sw[EU];
+#pragma unroll
+        for (int k = 0; k < EU; ++k) {
+            const uint64_t e = base + k * stride;
+            su[k] = e < m ? src[e] : 0u;
+            sv[k] = e < m ? dst[e] : 0u;
+            sw[k] = e < m ? w[e] : 1u;
+        }
+#pragma unroll
+        for (int k = 0; k < EU; ++k) {
+            const uint64_t e = base + k * stride;
+            if (e >= m) break;
+            const uint64_t u = su[k], v = sv[k], ww = sw[k];
+            b |= u >= n || v >= n || ww == 0;
+            wd |= ww >= wlim;
+            const uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
+            const uint64_t it = u != v ? (((lo << vb) | hi) << wb) | ww : ~0ull;
+            items[e] = it;
+            for (int p = 0; p < npass; ++p) {
+                const int left = 2 * vb - 8 * p;
+                const uint32_t dm = left >= 8 ? 0xFFu : ((1u << left) - 1u);
+                atomicAdd(&h[p * 256 + ((uint32_t)(it >> (wb + 8 * p)) & dm)], 1u);
+            }
         }
     }
     if (__any_sync(0xffffffffu, b) && lane_id() == 0) atomicExch(bad, 1u);
