@@ -565,6 +565,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     // packed path: the distinct edges in two orders and their run bounds (the adjacency in list form)
     DBuf<uint64_t> items, items2, uniq;
     DBuf<uint32_t> hist1;  // digit counts of the first sort, accumulated by the emission
+    DBuf<uint32_t> hist2;  // digit counts of the second sort, accumulated by the de-duplication
     DBuf<uint32_t> runs;
     ListAdj la{};
     uint32_t mu = 0;
@@ -599,12 +600,16 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             bool alt = false;
             CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), m, wb, 2 * vb, &alt, s, scal.get() + 8, nullptr,
                                         hist1.get()));
-            CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s));
+            const int npass2 = (vb + 7) / 8;
+            CLD_TRY(hist2.alloc((size_t)npass2 * 256, s));
+            CLD_CUDA(cudaMemsetAsync(hist2.get(), 0, (size_t)npass2 * 256 * 4, s));
+            CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s, hist2.get()));
             CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CLD_CUDA(cudaStreamSynchronize(s));
             mu = hbad[1];  // distinct undirected edges
             bool alt2 = false;
-            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), mu, wb, vb, &alt2, s, scal.get() + 8, uniq.get()));
+            CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), mu, wb, vb, &alt2, s, scal.get() + 8, uniq.get(),
+                                        hist2.get()));
             CLD_TRY(runs.alloc(4 * (size_t)n, s));
             CLD_CUDA(cudaMemsetAsync(runs.get(), 0, 4 * (size_t)n * 4, s));
             la.U = uniq.get();

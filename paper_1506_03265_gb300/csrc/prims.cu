@@ -823,39 +823,67 @@ __device__ __forceinline__ bool up_head(uint64_t prev, uint64_t x, uint64_t same
     return x < valid_lim && (prev ^ x) >= same_lim;
 }
 
-// First pass of the two-pass form: run heads per tile.
+// First pass of the two-pass form: run heads per tile (CTAs loop over tiles).  With hist2 the heads'
+// b digits are counted too, into per-warp shared histograms (dynamic, warps x npass x 256 words)
+// flushed once per CTA.
 __global__ void __launch_bounds__(UP_THREADS) k_unique_packed_count(const uint64_t* __restrict__ items, uint32_t cnt,
-                                                                    int vb, uint32_t* __restrict__ heads) {
+                                                                    int vb, uint32_t ntiles, uint32_t* __restrict__ heads,
+                                                                    uint32_t* __restrict__ hist2) {
+    extern __shared__ uint32_t uh[];
     __shared__ uint32_t s_w[UP_WARPS];
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
-    const uint64_t tbase = (uint64_t)blockIdx.x * UP_TILE;
-    const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
     const int wb = 64 - 2 * vb;
+    const int npass = (vb + 7) / 8;
+    if (hist2) {
+        for (int i = tid; i < UP_WARPS * npass * 256; i += UP_THREADS) uh[i] = 0;
+    }
+    uint32_t* h = uh + w * npass * 256;
     const uint64_t same_lim = 1ull << wb, valid_lim = ~0ull << wb;
     const uint32_t wstart = w * (UP_ITEMS * 32);
-    const uint64_t* it = items + tbase;
-    uint64_t x[UP_ITEMS];
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t tbase = (uint64_t)tile * UP_TILE;
+        const uint32_t rem = (uint32_t)min((uint64_t)UP_TILE, (uint64_t)cnt - tbase);
+        const uint64_t* it = items + tbase;
+        uint64_t x[UP_ITEMS];
 #pragma unroll
-    for (int i = 0; i < UP_ITEMS; ++i) {
-        const uint32_t li = wstart + (uint32_t)i * 32 + l;
-        x[i] = li < rem ? it[li] : ~0ull;
-    }
-    uint64_t carry = ~0ull;
-    if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
-    uint32_t run = 0;
+        for (int i = 0; i < UP_ITEMS; ++i) {
+            const uint32_t li = wstart + (uint32_t)i * 32 + l;
+            x[i] = li < rem ? it[li] : ~0ull;
+        }
+        uint64_t carry = ~0ull;
+        if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
+        uint32_t run = 0;
+        __syncthreads();  // the histograms are zeroed; s_w of the previous tile has been read
 #pragma unroll
-    for (int i = 0; i < UP_ITEMS; ++i) {
-        const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
-        const uint64_t prev = l == 0 ? carry : rot;
-        carry = rot;
-        run += (uint32_t)__popc(__ballot_sync(0xffffffffu, up_head(prev, x[i], same_lim, valid_lim)));
+        for (int i = 0; i < UP_ITEMS; ++i) {
+            const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
+            const uint64_t prev = l == 0 ? carry : rot;
+            carry = rot;
+            const bool hd = up_head(prev, x[i], same_lim, valid_lim);
+            run += (uint32_t)__popc(__ballot_sync(0xffffffffu, hd));
+            if (hist2 && hd) {
+                for (int p = 0; p < npass; ++p) {
+                    const int left = vb - 8 * p;
+                    const uint32_t dm = left >= 8 ? 0xFFu : ((1u << left) - 1u);
+                    atomicAdd(&h[p * 256 + ((uint32_t)(x[i] >> (wb + 8 * p)) & dm)], 1u);
+                }
+            }
+        }
+        if (l == 0) s_w[w] = run;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+            for (int ww = 0; ww < UP_WARPS; ++ww) t += s_w[ww];
+            heads[tile] = t;
+        }
     }
-    if (l == 0) s_w[w] = run;
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t t = 0;
-        for (int ww = 0; ww < UP_WARPS; ++ww) t += s_w[ww];
-        heads[blockIdx.x] = t;
+    if (hist2) {
+        __syncthreads();
+        for (int i = tid; i < npass * 256; i += UP_THREADS) {
+            uint32_t c = 0;
+            for (int ww = 0; ww < UP_WARPS; ++ww) c += uh[ww * npass * 256 + i];
+            if (c) atomicAdd(&hist2[i], c);
+        }
     }
 }
 
@@ -945,7 +973,7 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
 }
 
 cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64_t* out, uint32_t* total_dev,
-                               cudaStream_t s) {
+                               cudaStream_t s, uint32_t* hist2) {
     if (cnt == 0) {
         CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
         return CLDIAM_OK;
@@ -956,7 +984,9 @@ cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64
     DBuf<uint32_t> heads, first;
     CLD_TRY(heads.alloc(ntiles, s));
     CLD_TRY(first.alloc(ntiles, s));
-    CLD_K(K_CSR, s, k_unique_packed_count<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb, heads.get()));
+    const size_t usm = hist2 ? (size_t)UP_WARPS * ((vb + 7) / 8) * 256 * 4 : 0;  // <= 32 KB
+    CLD_K(K_CSR, s, k_unique_packed_count<<<grid_for((size_t)ntiles * UP_THREADS, UP_THREADS, 4), UP_THREADS, usm, s>>>(
+                        items, (uint32_t)cnt, vb, ntiles, heads.get(), hist2));
     CLD_LAUNCH_CHECK();
     CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, nullptr, s));
     CLD_K(K_CSR, s, k_unique_items<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb,
