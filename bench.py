@@ -1,24 +1,27 @@
 """Benchmark of the GB300 CL-DIAM hot path.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload rmat20]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload rmat24]
 
 One step = the whole CL-DIAM pass on one synthetic graph whose edge list is
 already resident in HBM: CSR build (dedup, symmetrise, LCC), initial Delta,
 CLUSTER(tau), quotient contraction and the estimate Phi(G_C) + 2R.  value =
 m_LCC / step time in GTEPS (undirected edges of the processed graph).  The
-edge list (201 MB for R-MAT 20) is larger than the 129 MB L2, so no flush is
-needed between steps.
+headline workload is R-MAT scale 24 (the paper's R-MAT(24) row, Table 2; its
+3.2 GB edge list and 6.2 GB CSR are far larger than the 129 MB L2, so no flush
+is needed between steps).
 
 Also reported on the same line: the end-to-end rate through cldiam_run with
 pinned host buffers (H2D copies inside the timed region), the roofline of the
-dominant kernel from live CUDA-event timing, the Delta-stepping baseline on
-the same graph, SM clocks sampled during the timed region, and the CPU oracle
-timed on a bounded sample of the same workload.
+dominant kernel class and of the Delta-growing step (both of its forms) from
+live CUDA-event timing, the same step on the R-MAT 20 and road-mesh workloads,
+the Delta-stepping baseline, the many-graph and served forms, SM clocks
+sampled during the timed region, and the CPU oracle timed on one host thread.
 
 With --impl reference the CPU oracle (a sequential program written from the
-paper) is timed instead, on a bounded sample of the workload.
-Under torchrun (N > 1) every rank runs an independent replica (weak scaling;
-the single-graph path has no exchange step), and rank 0 prints the line.
+paper) is timed instead, on a bounded sample (R-MAT scale 17, about a second a
+step).  Under torchrun (N > 1) every rank runs an independent replica (weak
+scaling; the single-graph path has no exchange step), and rank 0 prints the
+line.
 """
 from __future__ import annotations
 
@@ -44,10 +47,13 @@ SAMPLE_SCALE = 17  # CPU oracle sample: R-MAT scale 17 with the rmat20 recipe
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="rmat24")
+    ap.add_argument("--secondary", default="rmat20,roadmesh4096",
+                    help="other single-graph workloads timed the same way on the same line ('' = none)")
+    ap.add_argument("--secondary-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the many-graph leg")
@@ -74,35 +80,39 @@ def digest(a) -> str:
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample_run(scale: int = SAMPLE_SCALE):
-    """One oracle pass on the bounded sample; returns (seconds, m_LCC, describe)."""
-    import inputs
+def oracle_pass(e, tau, seed):
+    """One oracle pass (CSR build + LCC + CLUSTER + quotient + estimate); returns (seconds, m_LCC, n_LCC)."""
     import oracle
-    from inputs.workloads import WORKLOADS
-    wl = WORKLOADS["rmat20"]
-    e = inputs.rmat(scale, 16, 1 << 20, wl.seed)
     t0 = time.perf_counter()
     g = oracle.build_csr(e.n, e.src, e.dst, e.w, lcc=True)
     d0 = oracle.delta0(g)
-    cl = oracle.cluster(g, wl.tau, wl.seed, d0)
+    cl = oracle.cluster(g, tau, seed, d0)
     q = oracle.quotient(g, cl)
     oracle.estimate(q, cl)
-    dt = time.perf_counter() - t0
-    return dt, g.m, (f"R-MAT scale {scale} (edge factor 16, w in [1,2^20], seed {wl.seed}, LCC n={g.n}, "
-                     f"m={g.m}), tau {wl.tau}: CSR build + CLUSTER + quotient + estimate, one thread")
+    return time.perf_counter() - t0, g.m, g.n
 
 
-def cpu_baseline_leg(min_seconds: float = 10.0):
-    times, m, desc = [], 0, ""
-    t_all = time.perf_counter()
-    while True:
-        dt, m, desc = oracle_sample_run()
-        times.append(dt)
-        if time.perf_counter() - t_all >= min_seconds or len(times) >= 10:
-            break
-    t = statistics.median(times)
-    return {"value": round(m / t / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{desc}; median of {len(times)} runs ({t:.2f} s each)"}
+def oracle_sample_run(scale: int = SAMPLE_SCALE):
+    """One oracle pass on the bounded R-MAT sample; returns (seconds, m_LCC, describe)."""
+    import inputs
+    from inputs.workloads import WORKLOADS
+    wl = WORKLOADS["rmat20"]
+    e = inputs.rmat(scale, 16, 1 << 20, wl.seed)
+    dt, m, n = oracle_pass(e, wl.tau, wl.seed)
+    return dt, m, (f"R-MAT scale {scale} (edge factor 16, w in [1,2^20], seed {wl.seed}, LCC n={n}, "
+                   f"m={m}), tau {wl.tau}: CSR build + CLUSTER + quotient + estimate, one thread")
+
+
+def cpu_baseline_leg():
+    """The oracle, as it stands, on one host thread: one full pass over the R-MAT 20 workload (the headline's
+    R-MAT family at 1/16 of its edges; the R-MAT 24 pass takes about ten minutes)."""
+    from inputs.workloads import WORKLOADS
+    wl = WORKLOADS["rmat20"]
+    e = wl.make()
+    dt, m, n = oracle_pass(e, wl.tau, wl.seed)
+    return {"value": round(m / dt / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": (f"the rmat20 workload ({wl.describe}; LCC n={n}, m={m}), tau {wl.tau}, one full pass: "
+                       f"CSR build + LCC + CLUSTER + quotient + estimate on one thread, {dt:.1f} s")}
 
 
 def run_reference(args):
@@ -340,29 +350,55 @@ def delta0_leg(cd, side=2048, tau=5.4, seed=7):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def run_gpu(args):
+RELAX_CLASSES = ("relax", "relax_pull")  # the two forms of the Delta-growing step (row a5)
+
+
+def load_peaks():
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk)) if os.path.exists(pk) else {}
+
+
+def stored_traffic(workload, cls):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, while its source is unchanged."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    ent = json.load(open(tpath)).get(workload, {}).get(cls)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent.get("source_file", ""))
+    same = os.path.isfile(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == ent.get("source_sha256")
+    return ent.get("dram_bytes_per_launch") if same else None
+
+
+def roofline_of(prof, classes, peak, peaks, workload, tkey=None):
+    """HBM roofline of one kernel class (or the sum of several): algorithmic bytes of its launches in the
+    timed region / their CUDA-event time (events on the library's stream)."""
+    b = sum(prof[c]["bytes"] for c in classes)
+    ms = sum(prof[c]["ms"] for c in classes)
+    launches = sum(prof[c]["launches"] for c in classes)
+    achieved = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"bound": "hbm", "kernel": "+".join(classes), "achieved": round(achieved, 1) if achieved else None,
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+            "traffic": stored_traffic(workload, tkey or classes[0]), "launches": launches,
+            "alg_bytes_per_launch": round(b / max(1, launches)),
+            "avg_launch_us": round(1e3 * ms / max(1, launches), 2),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+
+
+def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None):
+    """Time `steps` whole CL-DIAM passes (CSR build .. estimate) on one workload with its edge list resident
+    in HBM; check the first pass against the oracle's stored result."""
     import torch
 
-    import paper_1506_03265_gb300 as cd
     from inputs.workloads import WORKLOADS
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cd.load()
-
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS[name]
     e = wl.make()
-    stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         src_d = torch.from_numpy(e.src.view(np.int32)).cuda()
         dst_d = torch.from_numpy(e.dst.view(np.int32)).cuda()
         w_d = torch.from_numpy(e.w.view(np.int32)).cuda()
     stream.synchronize()
-    in_bytes = 3 * 4 * e.m
 
     def step(mid_event=None):
         g = cd.build_csr(src_d, dst_d, w_d, e.n, lcc=True, stream=stream)
@@ -382,8 +418,8 @@ def run_gpu(args):
     m_lcc = nnz // 2
     center, D, cid = c.copy()
     qoff, qcol, qw = q.copy()
-    parity = "unchecked"
-    gold_path = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.json")
+    parity = "unchecked (no stored oracle result for this workload)"
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
     if os.path.exists(gold_path):
         gold = json.load(open(gold_path))
         ok = (gold["n"] == n_lcc and gold["nnz"] == nnz and gold["k"] == r["k"] and
@@ -393,8 +429,8 @@ def run_gpu(args):
               all(gold["stats"][k] == r[k] for k in gold["stats"]))
         parity = ("bit-exact vs the CPU oracle's stored result (centers, D, cluster ids, quotient CSR, estimate)"
                   if ok else "MISMATCH vs the CPU oracle's stored result")
-    del g, c, q
-    for _ in range(max(0, args.warmup - 1)):
+    del g, c, q, center, D, cid
+    for _ in range(max(0, warmup - 1)):
         g, c, q, r2 = step()
         del g, c, q
         assert r2["phi_approx"] == r["phi_approx"]
@@ -403,21 +439,19 @@ def run_gpu(args):
     tot = sum(shares.values()) or 1.0
     dominant = max((k for k in shares if prof_warm[k]["bytes"] > 0), key=lambda k: shares[k])
 
-    # timed region
-    cd.profile_set_timing([dominant])
+    # timed region: the dominant class and both growing-step forms are bracketed by CUDA events
+    cd.profile_set_timing(sorted({dominant, *RELAX_CLASSES}))
     cd.profile_reset()
-    sampler = ClockSampler(local)
-    sampler.wait_first()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev_end = [torch.cuda.Event(enable_timing=True) for _ in range(steps - 1)] + [ev1]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     ev0.record(stream)
-    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)] + [ev1]
-    for i in range(args.steps):
+    for i in range(steps):
         g, c, q, r2 = step(ev_mid[i])
         del g, c, q
         ev_end[i].record(stream)
@@ -425,45 +459,78 @@ def run_gpu(args):
     t_wall1 = time.time()
     if dist:
         dist.barrier()
-    sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    # split of each step: CSR build (a1) vs CLUSTER + quotient + estimate (a2-a11)
-    ms_csr = sum((ev0 if i == 0 else ev_end[i - 1]).elapsed_time(ev_mid[i]) for i in range(args.steps)) / args.steps
-    ms_rest = sum(ev_mid[i].elapsed_time(ev_end[i]) for i in range(args.steps)) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
+    ms_csr = sum((ev0 if i == 0 else ev_end[i - 1]).elapsed_time(ev_mid[i]) for i in range(steps)) / steps
+    ms_rest = sum(ev_mid[i].elapsed_time(ev_end[i]) for i in range(steps)) / steps
     prof = cd.profile_get()
-    launches = sum(v["launches"] for v in prof.values())
     if dist:
         from paper_1506_03265_gb300.shard import max_over_ranks
-        ms = max_over_ranks(ms, dist, torch.device("cuda", local))
-        ms_csr = max_over_ranks(ms_csr, dist, torch.device("cuda", local))
-        ms_rest = max_over_ranks(ms_rest, dist, torch.device("cuda", local))
-    value = ws * m_lcc / (ms * 1e-3) / 1e9
-    clocks = sampler.summary(t_wall0, t_wall1)
-
-    # roofline of the dominant kernel class, from its live event timing in the timed region
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
+        dev = torch.device("cuda", local)
+        ms, ms_csr, ms_rest = (max_over_ranks(x, dist, dev) for x in (ms, ms_csr, ms_rest))
+    ws = dist.get_world_size() if dist else 1
+    peaks = load_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    dk = prof[dominant]
-    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["ms"] > 0 else None
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tt = json.load(open(tpath))
-        ent = tt.get(args.workload, {}).get(dominant)
-        if ent:
-            src = os.path.join(ROOT, ent.get("source_file", ""))
-            same_kernel = os.path.isfile(src) and \
-                hashlib.sha256(open(src, "rb").read()).hexdigest() == ent.get("source_sha256")
-            traffic = ent.get("dram_bytes_per_launch") if same_kernel else None
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1) if achieved else None,
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-                "traffic": traffic, "launches": dk["launches"],
-                "alg_bytes_per_launch": round(dk["bytes"] / max(1, dk["launches"])),
-                "avg_launch_us": round(1e3 * dk["ms"] / max(1, dk["launches"]), 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback"}
+    relax_ms = sum(prof[c]["ms"] for c in RELAX_CLASSES) / steps
+    scanned = r["edges_scanned"]
+    out = {
+        "workload": name, "describe": wl.describe, "tau": wl.tau, "seed": wl.seed, "n_lcc": n_lcc, "m_lcc": m_lcc,
+        "ms_per_step": round(ms, 3), "gteps": round(ws * m_lcc / (ms * 1e-3) / 1e9, 4),
+        "result": {k: r[k] for k in ("k", "phi_gc", "radius", "phi_approx", "stages", "steps", "doublings",
+                                     "delta_end", "node_updates", "edges_scanned", "quotient_edges")},
+        "parity": parity,
+        "step_split": {"csr_build_ms": round(ms_csr, 3), "cluster_quotient_estimate_ms": round(ms_rest, 3),
+                       "gteps_excluding_csr_build": round(ws * m_lcc / (ms_rest * 1e-3) / 1e9, 4),
+                       "what": "m_LCC / time of CLUSTER + quotient + estimate on a built CSR (the same timed steps)"},
+        "roofline": roofline_of(prof, [dominant], peak, peaks, name),
+        "relax_roofline": dict(
+            roofline_of(prof, list(RELAX_CLASSES), peak, peaks, name, tkey="relax_steps"),
+            what=("both forms of the Delta-growing step (pushed relax and dense relax_pull) over the timed "
+                  "steps: algorithmic bytes = 16 B per adjacency entry a launch reads + per-entry/row/changed-"
+                  "node terms (DESIGN.md section 6) / CUDA-event time"),
+            ms_per_step=round(relax_ms, 4),
+            forms={c: {"launches": prof[c]["launches"], "ms": round(prof[c]["ms"] / steps, 4),
+                       "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9, 1) if prof[c]["ms"] else None}
+                   for c in RELAX_CLASSES},
+            edges_scanned_per_step=scanned,
+            scanned_16B_gbs=round(16.0 * scanned / (relax_ms * 1e-3) / 1e9, 1) if relax_ms else None,
+            scanned_16B_frac=round(16.0 * scanned / (relax_ms * 1e-3) / 1e9 / peak, 4) if relax_ms else None,
+            relax_gteps=round(scanned / (relax_ms * 1e-3) / 1e9, 3) if relax_ms else None),
+        "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
+        "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
+        "gpu_launches": sum(v["launches"] for v in prof.values()),
+        "wall": (t_wall0, t_wall1),
+        "in_bytes": 12 * e.m, "nnz": nnz,
+    }
+    return out, (e, src_d, dst_d, w_d, r)
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1506_03265_gb300 as cd
+    from inputs.workloads import WORKLOADS
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cd.load()
+    stream = torch.cuda.Stream()
+    wl = WORKLOADS[args.workload]
+
+    sampler = ClockSampler(local)
+    sampler.wait_first()
+    head, (e, src_d, dst_d, w_d, r) = measure_workload(cd, args.workload, args.steps, args.warmup, stream, dist, local)
+    t_wall0, t_wall1 = head.pop("wall")
+    clocks = sampler.summary(t_wall0, t_wall1)
+    in_bytes = head.pop("in_bytes")
+    nnz = head.pop("nnz")
+    m_lcc = head["m_lcc"]
+    ms = head["ms_per_step"]
+    value = head["gteps"]
+    launches = head["gpu_launches"]
 
     # end to end through the public API with pinned host buffers
     src_h = torch.from_numpy(e.src.view(np.int32)).pin_memory()
@@ -484,17 +551,28 @@ def run_gpu(args):
     e2e = {"value": round(ws * m_lcc / (ms_e2e * 1e-3) / 1e9, 4), "unit": "GTEPS", "ms_per_step": round(ms_e2e, 3),
            "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 88,
            "api": "cldiam_run (pinned host edge list in, cldiam_result out)"}
+    del src_h, dst_h, w_h
 
     # Delta-stepping baseline (Section 5) on the same graph
     g = cd.build_csr(src_d, dst_d, w_d, e.n, lcc=True, stream=stream)
     s = cd.sssp_source(g, wl.seed)
     cd.sssp_delta(g, s, want_dist=False)
     torch.cuda.synchronize()
+    cd.profile_set_timing(["delta_stepping"])
+    cd.profile_reset()
     t0 = time.perf_counter()
     reps = 3
     for _ in range(reps):
         _, ecc, rounds = cd.sssp_delta(g, s, want_dist=False)
     t_ds = (time.perf_counter() - t0) / reps
+    pds = cd.profile_get()["delta_stepping"]
+    peaks = load_peaks()
+    sssp = {"what": "Delta-stepping SSSP from the Philox source, 2*ecc = upper bound",
+            "ms": round(t_ds * 1e3, 3), "gteps": round(m_lcc / t_ds / 1e9, 4), "ecc": ecc,
+            "upper_bound": 2 * ecc, "rounds": rounds,
+            "roofline": roofline_of({"delta_stepping": pds}, ["delta_stepping"], peaks.get("hbm_gbs", 6800.0),
+                                    peaks, args.workload)}
+    cd.profile_set_timing([])
     cl2 = None
     if not args.no_cluster2:
         # CLUSTER2 (Algorithm 2) + quotient + estimate on the same CSR: the provable variant of Section 4
@@ -510,34 +588,48 @@ def run_gpu(args):
                "k": r2["k"], "radius": r2["radius"], "phi_gc": r2["phi_gc"], "phi_approx": r2["phi_approx"],
                "iterations": r2["stages"], "growth_rounds": r2["steps"], "r_cl": r2["delta_end"] // 2,
                "phi_approx_over_cluster": round(r2["phi_approx"] / r["phi_approx"], 4)}
-    del g
+    del g, src_d, dst_d, w_d, e
+    torch.cuda.empty_cache()
 
     line = {
-        "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "describe": wl.describe, "tau": wl.tau, "seed": wl.seed,
-                   "n_lcc": n_lcc, "m_lcc": m_lcc, "parallelism": f"replicas x{ws}",
+        "config": {"workload": args.workload, "describe": head["describe"], "tau": head["tau"], "seed": head["seed"],
+                   "n_lcc": head["n_lcc"], "m_lcc": m_lcc, "parallelism": f"replicas x{ws}",
                    "step": "CSR build + LCC + CLUSTER + quotient + estimate, edge list resident in HBM",
                    "l2": f"no flush: edge list {in_bytes / 1e6:.0f} MB and CSR {nnz * 12 / 1e6:.0f} MB exceed the 129 MB L2"},
-        "result": {k: r[k] for k in ("k", "phi_gc", "radius", "phi_approx", "stages", "steps", "doublings",
-                                     "delta_end", "node_updates", "edges_scanned", "quotient_edges")},
-        "parity": parity,
-        "step_split": {"csr_build_ms": round(ms_csr, 3), "cluster_quotient_estimate_ms": round(ms_rest, 3),
-                       "gteps_excluding_csr_build": round(ws * m_lcc / (ms_rest * 1e-3) / 1e9, 4),
-                       "what": "m_LCC / time of CLUSTER + quotient + estimate on a built CSR (the same timed steps)"},
+        "result": head["result"],
+        "parity": head["parity"],
+        "step_split": head["step_split"],
         "e2e": e2e,
-        "roofline": roofline,
-        "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
-        "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
+        "roofline": head["roofline"],
+        "relax_roofline": head["relax_roofline"],
+        "kernel_shares": head["kernel_shares"],
+        "kernel_ms_per_step": head["kernel_ms_per_step"],
         "clocks": clocks,
         "gpu_launches": launches,
-        "sssp_baseline": {"what": "Delta-stepping SSSP from the Philox source, 2*ecc = upper bound",
-                          "ms": round(t_ds * 1e3, 3), "gteps": round(m_lcc / t_ds / 1e9, 4), "ecc": ecc,
-                          "upper_bound": 2 * ecc, "rounds": rounds},
+        "sssp_baseline": sssp,
     }
     if cl2:
         line["cluster2"] = cl2
+    # the other single-graph workloads: same step, same checks, fewer steps
+    if args.secondary:
+        sec = {}
+        for name in [x for x in args.secondary.split(",") if x and x != args.workload]:
+            sm = ClockSampler(local)
+            sm.wait_first()
+            res, keep = measure_workload(cd, name, args.secondary_steps, args.warmup, stream, dist, local)
+            del keep
+            w0, w1 = res.pop("wall")
+            res.pop("in_bytes"); res.pop("nnz")
+            res["clocks"] = sm.summary(w0, w1)
+            sm.stop()
+            for k in ("kernel_shares",):
+                res.pop(k)
+            sec[name] = res
+            torch.cuda.empty_cache()
+        line["secondary_workloads"] = sec
     if not args.no_delta0_experiment and rank == 0:
         line["initial_delta_experiment"] = delta0_leg(cd)
     if not args.no_batched:
@@ -547,6 +639,7 @@ def run_gpu(args):
             # the serving leg runs on a single GPU: its query stream is one queue
             line["served"] = served_leg(cd, mix, [int(x) for x in args.serve_rates.split(",")])
         mix[0].free()
+    sampler.stop()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if dist:

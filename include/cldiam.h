@@ -341,11 +341,42 @@ cldiam_status cldiam_server_replay(cldiam_server* s, const uint32_t* graph_ids, 
 void cldiam_server_free(cldiam_server* s);
 
 /* ------------------------------------------------------------------------
+ * Tuning.  No counterpart in the paper: launch shapes of the kernels and the
+ * cut-overs between equivalent forms of one step.  Every knob is
+ * result-invariant -- each form computes the same integers -- so a choice only
+ * changes the time.  A field left 0 takes the library default.
+ */
+typedef struct {
+    float pull_ratio;              /* a growing step takes the dense pull form (every node reads its
+                                      own adjacency) when its relaxers' adjacency is at least this share
+                                      of all adjacency entries; < 0 = never; 0 = 0.3                */
+    uint32_t relax_ctas_per_sm;    /* CTAs per SM of the growing-step kernels; 0 = all that fit     */
+    uint32_t dense_quotient_k;     /* CLDIAM_QUOTIENT_AUTO: dense k x k de-duplication up to this k
+                                      (<= 65535), radix sort above; 0 = 4096                       */
+    uint32_t apsp_sources_per_cta; /* quotient diameter by batched SSSP: sources per CTA, 1, 4 or 8;
+                                      0 = by k (8 below 2,048 nodes, else 4)                       */
+    uint32_t apsp_fw_density;      /* quotient diameter by Floyd-Warshall when nnz >= k^2 / this,
+                                      batched SSSP otherwise; 0 = 8                                 */
+    uint32_t batch_fw_k;           /* many-graph form: quotients up to this k (<= 200) are closed by
+                                      Floyd-Warshall in shared memory; 0 = 200                     */
+    float sssp_delta_scale;        /* Delta-stepping with delta = 0: Delta = this x the average
+                                      weight (>= 1); 0 = 1                                          */
+    uint32_t reserved[9];          /* must be 0                                                     */
+} cldiam_tuning;
+
+/* The process-wide knobs (defaults filled in). */
+cldiam_status cldiam_tuning_get(cldiam_tuning* out);
+/* Replace the process-wide knobs; NULL restores the defaults.  INVALID_ARG on a value out of range.
+ * Takes effect for calls that start afterwards; not meant to race with calls in flight. */
+cldiam_status cldiam_tuning_set(const cldiam_tuning* t);
+
+/* ------------------------------------------------------------------------
  * Instrumentation.  No counterpart in the method itself; it exposes what the
  * paper measures (rounds and work, Table 2) plus per-kernel device time.
  * Kernel classes: 0 relax, 1 snapshot, 2 rebuild, 3 select, 4 finalize,
  * 5 growable, 6 radix_hist, 7 radix_scatter, 8 scan, 9 csr, 10 components,
- * 11 quotient, 12 floyd_warshall, 13 delta_stepping, 14 reduce, 15 misc.
+ * 11 quotient, 12 floyd_warshall, 13 delta_stepping, 14 reduce, 15 misc,
+ * 16 relax_pull (the dense form of a growing step).
  * Process-wide; not meant for concurrent use from several threads.
  */
 /* Bit i set: bracket every launch of class i with CUDA events on its stream. 0 = off (default). */

@@ -43,6 +43,17 @@ class Opts(ctypes.Structure):
                 ("reserved", ctypes.c_uint32 * 2)]
 
 
+class Tuning(ctypes.Structure):
+    """cldiam_tuning: result-invariant launch shapes and cut-overs (0 = library default)."""
+    _fields_ = [("pull_ratio", ctypes.c_float), ("relax_ctas_per_sm", ctypes.c_uint32),
+                ("dense_quotient_k", ctypes.c_uint32), ("apsp_sources_per_cta", ctypes.c_uint32),
+                ("apsp_fw_density", ctypes.c_uint32), ("batch_fw_k", ctypes.c_uint32),
+                ("sssp_delta_scale", ctypes.c_float), ("reserved", ctypes.c_uint32 * 9)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class Result(ctypes.Structure):
     _fields_ = [("phi_gc", ctypes.c_uint64), ("radius", ctypes.c_uint64), ("phi_approx", ctypes.c_uint64),
                 ("k", ctypes.c_uint32), ("stages", ctypes.c_uint32), ("steps", ctypes.c_uint32),
@@ -114,6 +125,8 @@ def load(build_if_missing: bool = True):
             "cldiam_server_poll": (st, [P, ctypes.c_uint64, P]),
             "cldiam_server_replay": (st, [P, P, P, P, P, ctypes.c_uint32, ctypes.c_int32, P, P, P]),
             "cldiam_server_free": (None, [P]),
+            "cldiam_tuning_get": (st, [P]),
+            "cldiam_tuning_set": (st, [P]),
             "cldiam_profile_set_timing": (st, [ctypes.c_uint32]),
             "cldiam_profile_reset": (st, []),
             "cldiam_profile_num_classes": (ctypes.c_uint32, []),
@@ -445,8 +458,30 @@ def sssp_delta(g: Graph, source: int, delta: int = 0, want_dist: bool = True):
     return dist, ecc.value, rounds.value
 
 
+def tuning_get() -> dict:
+    """cldiam_tuning_get: the process-wide knobs in effect (defaults filled in)."""
+    t = Tuning()
+    _check(load().cldiam_tuning_get(ctypes.byref(t)), "cldiam_tuning_get")
+    return t.as_dict()
+
+
+def tuning_set(**knobs) -> None:
+    """cldiam_tuning_set: replace the process-wide knobs (unnamed ones = library default);
+    no arguments restores every default."""
+    if not knobs:
+        _check(load().cldiam_tuning_set(None), "cldiam_tuning_set")
+        return
+    t = Tuning()
+    for k, v in knobs.items():
+        if k not in dict(Tuning._fields_) or k == "reserved":
+            raise KeyError(k)
+        setattr(t, k, v)
+    _check(load().cldiam_tuning_set(ctypes.byref(t)), "cldiam_tuning_set")
+
+
 KERNEL_CLASSES = ["relax", "snapshot", "rebuild", "select", "finalize", "growable", "radix_hist", "radix_scatter",
-                  "scan", "csr", "components", "quotient", "floyd_warshall", "delta_stepping", "reduce", "misc"]
+                  "scan", "csr", "components", "quotient", "floyd_warshall", "delta_stepping", "reduce", "misc",
+                  "relax_pull"]
 
 
 def profile_set_timing(classes) -> None:

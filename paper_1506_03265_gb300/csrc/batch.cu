@@ -327,7 +327,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                         ctr->nnext = 0;
                     }
                     __syncthreads();
-                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nullptr, nf, E, adj, ws.center,
+                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nf, E, adj, ws.center,
                                  job.cumulative ? ws.D : nullptr, ws.key,
                                  delta, ws.stamp, stepid, ws.next, ctr, sm.relax, sm.relax_next, 0, 1);
                     __syncthreads();

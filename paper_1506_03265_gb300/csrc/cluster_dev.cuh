@@ -53,22 +53,20 @@ struct Counters {
 static_assert(offsetof(Counters, pad) + 4 - offsetof(Counters, newly_covered) == 24,
               "the per-step counters form one block");
 
-constexpr int RT = 256;                        // relax threads per CTA in the grid form
-constexpr int RU = 4;                          // adjacency entries per relax thread per chunk (grid form)
-constexpr int RC = 1024;                       // adjacency entries per relax chunk
-static_assert(RT * RU == RC, "the grid form's chunk is RT x RU entries");
+constexpr int RC = 1024;  // adjacency entries per relax chunk of one CTA (the many-graph form)
+constexpr int QC = 128;   // frontier positions per chunk-table slot (one warp chunk of the one-graph form)
 // In shared memory a pull entry's key is kPullTag | v: a pushed key has
 // d < Delta <= 2^31, so its high word is never all ones.
 constexpr unsigned long long kPullTag = 0xFFFFFFFF00000000ull;
 
 // Chunk table of a frontier: cfirst[c] = the entry whose adjacency range
-// holds flattened position c * RC.  The producer of each entry writes the
+// holds flattened position c * QC.  The producer of each entry writes the
 // chunk starts that fall inside its range, so relax finds a chunk's entries
 // with two loads instead of a search over the frontier.
 __device__ __forceinline__ void chunk_table_put(uint32_t* __restrict__ cfirst, uint32_t slot, uint32_t pre,
                                                 uint32_t deg) {
     const uint64_t end = (uint64_t)pre + deg;
-    for (uint64_t c = ((uint64_t)pre + RC - 1) / RC; c * RC < end; ++c) cfirst[c] = slot;
+    for (uint64_t c = ((uint64_t)pre + QC - 1) / QC; c * QC < end; ++c) cfirst[c] = slot;
 }
 
 __device__ __forceinline__ void warp_add_u64(unsigned long long* p, unsigned long long v) {
@@ -105,7 +103,8 @@ __device__ __forceinline__ void front_append(unsigned long long* ctr, bool pred,
 // a3: draw the new centers of this stage among unfrozen nodes, reset the others.
 __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restrict__ center,
                                            unsigned long long* __restrict__ key, uint64_t seed, uint32_t stage,
-                                           uint64_t thr, Counters* ctr, uint32_t br, uint32_t nb) {
+                                           uint64_t thr, Counters* ctr, uint32_t br, uint32_t nb,
+                                           unsigned long long* __restrict__ keyS = nullptr) {
     unsigned long long cnt = 0;
     for (uint32_t base = br * blockDim.x; base < n; base += nb * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
@@ -113,6 +112,7 @@ __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restric
             const U4 r = philox4x32_10(seed, v, stage, 0u, 0u);
             const bool sel = (uint64_t)r.x < thr;
             key[v] = sel ? (unsigned long long)v : kInfKey;
+            if (keyS) keyS[v] = sel ? (unsigned long long)v : kInfKey;
             cnt += sel ? 1 : 0;
         }
     }
@@ -221,8 +221,7 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // entries cut into chunks of U x blockDim.x; each CTA takes chunks, each warp
 // U x 32 consecutive positions of it, and maps every position to its
 // frontier entry from the entries the chunk spans, held in shared memory, so
-// hubs spread over many CTAs.  With a chunk table (cfirst, chunks of RC) a chunk's entries come from
-// two loads; without one, a block-wide search finds them.  The entries of the
+// hubs spread over many CTAs.  A block-wide search finds a chunk's entries.  The entries of the
 // next chunk are copied into the other shared buffer (cp.async) while the
 // current one is processed, so one barrier per chunk remains.  Every thread
 // handles U positions per chunk with their loads issued together; a key is
@@ -234,7 +233,7 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // atomic per U x 32 or more nodes.
 template <int U>
 __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
-                                          const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
+                                          const uint32_t* __restrict__ fpre,
                                           uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
                                           const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
                                           unsigned long long* __restrict__ key, uint32_t delta,
@@ -242,7 +241,8 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
                                           uint32_t* __restrict__ next, Counters* ctr, RelaxSmem& sm,
                                           uint32_t* nbuf, uint32_t br, uint32_t nb) {
     constexpr uint32_t kNB = 2 * U * 32;  // a chunk adds at most U x 32 nodes per warp
-    const uint32_t tid = threadIdx.x, nt = blockDim.x, CL = U * nt;  // CL <= RC; == RC with a chunk table
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, CL = U * nt;  // CL <= RC
+    const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     unsigned long long newly = 0;
     uint32_t* wbuf = nbuf + (tid >> 5) * kNB;
     uint32_t wcnt = 0;  // entries in this warp's buffer (warp-uniform)
@@ -258,14 +258,8 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
     const auto range_of = [&](uint32_t c, uint32_t& i0, uint32_t& cnt) {
         const uint32_t e0 = c * CL;
         const uint32_t e1 = (uint32_t)min((uint64_t)E, (uint64_t)e0 + CL);
-        uint32_t il;
-        if (cfirst) {
-            i0 = __ldcg(&cfirst[c]);
-            il = e1 < E ? __ldcg(&cfirst[c + 1]) : nf - 1;  // may be an entry starting at e1: never matched
-        } else {
-            i0 = block_last_le(fpre, 0, nf, e0);
-            il = block_last_le(fpre, i0, nf, e1 - 1);
-        }
+        i0 = block_last_le(fpre, 0, nf, e0);
+        const uint32_t il = block_last_le(fpre, i0, nf, e1 - 1);
         cnt = il - i0 + 1;
     };
     const auto stage = [&](uint32_t b, uint32_t i0, uint32_t cnt) {
@@ -324,7 +318,8 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
         uint2 ed[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            ed[u] = pos[u] < e1 ? adj[sm.base[b][own[u]] + pos[u]] : make_uint2(0u, 0xFFFFFFFFu);
+            ed[u] = pos[u] < e1 ? ld_stream_u2(adj + (sm.base[b][own[u]] + pos[u]), pol_stream)
+                                : make_uint2(0u, 0xFFFFFFFFu);
         uint32_t target[U];
         unsigned long long nk[U], cur[U];
 #pragma unroll
@@ -352,14 +347,14 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
             }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) cur[u] = nk[u] != kInfKey ? __ldcg(&key[target[u]]) : 0ull;
+        for (int u = 0; u < U; ++u) cur[u] = nk[u] != kInfKey ? ld_cg_keep_u64(&key[target[u]], pol_keep) : 0ull;
         bool first[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             first[u] = false;
             if (nk[u] < cur[u]) {
                 // the key is below its start-of-step value after this, whoever wins the minimum
-                atomicMin(&key[target[u]], nk[u]);
+                red_min_keep_u64(&key[target[u]], nk[u], pol_keep);
                 // only the first changers of a node this step need the exchange (hubs see many)
                 if (__ldcg(&stamp[target[u]]) != stepid) {
                     const uint32_t old = atomicExch(&stamp[target[u]], stepid);
@@ -395,7 +390,8 @@ __device__ __forceinline__ void dev_snapshot(const uint32_t* __restrict__ next, 
                                              const uint64_t* __restrict__ off, uint32_t delta,
                                              uint32_t* __restrict__ fbase, unsigned long long* __restrict__ fkey,
                                              uint32_t* __restrict__ fpre, uint32_t* __restrict__ cfirst, Counters* ctr,
-                                             unsigned long long* scratch, uint32_t br, uint32_t nb) {
+                                             unsigned long long* scratch, uint32_t br, uint32_t nb,
+                                             unsigned long long* __restrict__ keyS = nullptr) {
     for (uint32_t base = br * blockDim.x; base < nn; base += nb * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         bool take = false;
@@ -404,6 +400,7 @@ __device__ __forceinline__ void dev_snapshot(const uint32_t* __restrict__ next, 
         if (i < nn) {
             v = __ldcg(&next[i]);
             k = __ldcg(&key[v]);
+            if (keyS) keyS[v] = k;  // the next step's start-of-step key
             const uint64_t o = off[v];
             b0 = (uint32_t)o;
             deg = (uint32_t)(off[v + 1] - o);
@@ -453,7 +450,9 @@ __device__ __forceinline__ void dev_finalize_d(uint32_t n, const unsigned long l
 __device__ __forceinline__ void dev_finalize_freeze(uint32_t n, unsigned long long* __restrict__ key,
                                                     uint32_t* __restrict__ center, uint32_t* __restrict__ R,
                                                     const uint32_t* __restrict__ D, const uint64_t* __restrict__ off,
-                                                    Counters* ctr, uint32_t br, uint32_t nb) {
+                                                    Counters* ctr, uint32_t br, uint32_t nb,
+                                                    unsigned long long* __restrict__ keyS = nullptr,
+                                                    bool cumulative = false) {
     unsigned long long cnt = 0, degs = 0;
     for (uint32_t base = br * blockDim.x; base < n; base += nb * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
@@ -467,6 +466,8 @@ __device__ __forceinline__ void dev_finalize_freeze(uint32_t n, unsigned long lo
                 dv = __ldcg(&D[v]);
                 center[v] = c;
                 key[v] = 0;
+                // as a relaxer a contracted node holds (0, c_v), or (D_v, c_v) in the cumulative mode
+                if (keyS) keyS[v] = ((cumulative ? (unsigned long long)dv : 0ull) << 32) | c;
                 ++cnt;
                 degs += off[v + 1] - off[v];
             }

@@ -233,6 +233,52 @@ __device__ T block_reduce(T v, Op op, T identity) {
     return v;  // valid in thread 0
 }
 
+// ---------------------------------------------------------------- L2 eviction priorities
+// A graph sweep streams adjacency that is read once per step; the node state
+// it looks up (keys, stamps) is far smaller and reused by every entry.  The
+// streamed lines are loaded with the evict-first policy (and no L1
+// allocation), the node state with evict-last, so that the state stays in L2
+// while the adjacency passes through.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2* p, uint64_t pol) {
+    uint2 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+// read-only for the whole kernel (a snapshot): may be cached in L1
+__device__ __forceinline__ unsigned long long ld_nc_keep_u64(const unsigned long long* p, uint64_t pol) {
+    unsigned long long r;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+// mutable node state: L2 only (other CTAs write it in the same kernel)
+__device__ __forceinline__ unsigned long long ld_cg_keep_u64(const unsigned long long* p, uint64_t pol) {
+    unsigned long long r;
+    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ unsigned long long atom_min_keep_u64(unsigned long long* p, unsigned long long v,
+                                                                uint64_t pol) {
+    unsigned long long old;
+    asm volatile("atom.global.min.L2::cache_hint.u64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(v), "l"(pol)
+                 : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_min_keep_u64(unsigned long long* p, unsigned long long v, uint64_t pol) {
+    asm volatile("red.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
 // ---------------------------------------------------------------- device-wide primitives (prims.cu)
 // Exclusive prefix sum of n values; *total (device pointer, may be null) gets the sum.
 cldiam_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, size_t n, uint32_t* total, cudaStream_t s);

@@ -99,4 +99,9 @@ uint64_t arena_device_bytes(const cldiam_arena* a);
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
                          uint64_t* rounds);
 
+// tuning knobs in effect (defaults filled in) and their validation (tune.cu)
+cldiam_tuning tuning_current();
+cldiam_tuning tuning_defaults_filled(const cldiam_tuning& t);
+cldiam_status tuning_check(const cldiam_tuning& t);
+
 }  // namespace cld

@@ -25,7 +25,8 @@ thread_local cudaEvent_t t_open[K_NCLASS];
 
 const char* kNames[K_NCLASS] = {"relax",     "snapshot",     "rebuild", "select", "finalize", "growable",
                                 "radix_hist", "radix_scatter", "scan",    "csr",    "components", "quotient",
-                                "floyd_warshall", "delta_stepping", "reduce", "misc"};
+                                "floyd_warshall", "delta_stepping", "reduce", "misc",
+                                "relax_pull"};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {

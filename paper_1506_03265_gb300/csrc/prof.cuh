@@ -27,6 +27,7 @@ enum KClass : int {
     K_SSSP,
     K_REDUCE,
     K_MISC,
+    K_PULL,
     K_NCLASS
 };
 
