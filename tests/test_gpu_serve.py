@@ -9,11 +9,16 @@ import numpy as np
 import pytest
 
 import inputs
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("phi_gc", "radius", "phi_approx", "k", "stages", "steps", "doublings", "delta_end", "guard_exits",
           "node_updates", "edges_scanned", "quotient_edges", "centers_drawn")
+# every field the oracle defines the same way (edges_scanned counts the GPU's frontier entries, while the
+# oracle re-reads every relaxer's adjacency at every step)
+ORACLE_FIELDS = tuple(f for f in FIELDS if f != "edges_scanned")
+EDGES = []  # edge lists of the arena's graphs, in arena order
 
 
 @pytest.fixture(scope="module")
@@ -22,13 +27,51 @@ def env():
     from inputs.workloads import mixture_tau
     cd.load()
     arena = cd.arena_create()
-    ids, ns = [], []
+    ids, ns, edges = [], [], []
     for g in range(18):
         kind, scale, side, sub = inputs.mix_params(5, g)
         e = inputs.rmat(min(scale, 11), 8, 1000, sub) if kind == 0 else inputs.grid(min(side, 80), 1000, sub)
         ids.append(arena.add(e.src, e.dst, e.w, e.n))
         ns.append(arena.graph(ids[-1]).n)
+        edges.append(e)
+    EDGES[:] = edges
     return cd, arena, ids, [mixture_tau(n) for n in ns], ns
+
+
+def oracle_result(e, tau, seed):
+    """The whole method on the CPU oracle, as a dict over ORACLE_FIELDS."""
+    og = oracle.build_csr(e.n, e.src, e.dst, e.w)
+    ores, ocl, oq = oracle.cldiam(og, tau, seed)
+    out = {"phi_gc": ores.phi_gc, "radius": ores.radius, "phi_approx": ores.phi_approx, "k": ores.k,
+           "quotient_edges": int(oq.col.size)}
+    out.update({f: int(ocl.stats[f]) for f in ("stages", "steps", "doublings", "delta_end", "guard_exits",
+                                                "node_updates", "centers_drawn")})
+    return out
+
+
+def test_served_results_equal_oracle(env):
+    # 24 queries, every graph of the arena at least once, on both lanes: the three largest graphs go to the
+    # one-graph lane (big_nodes), the rest to the persistent serving CTAs; every field equals the oracle's
+    cd, arena, ids, taus, ns = env
+    big = sorted(ns)[-3]
+    srv = cd.server_create(arena, ctas=8, big_nodes=big - 1, idle_seconds=2.0)
+    rng = np.random.default_rng(9)
+    picks = list(range(len(ids))) + [int(x) for x in rng.integers(0, len(ids), 6)]
+    seeds = [int(x) for x in rng.integers(1, 1 << 30, len(picks))]
+    tickets = [srv.submit(ids[g], taus[g], s) for g, s in zip(picks, seeds)]
+    got = {}
+    t0 = time.time()
+    while len(got) < len(tickets) and time.time() - t0 < 60:
+        for t in tickets:
+            if t not in got:
+                r = srv.poll(t)
+                if r is not None:
+                    got[t] = r
+    srv.free()
+    assert len(got) == len(tickets)
+    assert sum(ns[g] >= big for g in picks) >= 3 and sum(ns[g] < big for g in picks) >= 15  # both lanes
+    for g, s, t in zip(picks, seeds, tickets):
+        assert {f: got[t][f] for f in ORACLE_FIELDS} == oracle_result(EDGES[g], taus[g], s), (g, s)
 
 
 def alone(cd, arena, gid, tau, seed):
