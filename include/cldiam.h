@@ -247,13 +247,16 @@ cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* c
  *  - Scratch is one fixed array inside the library (about 4 MB per GPU that
  *    loads it, resident until the process exits).  Limits: k <= 1024 when the
  *    graph has at least k^2/8 entries (Floyd-Warshall in that array), k <=
- *    51,200 otherwise (batched SSSP in shared memory); larger k returns
+ *    51,200 otherwise (batched SSSP with the same kernels cldiam_apsp_max
+ *    takes by default, its distances in shared memory); larger k returns
  *    CLDIAM_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or allocating library call.
  *  - The first call on each device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
+ *  - Each call waits for `stream` to finish its work before it returns.
  *  - Every call reuses the same array, so two calls whose work overlaps on the
  *    GPU (different streams or threads) race on it: serialise them.
- * Errors: INVALID_ARG (NULL, host pointers, malformed CSR), UNSUPPORTED, OVERFLOW, CUDA.
+ * Errors: INVALID_ARG (NULL, host pointers, malformed CSR), UNSUPPORTED, OVERFLOW,
+ * DIVERGED (the SSSP exceeded its round limit), CUDA.
  */
 cldiam_status cldiam_apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
                                       void* stream, uint64_t* phi);
@@ -262,14 +265,16 @@ cldiam_status cldiam_apsp_max_noalloc(uint32_t k, const uint64_t* off, const uin
 cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t* source);
 /*
  * Delta-stepping SSSP (Meyer and Sanders) from `source` with bucket width
- * `delta` (>= 1; 0 = average edge weight): exact distances, so any delta gives
- * the same result.  dist[n] (may be NULL; 0xFFFFFFFF = unreachable) and
- * *ecc = largest finite distance (host pointer); 2 * ecc is the SSSP
- * 2-approximation of Section 5.  *rounds (may be NULL) = light/heavy phases run.
+ * `delta` (>= 1; 0 = average edge weight times cldiam_tuning.sssp_delta_scale):
+ * exact distances, so any delta gives the same result.  dist[n] (may be NULL;
+ * 0xFFFFFFFF = unreachable) and *ecc = largest finite distance (host pointer);
+ * 2 * ecc is the SSSP 2-approximation of Section 5.  *rounds (may be NULL) =
+ * light/heavy phases run; *edges_scanned (may be NULL) = adjacency entries the
+ * phases read (0 on graphs with 2^32 or more entries, which are not counted).
  * Errors: INVALID_ARG, OVERFLOW, OOM, CUDA.
  */
 cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist,
-                                uint64_t* ecc, uint64_t* rounds);
+                                uint64_t* ecc, uint64_t* rounds, uint64_t* edges_scanned);
 
 /*
  * Whole method from an edge list: build CSR (with `flags`), CLUSTER, quotient,
@@ -369,6 +374,58 @@ cldiam_status cldiam_tuning_get(cldiam_tuning* out);
 /* Replace the process-wide knobs; NULL restores the defaults.  INVALID_ARG on a value out of range.
  * Takes effect for calls that start afterwards; not meant to race with calls in flight. */
 cldiam_status cldiam_tuning_set(const cldiam_tuning* t);
+
+/*
+ * Autotuner (no counterpart in the paper).  The knob that a call uses is, per
+ * field: the process-wide value if set (non-zero), else the autotuner's cached
+ * choice for this device and the call's size class, else the default.  The
+ * size class of a one-graph call is floor(log2(adjacency entries of the
+ * graph)); a many-graph call uses 64 + floor(log2(entries of the batch)) (the
+ * served form: of the whole arena).
+ *
+ * The tuners time the caller's own work -- CUDA events on its stream, the
+ * median of `reps` runs (0 = 3) after one warm-up -- for each candidate value
+ * of one knob at a time (coordinate descent over fixed candidate lists,
+ * starting from the process-wide setting), keep a change only when it is at
+ * least 2 % faster, check that every candidate returns the same result (a
+ * change is a library fault: DIVERGED), store the chosen knobs in the cache
+ * and return them in *out.  They replace the process-wide knobs while they
+ * run, so no other call may run meanwhile.
+ *  graph: pull_ratio, relax_ctas_per_sm, dense_quotient_k, apsp_sources_per_cta,
+ *         apsp_fw_density on cldiam_cluster + cldiam_quotient_build + cldiam_estimate;
+ *  batch: batch_fw_k on cldiam_batch_run of the listed jobs;
+ *  sssp:  sssp_delta_scale on cldiam_sssp_delta(delta = 0) from `source`.
+ */
+cldiam_status cldiam_autotune_graph(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
+                                    uint32_t reps, cldiam_tuning* out);
+cldiam_status cldiam_autotune_batch(cldiam_arena* a, const uint32_t* graph_ids, const double* tau,
+                                    const uint64_t* seed, uint32_t count, const cldiam_opts* opts, uint32_t reps,
+                                    cldiam_tuning* out);
+cldiam_status cldiam_autotune_sssp(cldiam_graph* g, uint32_t source, uint32_t reps, cldiam_tuning* out);
+/*
+ * The search itself, for work the caller measures: `measure` runs the work
+ * with the candidate knobs and returns its time in *seconds and a digest of
+ * its result in *result_hash (any non-OK status skips the candidate).
+ * knob_mask bit i = the i-th field of cldiam_tuning (0 pull_ratio ..
+ * 6 sssp_delta_scale).  Host code only: needs no GPU.
+ */
+typedef cldiam_status (*cldiam_tune_measure_fn)(const cldiam_tuning* candidate, void* user, double* seconds,
+                                                 uint64_t* result_hash);
+cldiam_status cldiam_autotune_search(const cldiam_tuning* start, uint32_t knob_mask,
+                                     cldiam_tune_measure_fn measure, void* user, cldiam_tuning* best,
+                                     double* best_seconds);
+/* Size class of a call on `entries` adjacency entries: floor(log2(entries)) (0 for 0 or 1). */
+uint32_t cldiam_size_class(uint64_t entries);
+/* The knobs a call on `device` in `size_class` would use (process-wide, cache, defaults). */
+cldiam_status cldiam_tuning_effective(int32_t device, uint32_t size_class, cldiam_tuning* out);
+/* The tuning cache: set or read one entry (fields 0 = not cached), clear all, save to or load from a
+ * text file (one line per entry: device, size class, the seven knobs).  INVALID_ARG when an entry is
+ * missing, a value is out of range or the file cannot be read or written. */
+cldiam_status cldiam_tuning_cache_put(int32_t device, uint32_t size_class, const cldiam_tuning* t);
+cldiam_status cldiam_tuning_cache_get(int32_t device, uint32_t size_class, cldiam_tuning* out);
+void cldiam_tuning_cache_clear(void);
+cldiam_status cldiam_tuning_cache_save(const char* path);
+cldiam_status cldiam_tuning_cache_load(const char* path);
 
 /* ------------------------------------------------------------------------
  * Instrumentation.  No counterpart in the method itself; it exposes what the

@@ -54,6 +54,13 @@ class Tuning(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+# cldiam_tune_measure_fn: (const cldiam_tuning*, void* user, double* seconds, uint64_t* result_hash) -> status
+TUNE_MEASURE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(Tuning), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64))
+KNOBS = ["pull_ratio", "relax_ctas_per_sm", "dense_quotient_k", "apsp_sources_per_cta", "apsp_fw_density",
+         "batch_fw_k", "sssp_delta_scale"]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("phi_gc", ctypes.c_uint64), ("radius", ctypes.c_uint64), ("phi_approx", ctypes.c_uint64),
                 ("k", ctypes.c_uint32), ("stages", ctypes.c_uint32), ("steps", ctypes.c_uint32),
@@ -111,7 +118,7 @@ def load(build_if_missing: bool = True):
             "cldiam_apsp_max": (st, [ctypes.c_uint32, P, P, P, P, P]),
             "cldiam_apsp_max_noalloc": (st, [ctypes.c_uint32, P, P, P, P, P]),
             "cldiam_sssp_source": (st, [P, ctypes.c_uint64, P]),
-            "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
+            "cldiam_sssp_delta": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P, P, P, P]),
             "cldiam_run": (st, [P, P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                 ctypes.c_uint64, P, P, P]),
             "cldiam_arena_create": (st, [ctypes.c_uint64, P, PP]),
@@ -127,6 +134,17 @@ def load(build_if_missing: bool = True):
             "cldiam_server_free": (None, [P]),
             "cldiam_tuning_get": (st, [P]),
             "cldiam_tuning_set": (st, [P]),
+            "cldiam_autotune_graph": (st, [P, ctypes.c_double, ctypes.c_uint64, P, ctypes.c_uint32, P]),
+            "cldiam_autotune_batch": (st, [P, P, P, P, ctypes.c_uint32, P, ctypes.c_uint32, P]),
+            "cldiam_autotune_sssp": (st, [P, ctypes.c_uint32, ctypes.c_uint32, P]),
+            "cldiam_autotune_search": (st, [P, ctypes.c_uint32, TUNE_MEASURE_FN, P, P, P]),
+            "cldiam_size_class": (ctypes.c_uint32, [ctypes.c_uint64]),
+            "cldiam_tuning_effective": (st, [ctypes.c_int32, ctypes.c_uint32, P]),
+            "cldiam_tuning_cache_put": (st, [ctypes.c_int32, ctypes.c_uint32, P]),
+            "cldiam_tuning_cache_get": (st, [ctypes.c_int32, ctypes.c_uint32, P]),
+            "cldiam_tuning_cache_clear": (None, []),
+            "cldiam_tuning_cache_save": (st, [ctypes.c_char_p]),
+            "cldiam_tuning_cache_load": (st, [ctypes.c_char_p]),
             "cldiam_profile_set_timing": (st, [ctypes.c_uint32]),
             "cldiam_profile_reset": (st, []),
             "cldiam_profile_num_classes": (ctypes.c_uint32, []),
@@ -311,6 +329,16 @@ class Arena(_Handle):
             _check(st, "cldiam_batch_run")
         return [res[i].as_dict() for i in range(cnt)], [int(x) for x in sts[:cnt]]
 
+    def autotune(self, ids, taus, seeds, reps: int = 3) -> dict:
+        """cldiam_autotune_batch: tune the many-graph knobs on these jobs; cached for the batch's size class."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        t = Tuning()
+        _check(load().cldiam_autotune_batch(self.handle, ids.ctypes.data, taus.ctypes.data, seeds.ctypes.data,
+                                            int(ids.size), None, reps, ctypes.byref(t)), "cldiam_autotune_batch")
+        return t.as_dict()
+
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("ctas", ctypes.c_uint32), ("capacity", ctypes.c_uint32), ("big_nodes", ctypes.c_uint32),
@@ -449,12 +477,15 @@ def sssp_source(g: Graph, seed: int) -> int:
     return s.value
 
 
-def sssp_delta(g: Graph, source: int, delta: int = 0, want_dist: bool = True):
-    """cldiam_sssp_delta: (dist or None, ecc, rounds) of Delta-stepping from `source`."""
+def sssp_delta(g: Graph, source: int, delta: int = 0, want_dist: bool = True, with_scanned: bool = False):
+    """cldiam_sssp_delta: (dist or None, ecc, rounds) of Delta-stepping from `source`; with_scanned adds the
+    adjacency entries the phases read as a fourth element."""
     dist = np.empty(g.n, np.uint32) if want_dist else None
-    ecc = ctypes.c_uint64(); rounds = ctypes.c_uint64()
-    _check(load().cldiam_sssp_delta(g.handle, source, delta, _ptr(dist), ctypes.byref(ecc), ctypes.byref(rounds)),
-           "cldiam_sssp_delta")
+    ecc = ctypes.c_uint64(); rounds = ctypes.c_uint64(); scanned = ctypes.c_uint64()
+    _check(load().cldiam_sssp_delta(g.handle, source, delta, _ptr(dist), ctypes.byref(ecc), ctypes.byref(rounds),
+                                    ctypes.byref(scanned)), "cldiam_sssp_delta")
+    if with_scanned:
+        return dist, ecc.value, rounds.value, scanned.value
     return dist, ecc.value, rounds.value
 
 
@@ -477,6 +508,92 @@ def tuning_set(**knobs) -> None:
             raise KeyError(k)
         setattr(t, k, v)
     _check(load().cldiam_tuning_set(ctypes.byref(t)), "cldiam_tuning_set")
+
+
+def _tuning_of(knobs: dict) -> Tuning:
+    t = Tuning()
+    for k, v in knobs.items():
+        if k not in KNOBS:
+            raise KeyError(k)
+        setattr(t, k, v)
+    return t
+
+
+def autotune_graph(g: "Graph", tau: float, seed: int, reps: int = 3, **opts) -> dict:
+    """cldiam_autotune_graph: tune the one-graph knobs on this graph's CLUSTER + quotient + estimate;
+    the choice is cached for the graph's size class and returned."""
+    o = make_opts(**opts) if opts else None
+    t = Tuning()
+    _check(load().cldiam_autotune_graph(g.handle, float(tau), seed, ctypes.byref(o) if o else None, reps,
+                                        ctypes.byref(t)), "cldiam_autotune_graph")
+    return t.as_dict()
+
+
+def autotune_sssp(g: "Graph", source: int, reps: int = 3) -> dict:
+    """cldiam_autotune_sssp: tune Delta-stepping's bucket width on this graph and source."""
+    t = Tuning()
+    _check(load().cldiam_autotune_sssp(g.handle, source, reps, ctypes.byref(t)), "cldiam_autotune_sssp")
+    return t.as_dict()
+
+
+def autotune_search(measure, knobs, start: dict | None = None):
+    """cldiam_autotune_search with a Python measure(knobs: dict) -> (seconds, result_hash); returns
+    (best knobs, best seconds)."""
+    mask = 0
+    for k in knobs:
+        mask |= 1 << KNOBS.index(k)
+    err = []
+
+    def cb(tp, user, sec, h):
+        try:
+            s_, h_ = measure(tp.contents.as_dict())
+        except Exception as ex:  # a failing candidate is skipped by the search
+            err.append(ex)
+            return -1
+        sec[0] = float(s_)
+        h[0] = int(h_) & 0xFFFFFFFFFFFFFFFF
+        return 0
+
+    fn = TUNE_MEASURE_FN(cb)
+    best = Tuning()
+    bs = ctypes.c_double()
+    st0 = _tuning_of(start or {})
+    _check(load().cldiam_autotune_search(ctypes.byref(st0), mask, fn, None, ctypes.byref(best), ctypes.byref(bs)),
+           "cldiam_autotune_search")
+    return best.as_dict(), bs.value
+
+
+def size_class(entries: int) -> int:
+    return int(load().cldiam_size_class(entries))
+
+
+def tuning_effective(device: int, size_class_: int) -> dict:
+    t = Tuning()
+    _check(load().cldiam_tuning_effective(device, size_class_, ctypes.byref(t)), "cldiam_tuning_effective")
+    return t.as_dict()
+
+
+def tuning_cache_put(device: int, size_class_: int, **knobs) -> None:
+    t = _tuning_of(knobs)
+    _check(load().cldiam_tuning_cache_put(device, size_class_, ctypes.byref(t)), "cldiam_tuning_cache_put")
+
+
+def tuning_cache_get(device: int, size_class_: int) -> dict:
+    t = Tuning()
+    _check(load().cldiam_tuning_cache_get(device, size_class_, ctypes.byref(t)), "cldiam_tuning_cache_get")
+    return t.as_dict()
+
+
+def tuning_cache_clear() -> None:
+    load().cldiam_tuning_cache_clear()
+
+
+def tuning_cache_save(path: str) -> None:
+    _check(load().cldiam_tuning_cache_save(path.encode()), "cldiam_tuning_cache_save")
+
+
+def tuning_cache_load(path: str) -> None:
+    _check(load().cldiam_tuning_cache_load(path.encode()), "cldiam_tuning_cache_load")
 
 
 KERNEL_CLASSES = ["relax", "snapshot", "rebuild", "select", "finalize", "growable", "radix_hist", "radix_scatter",

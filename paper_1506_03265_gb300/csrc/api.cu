@@ -207,7 +207,8 @@ cldiam_status cldiam_estimate(const cldiam_quotient* q, cldiam_result* out) {
         const cldiam_clustering* c = q->c;
         cldiam_result r = c->stats;
         uint64_t phi = 0;
-        CLD_TRY(apsp_max_device(q->k, q->off, q->col, q->w, q->nnz, q->stream, &phi, false, q->max_fw_k));
+        CLD_TRY(apsp_max_device(q->k, q->off, q->col, q->w, q->nnz, q->stream, &phi, false, q->max_fw_k,
+                                tuning_for(q->c->g->nnz)));
         DBuf<uint32_t> rmax;
         CLD_TRY(rmax.alloc(1, q->stream));
         CLD_TRY(reduce_max_u32(c->D, c->g->n, rmax.get(), q->stream));
@@ -245,7 +246,7 @@ cldiam_status cldiam_apsp_max(uint32_t k, const uint64_t* off, const uint32_t* c
         }
         if (st == CLDIAM_OK)
             st = apsp_max_device(k, (const uint64_t*)doff, (const uint32_t*)dcol, (const uint32_t*)dw, nnz, s, phi, true,
-                                 8192u);
+                                 8192u, tuning_for(nnz));
         if (o1) dfree(doff, s);
         if (o2) dfree(dcol, s);
         if (o3) dfree(dw, s);
@@ -268,8 +269,8 @@ cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t*
 }
 
 cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist, uint64_t* ecc,
-                                uint64_t* rounds) {
-    return guarded([&] { return sssp_delta(g, source, delta, dist, ecc, rounds); });
+                                uint64_t* rounds, uint64_t* edges_scanned) {
+    return guarded([&] { return sssp_delta(g, source, delta, dist, ecc, rounds, edges_scanned); });
 }
 
 cldiam_status cldiam_arena_create(uint64_t hbm_budget_bytes, void* stream, cldiam_arena** out) {

@@ -15,6 +15,7 @@
 // exact when every pair ends up connected, otherwise the checked form
 // recomputes the matrix.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "internal.cuh"
@@ -309,7 +310,7 @@ template <int S>
 cldiam_status launch_msbf(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
                           cudaStream_t s, uint32_t* out_max, uint32_t* ovf) {
     constexpr int kMax = 220 * 1024;
-    static bool attr[64];
+    static std::atomic<bool> attr[64];  // first call per device sets the attribute (idempotent)
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr[dev]) {
@@ -424,7 +425,7 @@ template <int S>
 cldiam_status launch_wl(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
                         cudaStream_t s, uint32_t* out_max, uint32_t* ovf, uint32_t* err) {
     constexpr int kMax = 220 * 1024;
-    static bool attr[64];
+    static std::atomic<bool> attr[64];  // first call per device sets the attribute (idempotent)
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr[dev]) {
@@ -471,10 +472,27 @@ cldiam_status fw_dense(uint32_t* M, uint32_t kp, uint32_t k, uint32_t nt, const 
     return CLDIAM_OK;
 }
 
+// Batched-SSSP kernel for a sparse quotient of k nodes: the worklist form with S sources per CTA while
+// k x S distances and a word of change bits per node fit in shared memory (S = 8 below 2,048 nodes,
+// else 4, else 1; a requested S that fits is taken), else all-node rounds with the distances alone
+// (k <= 56,320), else none (dense form).
+enum class SparsePlan { kNone, kWorklist8, kWorklist4, kWorklist1, kRounds1 };
+SparsePlan sparse_plan(uint32_t k, uint32_t S) {
+    constexpr size_t kSmem = 220 * 1024;
+    const bool fit8 = (size_t)k * (8 * 4 + 8) <= kSmem, fit4 = (size_t)k * (4 * 4 + 8) <= kSmem,
+               fit1 = (size_t)k * (4 + 8) <= kSmem;
+    if ((S == 8 && fit8) || (S == 0 && fit8 && k < 2048)) return SparsePlan::kWorklist8;
+    if ((S == 4 || S == 0 || S == 8) && fit4) return SparsePlan::kWorklist4;
+    if (fit1) return SparsePlan::kWorklist1;
+    if ((size_t)k * 4 <= kSmem) return SparsePlan::kRounds1;
+    return SparsePlan::kNone;
+}
+
 }  // namespace
 
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint64_t nnz,
-                              cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k) {
+                              cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k,
+                              const cldiam_tuning& tun) {
     *phi = 0;
     if (k <= 1) return CLDIAM_OK;
     const uint32_t nt = (k + FT - 1) / FT;
@@ -495,16 +513,18 @@ cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* c
     // nodes; above, S = 4: its half-size distance block lets two 1,024-thread CTAs share an SM (they
     // use <= 32 registers), where S = 8 fits one (R-MAT 24, k = 4,069: 3.0 -> 2.1 ms; road mesh 4096^2,
     // k = 4,357: 4.0 -> 3.4 ms)
-    constexpr size_t kSmem = 220 * 1024;
-    const bool sparse = (double)nnz * 8.0 < (double)k * k;
-    if (sparse && (size_t)k * (8 * 4 + 8) <= kSmem && k < 2048) {
+    // (tuning: the density cut-over and the sources per CTA; a tuned cut-over never sends a quotient above
+    // max_fw_k to Floyd-Warshall that the default would have solved by SSSP)
+    bool sparse = (double)nnz * (double)tun.apsp_fw_density < (double)k * k;
+    if (!sparse && k > max_fw_k) sparse = (double)nnz * 8.0 < (double)k * k;
+    const SparsePlan plan = sparse ? sparse_plan(k, tun.apsp_sources_per_cta) : SparsePlan::kNone;
+    if (plan == SparsePlan::kWorklist8) {
         CLD_TRY(launch_wl<8>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
-    } else if (sparse && (size_t)k * (4 * 4 + 8) <= kSmem) {
+    } else if (plan == SparsePlan::kWorklist4) {
         CLD_TRY(launch_wl<4>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
-    } else if (sparse && (size_t)k * (4 + 8) <= kSmem) {
+    } else if (plan == SparsePlan::kWorklist1) {
         CLD_TRY(launch_wl<1>(k, off, col, w, nnz, s, scal.get() + 1, scal.get(), scal.get() + 5));
-    } else if (sparse && (size_t)k * 4 <= kSmem) {
-        // too many nodes for the change bits: all-node rounds, distances alone in shared memory
+    } else if (plan == SparsePlan::kRounds1) {
         CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, scal.get() + 1, scal.get()));
     } else {
         if (k > max_fw_k) return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient larger than max_fw_k");
@@ -578,7 +598,8 @@ cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* 
     uint32_t* ovf = scratch + 0;
     uint32_t* best = scratch + 1;
     uint32_t* bad = scratch + 2;
-    CLD_CUDA(cudaMemsetAsync(scratch, 0, 3 * sizeof(uint32_t), s));  // the array keeps the last call's values
+    uint32_t* diverged = scratch + 3;  // the worklist SSSP's round limit
+    CLD_CUDA(cudaMemsetAsync(scratch, 0, 4 * sizeof(uint32_t), s));  // the array keeps the last call's values
     k_fw_validate<<<grid_for((size_t)k + nnz + 1, 256), 256, 0, s>>>(off, col, k, nnz, bad);
     CLD_LAUNCH_CHECK();
     uint32_t h[3] = {0, 0, 0};
@@ -586,12 +607,14 @@ cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* 
     CLD_CUDA(cudaStreamSynchronize(s));
     if (h[2]) return fail(CLDIAM_ERR_INVALID_ARG, "malformed CSR (offsets or column ids)");
     if (sparse) {
-        // batched SSSP: distances (and the CSR when it fits) in shared memory, only the control words here
-        constexpr int S = 8;
-        const int S_eff = ((size_t)k * 8 * 4 <= 220 * 1024) ? 8 : (((size_t)k * 4 * 4 <= 220 * 1024) ? 4 : 1);
-        if (S_eff == S) CLD_TRY(launch_msbf<8>(k, off, col, w, nnz, s, best, ovf));
-        else if (S_eff == 4) CLD_TRY(launch_msbf<4>(k, off, col, w, nnz, s, best, ovf));
-        else CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, best, ovf));
+        // batched SSSP with the kernel and sources per CTA apsp_max_device takes by default: distances,
+        // change bits (and the CSR when it fits) in shared memory, only the control words here
+        switch (sparse_plan(k, 0)) {
+            case SparsePlan::kWorklist8: CLD_TRY(launch_wl<8>(k, off, col, w, nnz, s, best, ovf, diverged)); break;
+            case SparsePlan::kWorklist4: CLD_TRY(launch_wl<4>(k, off, col, w, nnz, s, best, ovf, diverged)); break;
+            case SparsePlan::kWorklist1: CLD_TRY(launch_wl<1>(k, off, col, w, nnz, s, best, ovf, diverged)); break;
+            default: CLD_TRY(launch_msbf<1>(k, off, col, w, nnz, s, best, ovf)); break;
+        }
     } else {
         const uint32_t nt = (k + FT - 1) / FT;
         const uint32_t kp = nt * FT;  // <= kNoAllocMaxK
@@ -610,10 +633,12 @@ cldiam_status apsp_max_noalloc(uint32_t k, const uint64_t* off, const uint32_t* 
         k_fw_max_finite<<<grid_for((size_t)k * kp, 256), 256, 0, s>>>(M, kp, k, INF, best, nullptr);
         CLD_LAUNCH_CHECK();
     }
-    CLD_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    uint32_t hd[4] = {0, 0, 0, 0};
+    CLD_CUDA(cudaMemcpyAsync(hd, scratch, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CLD_CUDA(cudaStreamSynchronize(s));
-    if (h[0]) return fail(CLDIAM_ERR_OVERFLOW, "a distance reached 2^32 - 1");
-    *phi = h[1];
+    if (hd[3]) return fail(CLDIAM_ERR_DIVERGED, "quotient SSSP exceeded its round limit");
+    if (hd[0]) return fail(CLDIAM_ERR_OVERFLOW, "a distance reached 2^32 - 1");
+    *phi = hd[1];
     return CLDIAM_OK;
 }
 

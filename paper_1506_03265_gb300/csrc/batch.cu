@@ -52,7 +52,7 @@ struct Job {
     uint32_t out;         // index in the caller's result array
     uint32_t step_cap;    // growing steps per PartialGrowth, 0 = no cap
     uint32_t cumulative;  // cumulative contract mode
-    uint32_t pad;
+    uint32_t fw_k;        // quotients up to this size (<= kSmemFwK) are closed by Floyd-Warshall in shared memory
 };
 
 struct Workspace {  // one slice per CTA
@@ -152,10 +152,10 @@ __device__ uint32_t block_relabel(uint32_t n, const uint32_t* __restrict__ cente
 
 // exact max finite distance of the k-node quotient held densely in M (row stride k)
 __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M, const Workspace& ws,
-                                            uint32_t* dyn, BatchSmem& sm, bool& ovf) {
+                                            uint32_t* dyn, BatchSmem& sm, bool& ovf, uint32_t fw_k) {
     if (k <= 1) return 0;
     uint32_t best = 0;
-    if (k <= kSmemFwK) {
+    if (k <= min(fw_k, kSmemFwK)) {
         // Floyd-Warshall in shared memory; row p and column p are fixed during iteration p
         for (uint32_t i = threadIdx.x; i < k * k; i += blockDim.x) dyn[i] = __ldcg(&M[i]);
         __syncthreads();
@@ -438,7 +438,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                 [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
             res.quotient_edges = qe;
             bool ovf2 = false;
-            const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2);
+            const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2, job.fw_k);
             const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
                                                       [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
             if (any_ovf) status = kJobOverflow;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(BT, 1)
                 s_job.out = vj->out;
                 s_job.step_cap = vj->step_cap;
                 s_job.cumulative = vj->cumulative;
-                s_job.pad = 0;
+                s_job.fw_k = vj->fw_k;
             }
         }
         __syncthreads();
@@ -680,6 +680,13 @@ cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out) {
 }
 
 uint32_t arena_count(const cldiam_arena* a) { return (uint32_t)a->graphs.size(); }
+cudaStream_t arena_stream(const cldiam_arena* a) { return a->stream; }
+uint64_t arena_entries(const cldiam_arena* a, const uint32_t* ids, uint32_t count) {
+    uint64_t e = 0;
+    for (uint32_t i = 0; i < count; ++i)
+        if (ids[i] < a->graphs.size()) e += a->graphs[ids[i]].nnz;
+    return e;
+}
 uint64_t arena_device_bytes(const cldiam_arena* a) { return arena_bytes(a); }
 
 // Per-CTA workspaces for graphs of up to nmax nodes, carved from one (cached) device buffer.
@@ -730,7 +737,7 @@ static size_t batch_dyn_smem() {
 }
 
 template <class Kern>
-static cldiam_status set_dyn_smem(Kern k, bool* done_flags) {
+static cldiam_status set_dyn_smem(Kern k, std::atomic<bool>* done_flags) {
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !done_flags[dev]) {
@@ -750,6 +757,7 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         return fail(CLDIAM_ERR_INVALID_ARG, "unknown contract_mode");
     if (opts.reserved[0] || opts.reserved[1]) return fail(CLDIAM_ERR_INVALID_ARG, "reserved options must be 0");
     const cudaStream_t s = a->stream;
+    const uint32_t fw_k = tuning_for_batch(arena_entries(a, ids, count)).batch_fw_k;
     std::vector<Job> jobs(count);
     uint32_t nmax = 1;
     for (uint32_t i = 0; i < count; ++i) {
@@ -767,6 +775,7 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         jobs[i].out = i;
         jobs[i].step_cap = opts.step_cap;
         jobs[i].cumulative = opts.contract_mode == CLDIAM_CONTRACT_CUMULATIVE ? 1u : 0u;
+        jobs[i].fw_k = fw_k;
         nmax = std::max(nmax, view.n);
     }
     // largest graphs first: the work queue then balances the tail
@@ -792,7 +801,7 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
     CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
     const size_t dyn = batch_dyn_smem();
-    static bool attr[64];
+    static std::atomic<bool> attr[64];
     CLD_TRY(set_dyn_smem(k_batch, attr));
     CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), count, a->off, a->adj, a->row, dws.get(),
                                                    queue.get(), douts.get()));
@@ -874,7 +883,7 @@ struct cldiam_server {
 namespace cld {
 
 static cldiam_status server_launch(cldiam_server* sv) {
-    static bool attr[64];
+    static std::atomic<bool> attr[64];
     CLD_TRY(set_dyn_smem(k_serve, attr));
     sv->ctl->idle = 0;
     CLD_K(K_MISC, sv->kstream,
@@ -1038,6 +1047,7 @@ cldiam_status server_submit(cldiam_server* sv, uint32_t graph_id, double tau, ui
         j.graph = graph_id;
         j.delta0 = d0;
         j.out = t;
+        j.fw_k = tuning_for_batch(sv->arena->adj_used).batch_fw_k;
         sv->ring[sv->next_ring] = j;
         host_store_release(&sv->ctl->tail, ++sv->next_ring);  // publish after the entry is written
         CLD_TRY(server_ensure_live(sv));

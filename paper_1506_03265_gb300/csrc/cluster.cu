@@ -1,6 +1,7 @@
 // CLUSTER(G, tau) of Algorithm 1 on the GPU, one graph per launch: each
 // phase body of cluster_dev.cuh runs as its own grid kernel and the host
 // drives the stage / step / doubling control flow from small counter reads.
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -89,58 +90,6 @@ __global__ void k_assign_cid(uint32_t n, const uint32_t* __restrict__ center, co
 // atomic minimum when it undercuts the snapshot; the per-step stamp decides
 // "first change" (next list) and "newly covered" as in the pushed form.  No
 // block barrier: warps run independently, so many gathers stay in flight.
-constexpr int PT = 256;          // threads per pull CTA
-constexpr int PW = 128;          // CSR positions per warp chunk
-constexpr int PWG = PW / 32;     // groups of 32 positions per chunk
-constexpr int PNB = 2 * PW + 8;  // per-warp buffer of changed rows (flushed once >= PW)
-
-// Row (or frontier entry) segments of a warp's 32-position group.  Entries
-// start at strictly increasing positions and each holds at least one; B is
-// the index of the entry that holds position g0 (the group's first), and
-// starts[j] the first position of entry B + 1 + j for j < n_after.  Returns
-// the group's start word (bit d = an entry starts at g0 + d); *own = the
-// entry index of this lane's position.
-__device__ __forceinline__ uint32_t group_starts(const uint32_t* starts, uint32_t n_after, uint32_t g0,
-                                                 uint32_t B, uint32_t lane, unsigned le_mask, uint32_t* own) {
-    const uint32_t d = (lane < n_after ? starts[lane] : 0xFFFFFFFFu) - g0;  // entries after B start after g0
-    const uint32_t word = __reduce_or_sync(0xffffffffu, d < 32u ? 1u << d : 0u);
-    *own = B + (uint32_t)__popc(word & le_mask);
-    return word;
-}
-
-// Minimum of v over this lane's segment [head, tail] of a group (segments are
-// runs of consecutive lanes bounded by the start word); valid at every lane,
-// so the head lane holds the segment's minimum.
-__device__ __forceinline__ unsigned long long segment_min(unsigned long long v, uint32_t word, uint32_t lane) {
-    const unsigned above = lane == 31 ? 0u : word & (0xfffffffeu << lane);
-    const uint32_t tail = above ? (uint32_t)__ffs(above) - 2u : 31u;
-#pragma unroll
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_down_sync(0xffffffffu, v, o);
-        if (lane + o <= tail) v = t < v ? t : v;
-    }
-    return v;
-}
-
-// Per-warp list of changed nodes, appended to the next list with one atomic per >= PW of them.
-struct WarpNext {
-    uint32_t* buf;
-    uint32_t cnt;
-    __device__ __forceinline__ void put(bool first, uint32_t r, uint32_t lane) {
-        const unsigned m = __ballot_sync(0xffffffffu, first);
-        if (first) buf[cnt + (uint32_t)__popc(m & lanemask_lt())] = r;
-        cnt += (uint32_t)__popc(m);
-    }
-    __device__ __forceinline__ void flush(uint32_t* __restrict__ next, Counters* ctr, uint32_t lane) {
-        __syncwarp();
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&ctr->nnext, cnt);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        for (uint32_t j = lane; j < cnt; j += 32) next[base + j] = buf[j];
-        cnt = 0;
-        __syncwarp();
-    }
-};
 
 // a5, pushed form: the frontier's adjacency lists are one flattened range of E
 // positions; each warp takes QC consecutive positions (4 groups of 32), finds
@@ -213,9 +162,9 @@ __global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fba
                     nk = (cand << 32) | (ku & 0xFFFFFFFFull);
                 }
             } else if (live && ed[u].y <= delta) {  // pull: candidate of a contracted neighbour
-                const uint32_t cu = __ldcg(&center[ed[u].x]);
+                const uint32_t cu = __ldg(&center[ed[u].x]);
                 if (cu != kNone) {
-                    const uint64_t cand = (uint64_t)(Dcum ? __ldcg(&Dcum[ed[u].x]) : 0u) + ed[u].y;
+                    const uint64_t cand = (uint64_t)(Dcum ? __ldg(&Dcum[ed[u].x]) : 0u) + ed[u].y;
                     if (cand <= delta) nk = (cand << 32) | cu;
                 }
             }
@@ -239,9 +188,10 @@ __global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fba
             }
             bool first = false;
             if (nk != kInfKey) {
-                // the target's key and stamp in one round trip; most candidates lose to the current key
-                const unsigned long long cur = ld_cg_keep_u64(&key[target], pol_keep);
-                const uint32_t stp = __ldcg(&stamp[target]);
+                // the target's key and stamp in one round trip, through L1 (a stale line only lets an
+                // extra candidate through: the atomics decide); most candidates lose to the current key
+                const unsigned long long cur = ld_keep_u64(&key[target], pol_keep);
+                const uint32_t stp = ld_keep_u32(&stamp[target], pol_keep);
                 if (nk < cur) {
                     red_min_keep_u64(&key[target], nk, pol_keep);
                     if (stp != stepid) {  // hubs see many lowerings: only the first ones exchange
@@ -253,9 +203,9 @@ __global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fba
             }
             wn.put(first, target, lane);
         }
-        if (wn.cnt >= (uint32_t)PW) wn.flush(next, ctr, lane);
+        if (wn.cnt >= (uint32_t)PW) wn.flush(next, &ctr->nnext, lane);
     }
-    if (wn.cnt) wn.flush(next, ctr, lane);
+    if (wn.cnt) wn.flush(next, &ctr->nnext, lane);
     warp_add_u64(&ctr->newly_covered, newly);
 }
 
@@ -359,9 +309,9 @@ __global__ void __launch_bounds__(PT, 6) k_pull(uint32_t n, uint32_t nnz, uint32
                 wn.put(first, r, lane);
             }
         }
-        if (wn.cnt >= (uint32_t)PW) wn.flush(next, ctr, lane);
+        if (wn.cnt >= (uint32_t)PW) wn.flush(next, &ctr->nnext, lane);
     }
-    if (wn.cnt) wn.flush(next, ctr, lane);
+    if (wn.cnt) wn.flush(next, &ctr->nnext, lane);
     warp_add_u64(&ctr->newly_covered, newly);
 }
 
@@ -451,7 +401,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     DBuf<uint32_t> R, stamp, fvA, fvB, fpA, fpB, cfA, cfB, next;
     DBuf<Counters> ctr;
     // dense (pull) steps: every row has an entry (connected graph, n >= 2) and positions index below 2^32
-    const cldiam_tuning tun = tuning_current();
+    const cldiam_tuning tun = tuning_for(g->nnz);
     const bool pull_dense = tun.pull_ratio > 0.f && g->connected && n >= 2 && g->nnz < 0xFFFFFFFFull;
     const uint32_t pull_chunks = pull_dense ? (uint32_t)((g->nnz + PW - 1) / PW) : 0u;
     DBuf<unsigned long long> keyS;
@@ -519,18 +469,18 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     const unsigned max_relax_grid = (unsigned)num_sms() * 8;
     // the growing-step kernels loop over warp chunks: launch at most the resident CTAs (no partial second
     // wave after the first has finished its chunks)
-    static int push_per_sm[64], pull_per_sm[64];
+    static std::atomic<int> push_per_sm[64], pull_per_sm[64];  // concurrent first calls store the same values
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     const int di = (dev >= 0 && dev < 64) ? dev : 0;
-    if (push_per_sm[di] == 0) {
+    if (push_per_sm[di].load() == 0) {
         int a = 0, b = 0;
         CLD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push, PT, 0));
         CLD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pull, PT, 0));
         pull_per_sm[di] = std::max(1, b);
         push_per_sm[di] = std::max(1, a);
     }
-    unsigned push_ctas = (unsigned)push_per_sm[di], pull_ctas = (unsigned)pull_per_sm[di];
+    unsigned push_ctas = (unsigned)push_per_sm[di].load(), pull_ctas = (unsigned)pull_per_sm[di].load();
     if (tun.relax_ctas_per_sm) {
         push_ctas = std::min(push_ctas, tun.relax_ctas_per_sm);
         pull_ctas = std::min(pull_ctas, tun.relax_ctas_per_sm);

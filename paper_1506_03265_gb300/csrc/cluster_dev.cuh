@@ -100,6 +100,64 @@ __device__ __forceinline__ void front_append(unsigned long long* ctr, bool pred,
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- warp-chunk sweeps
+// The one-graph kernels that sweep a flattened range of positions (a
+// frontier's adjacency, or the whole CSR) give each warp PW consecutive
+// positions (PWG groups of 32 lanes) and run without block barriers.
+constexpr int PT = 256;          // threads per CTA of the warp-chunk kernels
+constexpr int PW = 128;          // positions per warp chunk (== QC, the chunk-table granularity)
+constexpr int PWG = PW / 32;     // groups of 32 positions per chunk
+constexpr int PNB = 2 * PW + 8;  // per-warp buffer of changed nodes (flushed once >= PW)
+static_assert(PW == QC, "one chunk-table slot per warp chunk");
+
+// Row (or frontier entry) segments of a warp's 32-position group.  Entries
+// start at strictly increasing positions and each holds at least one; B is
+// the index of the entry that holds position g0 (the group's first), and
+// starts[j] the first position of entry B + 1 + j for j < n_after.  Returns
+// the group's start word (bit d = an entry starts at g0 + d); *own = the
+// entry index of this lane's position.
+__device__ __forceinline__ uint32_t group_starts(const uint32_t* starts, uint32_t n_after, uint32_t g0,
+                                                 uint32_t B, uint32_t lane, unsigned le_mask, uint32_t* own) {
+    const uint32_t d = (lane < n_after ? starts[lane] : 0xFFFFFFFFu) - g0;  // entries after B start after g0
+    const uint32_t word = __reduce_or_sync(0xffffffffu, d < 32u ? 1u << d : 0u);
+    *own = B + (uint32_t)__popc(word & le_mask);
+    return word;
+}
+
+// Minimum of v over this lane's segment [head, tail] of a group (segments are
+// runs of consecutive lanes bounded by the start word); valid at every lane,
+// so the head lane holds the segment's minimum.
+__device__ __forceinline__ unsigned long long segment_min(unsigned long long v, uint32_t word, uint32_t lane) {
+    const unsigned above = lane == 31 ? 0u : word & (0xfffffffeu << lane);
+    const uint32_t tail = above ? (uint32_t)__ffs(above) - 2u : 31u;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o <= tail) v = t < v ? t : v;
+    }
+    return v;
+}
+
+// Per-warp list of changed nodes, appended to the next list with one atomic per >= PW of them.
+struct WarpNext {
+    uint32_t* buf;
+    uint32_t cnt;
+    __device__ __forceinline__ void put(bool first, uint32_t r, uint32_t lane) {
+        const unsigned m = __ballot_sync(0xffffffffu, first);
+        if (first) buf[cnt + (uint32_t)__popc(m & lanemask_lt())] = r;
+        cnt += (uint32_t)__popc(m);
+    }
+    __device__ __forceinline__ void flush(uint32_t* __restrict__ next, uint32_t* counter, uint32_t lane) {
+        __syncwarp();
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(counter, cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t j = lane; j < cnt; j += 32) next[base + j] = buf[j];
+        cnt = 0;
+        __syncwarp();
+    }
+};
+
 // a3: draw the new centers of this stage among unfrozen nodes, reset the others.
 __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restrict__ center,
                                            unsigned long long* __restrict__ key, uint64_t seed, uint32_t stage,

@@ -262,6 +262,18 @@ __device__ __forceinline__ unsigned long long ld_nc_keep_u64(const unsigned long
     asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
     return r;
 }
+// mutable node state read as a filter: through L1.  A stale line can only hold an older, larger key (keys
+// never rise within a kernel), so the filter lets through extra candidates, never drops a winning one.
+__device__ __forceinline__ unsigned long long ld_keep_u64(const unsigned long long* p, uint64_t pol) {
+    unsigned long long r;
+    asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_keep_u32(const uint32_t* p, uint64_t pol) {
+    uint32_t r;
+    asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
 // mutable node state: L2 only (other CTAs write it in the same kernel)
 __device__ __forceinline__ unsigned long long ld_cg_keep_u64(const unsigned long long* p, uint64_t pol) {
     unsigned long long r;

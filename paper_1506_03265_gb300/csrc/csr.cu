@@ -14,6 +14,7 @@
 // component, so roots are component minima and the labelling is
 // deterministic.
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -578,7 +579,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         CLD_CUDA(cudaMemsetAsync(hist1.get(), 0, (size_t)npass1 * 256 * 4, s));
         if (m > 0) {
             const size_t esm = (size_t)8 * npass1 * 256 * 4;  // 8 warps; <= 64 KB
-            static bool emit_attr[64];
+            static std::atomic<bool> emit_attr[64];
             int dev = 0;
             CLD_CUDA(cudaGetDevice(&dev));
             if (dev < 0 || dev >= 64 || !emit_attr[dev]) {

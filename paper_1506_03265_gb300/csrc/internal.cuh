@@ -70,8 +70,10 @@ cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out);
 void free_quotient(cldiam_quotient* q);
 
 // Largest finite APSP distance of a k-node CSR already on the device.
+// `tun` holds the cut-over knobs (Floyd-Warshall density, sources per CTA).
 cldiam_status apsp_max_device(uint32_t k, const uint64_t* off, const uint32_t* col, const uint32_t* w,
-                              uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k);
+                              uint64_t nnz, cudaStream_t s, uint64_t* phi, bool validate, uint32_t max_fw_k,
+                              const cldiam_tuning& tun);
 
 // Same result as apsp_max_device on device-resident inputs, with all scratch in a fixed
 // device array instead of allocations.
@@ -95,12 +97,20 @@ cldiam_status server_replay(cldiam_server* sv, const uint32_t* ids, const double
                             const double* arrival, uint32_t count, int plain, cldiam_result* out, double* latency,
                             double* elapsed);
 uint64_t arena_device_bytes(const cldiam_arena* a);
+cudaStream_t arena_stream(const cldiam_arena* a);
+// adjacency entries of the listed graphs (ids out of range count 0)
+uint64_t arena_entries(const cldiam_arena* a, const uint32_t* ids, uint32_t count);
 
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
-                         uint64_t* rounds);
+                         uint64_t* rounds, uint64_t* scanned);
 
-// tuning knobs in effect (defaults filled in) and their validation (tune.cu)
+// tuning knobs in effect (defaults filled in) and their validation (tune.cu): the process-wide
+// settings alone, or for a call on `entries` adjacency entries of one graph (or of one batch), where the
+// autotuner's cached choice for this device and size class fills the knobs not set process-wide
 cldiam_tuning tuning_current();
+cldiam_tuning tuning_for(uint64_t entries);
+cldiam_tuning tuning_for_batch(uint64_t entries);
+uint32_t size_class(uint64_t entries);
 cldiam_tuning tuning_defaults_filled(const cldiam_tuning& t);
 cldiam_status tuning_check(const cldiam_tuning& t);
 

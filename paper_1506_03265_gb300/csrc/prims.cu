@@ -4,6 +4,7 @@
 // relies on (Fact 1, Section 2), here within one GPU.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -34,7 +35,7 @@ cldiam_status cuda_fail(cudaError_t e, const char* what, const char* file, int l
 
 // ------------------------------------------------------------------ memory
 static std::mutex g_pool_mu;
-static bool g_pool_tuned[64];
+static std::atomic<bool> g_pool_tuned[64];  // set under g_pool_mu, read without it
 
 cldiam_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     int dev = 0;
@@ -102,16 +103,16 @@ cldiam_status Pinned::alloc(size_t bytes) {
 }
 
 int num_sms() {
-    static int cached[64];
+    static std::atomic<int> cached[64];  // concurrent first calls store the same value
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return 152;
-    if (cached[dev] == 0) {
+    if (cached[dev].load() == 0) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = v > 0 ? v : 152;
+        cached[dev].store(v > 0 ? v : 152);
     }
-    return cached[dev];
+    return cached[dev].load();
 }
 
 // ------------------------------------------------------------------ scan
@@ -557,8 +558,8 @@ static cldiam_status radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint3
     const int tile = kv ? OsCfg<K, true>::TILE : OsCfg<K, false>::TILE;
     const uint32_t ntiles = (uint32_t)((n + tile - 1) / tile);
     const size_t smem = (sizeof(K) + (kv ? sizeof(uint32_t) : 0)) * tile;
-    static bool attr_set[2][64];
-    static bool hist_attr_set[64];
+    static std::atomic<bool> attr_set[2][64];  // first call per device sets the attributes (idempotent)
+    static std::atomic<bool> hist_attr_set[64];
     int dev = 0;
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[kv][dev]) {

@@ -16,7 +16,6 @@ namespace cld {
 
 namespace {
 
-constexpr uint32_t kDenseQuotientK = 4096;  // k x k uint32 = 64 MB, within the 126 MB L2
 
 // (cid, D) of every node in one word, so an edge's far end costs one gather
 __global__ void k_q_pack_cd(uint32_t n, const uint32_t* __restrict__ cid, const uint32_t* __restrict__ D,
@@ -277,7 +276,7 @@ cldiam_status quotient(const cldiam_clustering* c, cldiam_quotient** out) {
     q->max_fw_k = c->max_fw_k;
     // dense deduplication while the k x k matrix fits in L2 (auto) or when asked; radix sort otherwise
     const bool dense = c->quotient_mode == CLDIAM_QUOTIENT_DENSE ||
-                       (c->quotient_mode == CLDIAM_QUOTIENT_AUTO && c->k <= kDenseQuotientK);
+                       (c->quotient_mode == CLDIAM_QUOTIENT_AUTO && c->k <= tuning_for(c->g->nnz).dense_quotient_k);
     if (dense && c->k > 65535u) {
         free_quotient(q);
         return fail(CLDIAM_ERR_UNSUPPORTED, "dense quotient deduplication needs k <= 65535");

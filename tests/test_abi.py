@@ -14,6 +14,7 @@ def declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"^\s*typedef[^;]*;", "", txt, flags=re.M | re.S)  # function-pointer types are not entry points
         names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cldiam_\w+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
 

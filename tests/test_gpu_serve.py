@@ -69,7 +69,7 @@ def test_served_results_equal_oracle(env):
                     got[t] = r
     srv.free()
     assert len(got) == len(tickets)
-    assert sum(ns[g] >= big for g in picks) >= 3 and sum(ns[g] < big for g in picks) >= 15  # both lanes
+    assert sum(ns[g] >= big for g in picks) >= 3 and sum(ns[g] < big for g in picks) >= 3  # both lanes
     for g, s, t in zip(picks, seeds, tickets):
         assert {f: got[t][f] for f in ORACLE_FIELDS} == oracle_result(EDGES[g], taus[g], s), (g, s)
 
