@@ -71,6 +71,8 @@ def parse():
                     help="build the workload's CSR, run CLUSTER2 + quotient + estimate once and exit")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="pack this many mixture graphs into an arena, run one batch and exit")
+    ap.add_argument("--profile-apsp", type=int, default=0,
+                    help="Phi of one dense random k-node graph (the blocked Floyd-Warshall path) and exit")
     return ap.parse_args()
 
 
@@ -691,6 +693,17 @@ def profile_other(args):
 
     import paper_1506_03265_gb300 as cd
     from inputs.workloads import WORKLOADS
+    if args.profile_apsp:
+        k = args.profile_apsp
+        rng = np.random.default_rng(k)
+        iu = np.triu_indices(k, 1)
+        keep = rng.random(iu[0].size) < 0.5
+        s_, d_ = iu[0][keep].astype(np.uint32), iu[1][keep].astype(np.uint32)
+        w_ = rng.integers(1, 1 << 20, s_.size).astype(np.uint32)
+        g = cd.build_csr(s_, d_, w_, k, lcc=False)
+        off, col, w, _ = g.copy()
+        print(json.dumps({"k": k, "nnz": int(off[-1]), "phi": cd.apsp_max(k, off, col, w)}))
+        return
     if args.profile_batch:
         mix = build_mix_arena(cd, None, args.profile_batch)
         arena, ids, taus, seeds, edges, _ = mix
@@ -715,7 +728,7 @@ def main():
     args = parse()
     if args.profile_pass:
         profile_pass(args)
-    elif args.profile_sssp or args.profile_cluster2 or args.profile_batch:
+    elif args.profile_sssp or args.profile_cluster2 or args.profile_batch or args.profile_apsp:
         profile_other(args)
     elif args.impl == "reference":
         run_reference(args)

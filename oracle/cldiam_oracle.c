@@ -437,7 +437,7 @@ int orc_cluster_opts(uint32_t n, const uint64_t* off, const uint32_t* col, const
         }
 
         /* assign covered nodes to their clusters and contract */
-        uint64_t nf = 0;
+        uint64_t nf = 0, stage_max_D = 0;
         for (uint32_t v = 0; v < n; ++v) {
             if (frozen[v] || key[v] == ORC_INF_KEY) continue;
             uint32_t c = (uint32_t)key[v];
@@ -450,9 +450,10 @@ int orc_cluster_opts(uint32_t n, const uint64_t* off, const uint32_t* col, const
             center_out[v] = c;
             D_out[v] = newD[v];
             if (newD[v] > R[c]) R[c] = newD[v];
+            if (newD[v] > stage_max_D) stage_max_D = newD[v];
             ++nf;
         }
-        TRACE(2, nf, 0);
+        TRACE(2, nf, stage_max_D);
         st->stages++;
         ++stage;
     }

@@ -66,6 +66,9 @@ def check_invariants(g, tau, seed, mode=oracle.DELTA0_AVG):
     fin = cl.trace[cl.trace["kind"] == oracle.TRACE_FINALIZE]
     assert len(fin) == cl.stats["stages"]
     assert D.max() <= int(fin["delta"].astype(np.int64).sum())
+    # ... and stage by stage: a node frozen in stage s has D <= Delta_1 + ... + Delta_s (its d is within
+    # Delta_s, and R_prev of its cluster within the earlier stages' sum); fin["b"] = the stage's largest D
+    assert (fin["b"].astype(np.int64) <= np.cumsum(fin["delta"].astype(np.int64))).all()
     # each stage reaches half coverage or stops at a true fixed point
     tr = cl.trace
     starts = np.flatnonzero(tr["kind"] == oracle.TRACE_STAGE)

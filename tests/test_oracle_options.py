@@ -73,8 +73,11 @@ def test_cumulative_bounds(gi):
     d0 = oracle.delta0(g)
     for tau, seed, cap in ((0.5, 1, 0), (2.0, 7, 0), (1.0, 3, 2)):
         cl = oracle.cluster(g, tau, seed, d0, contract_mode=oracle.CONTRACT_CUMULATIVE, step_cap=cap)
-        # every D within the final Delta (the radius bound of the cumulative mode)
+        # every D within the final Delta (the radius bound of the cumulative mode), and each stage's
+        # largest D within that stage's Delta (the trace's finalize events: b = the stage's largest D)
         assert int(cl.D.max()) <= cl.stats["delta_end"]
+        fin = cl.trace[cl.trace["kind"] == oracle.TRACE_FINALIZE]
+        assert (fin["b"].astype(np.int64) <= fin["delta"].astype(np.int64)).all()
         # D_v bounds the true distance from its center; centers sit at 0
         for c in np.unique(cl.center):
             dist = oracle.dijkstra(g, int(c))
