@@ -508,12 +508,18 @@ def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None)
         "roofline": roofline_of(prof, [dominant], peak, peaks, name),
         "relax_roofline": dict(
             roofline_of(prof, list(RELAX_CLASSES), peak, peaks, name, tkey="relax_steps"),
+            traffic_note=("per form below (ncu, one launch, R-MAT 20 only); no full-size capture of R-MAT 24 "
+                          "(multi-metric captures stay at R-MAT 20 or smaller)"),
             what=("both forms of the Delta-growing step (pushed relax and dense relax_pull) over the timed "
                   "steps: algorithmic bytes = 16 B per adjacency entry a launch reads + per-entry/row/changed-"
                   "node terms (DESIGN.md section 6) / CUDA-event time"),
             ms_per_step=round(relax_ms, 4),
             forms={c: {"launches": prof[c]["launches"], "ms": round(prof[c]["ms"] / steps, 4),
-                       "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9, 1) if prof[c]["ms"] else None}
+                       "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9, 1) if prof[c]["ms"] else None,
+                       "frac": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9 / peak, 4) if prof[c]["ms"]
+                       else None,
+                       "alg_bytes_per_launch": round(prof[c]["bytes"] / max(1, prof[c]["launches"])),
+                       "traffic": stored_traffic(name, c)}
                    for c in RELAX_CLASSES},
             edges_scanned_per_step=scanned,
             scanned_16B_gbs=round(16.0 * scanned / (relax_ms * 1e-3) / 1e9, 1) if relax_ms else None,
