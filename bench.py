@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GTEPS and graphs/sec (batched+served vs plain) at bit-exact; HBM % peak; p99 ms"
 SAMPLE_SCALE = 17  # CPU oracle sample: R-MAT scale 17 with the rmat20 recipe
+BASE_TUNING = {}  # --tuning: process-wide knobs for the whole run
 
 
 def parse():
@@ -55,6 +56,8 @@ def parse():
                     help="other single-graph workloads timed the same way on the same line ('' = none)")
     ap.add_argument("--secondary-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="process-wide tuning knobs for the whole run, e.g. pull_ratio=0.5,relax_ctas_per_sm=4")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the many-graph leg")
     ap.add_argument("--batched-count", type=int, default=2000)
@@ -258,6 +261,42 @@ def batched_leg(cd, stream, mix, sample_every, reps=3, dist=None, total_count=No
     t_batch = e0.elapsed_time(e1) / 1e3 / reps
     launches = sum(v["launches"] for v in cd.profile_get().values()) / reps
     assert res2 == res
+    # per-job device times of the last batch: the tail of the persistent launch
+    js, je = arena.job_times(count)
+    jt = je - js
+    ctas = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    job_times = {"job_ms_p50": round(1e3 * float(np.percentile(jt, 50)), 3),
+                 "job_ms_p99": round(1e3 * float(np.percentile(jt, 99)), 3),
+                 "job_ms_max": round(1e3 * float(jt.max()), 3),
+                 "makespan_ms": round(1e3 * float(je.max()), 3),
+                 "balanced_ms": round(1e3 * float(jt.sum()) / ctas, 3),
+                 "last_job_start_ms": round(1e3 * float(js.max()), 3),
+                 "what": ("device time per job (one CTA each: no graph of this batch outweighs the per-CTA average); "
+                          f"balanced_ms = the sum of job times over the {ctas} CTAs, the makespan a perfect split "
+                          "would give")}
+    # a small batch (the first 50 jobs) is bound by its largest job: one CTA per job vs CTA groups
+    small = {}
+    sids, staus, sseeds = ids[:50], taus[:50], seeds[:50]
+    for split in (1, 2):
+        cd.tuning_set(**{**BASE_TUNING, "batch_split": split})
+        ref_small, _ = arena.run(sids, staus, sseeds)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            rs, _ = arena.run(sids, staus, sseeds)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sj, sje = arena.job_times(len(sids))
+        small["split" if split == 2 else "all_in_launch"] = {
+            "ms_per_batch": round(e0.elapsed_time(e1) / reps, 3), "makespan_ms": round(1e3 * float(sje.max()), 3),
+            "job_ms_max": round(1e3 * float((sje - sj).max()), 3), "identical": bool(rs == ref_small)}
+        small.setdefault("results", []).append(rs)
+    cd.tuning_set(**BASE_TUNING)
+    small_same = small.pop("results")
+    small["identical_across_forms"] = bool(small_same[0] == small_same[1])
+    small["what"] = ("the mixture's first 50 jobs: batch_split = 1 (every graph in the persistent launch, one CTA "
+                     "each) vs 2, the default (a graph that outweighs the per-CTA average runs first on the "
+                     "one-graph path with the whole device)")
     # autotuned: the many-graph knobs picked on these jobs (cached for the batch's size class), then timed
     tuned = arena.autotune(ids, taus, seeds, reps=2)
     torch.cuda.synchronize()
@@ -288,8 +327,10 @@ def batched_leg(cd, stream, mix, sample_every, reps=3, dist=None, total_count=No
     if dist is not None and dist.is_initialized():
         t_tuned = max_over_ranks(t_tuned, dist, dev)
     return {"workload": "mix2000", "describe": MIX_DESCRIBE, "graphs": count, "undirected_edges": edges,
+            "job_times": job_times, "small_batch": small,
             "tuned": {"graphs_per_s": round(count / t_tuned, 1), "ms_per_batch": round(t_tuned * 1e3, 2),
-                      "knobs": {"batch_fw_k": tuned["batch_fw_k"]}, "identical_to_default": bool(tuned_same),
+                      "knobs": {"batch_fw_k": tuned["batch_fw_k"], "batch_split": tuned["batch_split"]},
+                      "identical_to_default": bool(tuned_same),
                       "what": "cldiam_autotune_batch on the same jobs (median of 2 runs per candidate), then "
                               "the same timed loop with the cached choice"},
             "scaling": "strong (the 2,000 graphs are split across ranks by size)",
@@ -547,6 +588,9 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cd.load()
+    if args.tuning:
+        BASE_TUNING.update({k: float(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        cd.tuning_set(**BASE_TUNING)
     stream = torch.cuda.Stream()
     wl = WORKLOADS[args.workload]
 

@@ -289,7 +289,10 @@ cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_
  * cluster): graphs are packed into one device-resident CSR arena and a batch
  * of (graph, tau, seed) jobs runs the whole method -- CLUSTER (Algorithm 1),
  * the weighted quotient graph and Phi_approx (Section 4) -- in one persistent
- * launch, one graph per CTA at a time, largest graphs first.  Every result is
+ * launch, one graph per CTA at a time, largest graphs first.  A graph that
+ * alone outweighs the batch's per-CTA average would hold its CTA past the
+ * end of an even split: such graphs run first on the one-graph path with the
+ * whole device (cldiam_tuning.batch_split).  Every result is
  * identical to cldiam_cluster + cldiam_quotient_build + cldiam_estimate on the
  * same graph, tau and seed with the same options.
  */
@@ -309,6 +312,13 @@ cldiam_status cldiam_arena_graph(cldiam_arena* a, uint32_t graph_id, cldiam_grap
  * first failing status (OVERFLOW, DIVERGED, TIMEOUT) if any job failed, else OK. */
 cldiam_status cldiam_batch_run(cldiam_arena* a, const uint32_t* graph_ids, const double* tau, const uint64_t* seed,
                                uint32_t count, const cldiam_opts* opts, cldiam_result* out, cldiam_status* status);
+/* Device time of each job of the last cldiam_batch_run on this arena, in the caller's job order:
+ * start_s[i] / end_s[i] (host arrays of `count`) = when job i started / ended, in seconds from the start
+ * of the batch: the graphs run first on the one-graph path back to back (CUDA events), then the
+ * persistent launch's jobs (device global timer, offset by the one-graph runs); a job finished on the
+ * one-graph path after the launch keeps its in-kernel times.  INVALID_ARG if count exceeds the last
+ * batch. */
+cldiam_status cldiam_arena_job_times(const cldiam_arena* a, uint32_t count, double* start_s, double* end_s);
 void cldiam_arena_free(cldiam_arena* a);
 
 /* ------------------------------------------------------------------------
@@ -366,7 +376,12 @@ typedef struct {
                                       Floyd-Warshall in shared memory; 0 = 200                     */
     float sssp_delta_scale;        /* Delta-stepping with delta = 0: Delta = this x the average
                                       weight (>= 1); 0 = 1                                          */
-    uint32_t reserved[9];          /* must be 0                                                     */
+    uint32_t batch_split;          /* many-graph form: 2 = a graph whose work (entries + nodes)
+                                      exceeds the batch's per-CTA average (and that has at least
+                                      2^16 entries) runs first on the one-graph path with the whole
+                                      device, the rest in the persistent launch; 1 = every graph in
+                                      the launch; 0 = 2                                             */
+    uint32_t reserved[8];          /* must be 0                                                     */
 } cldiam_tuning;
 
 /* The process-wide knobs (defaults filled in). */
@@ -393,7 +408,7 @@ cldiam_status cldiam_tuning_set(const cldiam_tuning* t);
  * run, so no other call may run meanwhile.
  *  graph: pull_ratio, relax_ctas_per_sm, dense_quotient_k, apsp_sources_per_cta,
  *         apsp_fw_density on cldiam_cluster + cldiam_quotient_build + cldiam_estimate;
- *  batch: batch_fw_k on cldiam_batch_run of the listed jobs;
+ *  batch: batch_split, batch_fw_k on cldiam_batch_run of the listed jobs;
  *  sssp:  sssp_delta_scale on cldiam_sssp_delta(delta = 0) from `source`.
  */
 cldiam_status cldiam_autotune_graph(cldiam_graph* g, double tau, uint64_t seed, const cldiam_opts* opts,
@@ -407,7 +422,7 @@ cldiam_status cldiam_autotune_sssp(cldiam_graph* g, uint32_t source, uint32_t re
  * with the candidate knobs and returns its time in *seconds and a digest of
  * its result in *result_hash (any non-OK status skips the candidate).
  * knob_mask bit i = the i-th field of cldiam_tuning (0 pull_ratio ..
- * 6 sssp_delta_scale).  Host code only: needs no GPU.
+ * 7 batch_split).  Host code only: needs no GPU.
  */
 typedef cldiam_status (*cldiam_tune_measure_fn)(const cldiam_tuning* candidate, void* user, double* seconds,
                                                  uint64_t* result_hash);
@@ -419,7 +434,7 @@ uint32_t cldiam_size_class(uint64_t entries);
 /* The knobs a call on `device` in `size_class` would use (process-wide, cache, defaults). */
 cldiam_status cldiam_tuning_effective(int32_t device, uint32_t size_class, cldiam_tuning* out);
 /* The tuning cache: set or read one entry (fields 0 = not cached), clear all, save to or load from a
- * text file (one line per entry: device, size class, the seven knobs).  INVALID_ARG when an entry is
+ * text file (one line per entry: device, size class, the eight knobs).  INVALID_ARG when an entry is
  * missing, a value is out of range or the file cannot be read or written. */
 cldiam_status cldiam_tuning_cache_put(int32_t device, uint32_t size_class, const cldiam_tuning* t);
 cldiam_status cldiam_tuning_cache_get(int32_t device, uint32_t size_class, cldiam_tuning* out);

@@ -48,7 +48,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("pull_ratio", ctypes.c_float), ("relax_ctas_per_sm", ctypes.c_uint32),
                 ("dense_quotient_k", ctypes.c_uint32), ("apsp_sources_per_cta", ctypes.c_uint32),
                 ("apsp_fw_density", ctypes.c_uint32), ("batch_fw_k", ctypes.c_uint32),
-                ("sssp_delta_scale", ctypes.c_float), ("reserved", ctypes.c_uint32 * 9)]
+                ("sssp_delta_scale", ctypes.c_float), ("batch_split", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 8)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -58,7 +59,7 @@ class Tuning(ctypes.Structure):
 TUNE_MEASURE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(Tuning), ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64))
 KNOBS = ["pull_ratio", "relax_ctas_per_sm", "dense_quotient_k", "apsp_sources_per_cta", "apsp_fw_density",
-         "batch_fw_k", "sssp_delta_scale"]
+         "batch_fw_k", "sssp_delta_scale", "batch_split"]
 
 
 class Result(ctypes.Structure):
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True):
             "cldiam_arena_info": (st, [P, P, P]),
             "cldiam_arena_graph": (st, [P, ctypes.c_uint32, PP]),
             "cldiam_batch_run": (st, [P, P, P, P, ctypes.c_uint32, P, P, P]),
+            "cldiam_arena_job_times": (st, [P, ctypes.c_uint32, P, P]),
             "cldiam_arena_free": (None, [P]),
             "cldiam_server_create": (st, [P, P, PP]),
             "cldiam_server_submit": (st, [P, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64, P]),
@@ -329,6 +331,13 @@ class Arena(_Handle):
             _check(st, "cldiam_batch_run")
         return [res[i].as_dict() for i in range(cnt)], [int(x) for x in sts[:cnt]]
 
+    def job_times(self, count: int):
+        """cldiam_arena_job_times: (start, end) seconds of each job of the last batch, in job order."""
+        a = np.zeros(count, np.float64); b = np.zeros(count, np.float64)
+        _check(load().cldiam_arena_job_times(self.handle, count, a.ctypes.data, b.ctypes.data),
+               "cldiam_arena_job_times")
+        return a, b
+
     def autotune(self, ids, taus, seeds, reps: int = 3) -> dict:
         """cldiam_autotune_batch: tune the many-graph knobs on these jobs; cached for the batch's size class."""
         ids = np.ascontiguousarray(ids, dtype=np.uint32)
@@ -502,11 +511,7 @@ def tuning_set(**knobs) -> None:
     if not knobs:
         _check(load().cldiam_tuning_set(None), "cldiam_tuning_set")
         return
-    t = Tuning()
-    for k, v in knobs.items():
-        if k not in dict(Tuning._fields_) or k == "reserved":
-            raise KeyError(k)
-        setattr(t, k, v)
+    t = _tuning_of(knobs)
     _check(load().cldiam_tuning_set(ctypes.byref(t)), "cldiam_tuning_set")
 
 
@@ -515,7 +520,7 @@ def _tuning_of(knobs: dict) -> Tuning:
     for k, v in knobs.items():
         if k not in KNOBS:
             raise KeyError(k)
-        setattr(t, k, v)
+        setattr(t, k, v if k in ("pull_ratio", "sssp_delta_scale") else int(v))
     return t
 
 

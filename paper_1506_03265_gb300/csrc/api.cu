@@ -1,5 +1,6 @@
 // extern "C" entry points of include/cldiam.h: argument checks, stream and
 // pointer plumbing, and translation of internal failures into status codes.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -101,6 +102,7 @@ const char* cldiam_status_string(cldiam_status s) {
 }
 
 const char* cldiam_last_error(void) { return last_error_cstr(); }
+
 
 cldiam_status cldiam_version(int32_t* major, int32_t* minor) {
     if (major) *major = 1;
@@ -271,6 +273,10 @@ cldiam_status cldiam_sssp_source(const cldiam_graph* g, uint64_t seed, uint32_t*
 cldiam_status cldiam_sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist, uint64_t* ecc,
                                 uint64_t* rounds, uint64_t* edges_scanned) {
     return guarded([&] { return sssp_delta(g, source, delta, dist, ecc, rounds, edges_scanned); });
+}
+
+cldiam_status cldiam_arena_job_times(const cldiam_arena* a, uint32_t count, double* start_s, double* end_s) {
+    return guarded([&] { return arena_job_times(a, count, start_s, end_s); });
 }
 
 cldiam_status cldiam_arena_create(uint64_t hbm_budget_bytes, void* stream, cldiam_arena** out) {

@@ -32,6 +32,13 @@ namespace {
 
 constexpr int BT = 1024;              // threads per CTA
 constexpr uint32_t kDenseCap = 1024;  // largest quotient deduplicated in the dense matrix
+constexpr uint64_t kSplitMinEntries = 1u << 16;  // graphs below this many entries always stay in the launch
+// makespan model of the many-graph split (GB300): seconds per unit of work (entry or node) on one 1,024-thread
+// CTA of the launch, and a graph's cost on the one-graph path (a fixed part for its launches and counter
+// reads, and a per-unit part with the whole device)
+constexpr double kCtaSecPerUnit = 37e-9;
+constexpr double kPlainSecPerGraph = 1.5e-3;
+constexpr double kPlainSecPerUnit = 0.05e-9;
 constexpr uint32_t kSmemFwK = 200;    // quotients up to this size are closed by Floyd-Warshall in shared memory
 constexpr uint32_t kJobOk = 0, kJobNeedsPlain = 1, kJobOverflow = 2, kJobDiverged = 3, kJobTimeout = 4;
 
@@ -53,6 +60,7 @@ struct Job {
     uint32_t step_cap;    // growing steps per PartialGrowth, 0 = no cap
     uint32_t cumulative;  // cumulative contract mode
     uint32_t fw_k;        // quotients up to this size (<= kSmemFwK) are closed by Floyd-Warshall in shared memory
+    uint32_t pad;
 };
 
 struct Workspace {  // one slice per CTA
@@ -77,7 +85,9 @@ struct JobOut {
     cldiam_result r;
     uint32_t status;
     uint32_t pad;
+    uint64_t t_start, t_end;  // device global timer (ns) when the job started and ended
 };
+
 
 __device__ __forceinline__ uint32_t relax_min_u32(uint32_t c, uint32_t a, uint32_t b, bool& ovf) {
     const uint32_t s = a + b;
@@ -260,6 +270,73 @@ __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M
 }
 
 // One job: CLUSTER + quotient + Phi(G_C) of one arena graph by this CTA; thread 0 stores the result.
+// The end of a job on one CTA: singletons, relabel, the dense quotient and Phi(G_C); thread 0 stores
+// the result.  `res` holds the CLUSTER counters so far.
+__device__ void finish_job(const Job& job, const ArenaDesc& d, const uint64_t* __restrict__ off,
+                           const uint2* __restrict__ adj, const uint32_t* __restrict__ row, const Workspace& ws,
+                           BatchSmem& sm, uint32_t* dyn, JobOut* out, cldiam_result res, uint32_t status,
+                           uint32_t delta) {
+    const unsigned tid = threadIdx.x;
+    const uint32_t n = d.n;
+    if (status == kJobOk) {
+        dev_singletons(n, ws.center, ws.D, 0, 1);
+        __syncthreads();
+        res.delta_end = delta;
+        const uint32_t k = block_relabel(n, ws.center, ws.stamp, ws.cid, sm);  // stamp reused as rank
+        res.k = k;
+        const uint32_t rmax =
+            block_all_reduce([&] {
+                uint32_t m = 0;
+                for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
+                return m;
+            }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+        res.radius = rmax;
+        if (k > kDenseCap) {
+            status = kJobNeedsPlain;
+        } else {
+            // weighted quotient graph, deduplicated densely
+            uint32_t* M = ws.M;
+            for (uint32_t i = tid; i < k * k; i += BT) M[i] = (i / k == i % k) ? 0u : kNone;
+            __syncthreads();
+            bool ovf = false;
+            for (uint64_t i = tid; i < d.nnz; i += BT) {
+                const uint32_t u = row[i];
+                const uint2 e = adj[i];
+                const uint32_t a = __ldcg(&ws.cid[u]), b = __ldcg(&ws.cid[e.x]);
+                if (a != b) {
+                    uint64_t s = (uint64_t)__ldcg(&ws.D[u]) + e.y + __ldcg(&ws.D[e.x]);
+                    if (s >= 0xFFFFFFFFull) {
+                        ovf = true;
+                        s = 0xFFFFFFFEull;
+                    }
+                    atomicMin(&M[(size_t)a * k + b], (uint32_t)s);
+                }
+            }
+            __syncthreads();
+            const unsigned long long qe = block_all_reduce(
+                [&] {
+                    unsigned long long c = 0;
+                    for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
+                    return c;
+                }(),
+                [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
+            res.quotient_edges = qe;
+            bool ovf2 = false;
+            const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2, job.fw_k);
+            const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
+                                                      [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
+            if (any_ovf) status = kJobOverflow;
+            res.phi_gc = phi;
+            res.phi_approx = (uint64_t)phi + 2ull * rmax;
+        }
+    }
+    if (tid == 0) {
+        out->r = res;
+        out->status = status;
+    }
+    __syncthreads();
+}
+
 __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __restrict__ arena_off,
                         const uint2* __restrict__ arena_adj, const uint32_t* __restrict__ arena_row,
                         const Workspace& ws, BatchSmem& sm, uint32_t* dyn, JobOut* out) {
@@ -394,67 +471,11 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
         __syncthreads();
         if (status != kJobOk) break;
     }
-    if (status == kJobOk) {
-        dev_singletons(n, ws.center, ws.D, 0, 1);
-        __syncthreads();
-        res.delta_end = delta;
-        const uint32_t k = block_relabel(n, ws.center, ws.stamp, ws.cid, sm);  // stamp reused as rank
-        res.k = k;
-        const uint32_t rmax =
-            block_all_reduce([&] {
-                uint32_t m = 0;
-                for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
-                return m;
-            }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
-        res.radius = rmax;
-        if (k > kDenseCap) {
-            status = kJobNeedsPlain;
-        } else {
-            // weighted quotient graph, deduplicated densely
-            uint32_t* M = ws.M;
-            for (uint32_t i = tid; i < k * k; i += BT) M[i] = (i / k == i % k) ? 0u : kNone;
-            __syncthreads();
-            bool ovf = false;
-            for (uint64_t i = tid; i < d.nnz; i += BT) {
-                const uint32_t u = row[i];
-                const uint2 e = adj[i];
-                const uint32_t a = __ldcg(&ws.cid[u]), b = __ldcg(&ws.cid[e.x]);
-                if (a != b) {
-                    uint64_t s = (uint64_t)__ldcg(&ws.D[u]) + e.y + __ldcg(&ws.D[e.x]);
-                    if (s >= 0xFFFFFFFFull) {
-                        ovf = true;
-                        s = 0xFFFFFFFEull;
-                    }
-                    atomicMin(&M[(size_t)a * k + b], (uint32_t)s);
-                }
-            }
-            __syncthreads();
-            const unsigned long long qe = block_all_reduce(
-                [&] {
-                    unsigned long long c = 0;
-                    for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
-                    return c;
-                }(),
-                [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
-            res.quotient_edges = qe;
-            bool ovf2 = false;
-            const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2, job.fw_k);
-            const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
-                                                      [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
-            if (any_ovf) status = kJobOverflow;
-            res.phi_gc = phi;
-            res.phi_approx = (uint64_t)phi + 2ull * rmax;
-        }
-    }
-    if (tid == 0) {
-        out->r = res;
-        out->status = status;
-    }
-    __syncthreads();
+    finish_job(job, d, off, adj, row, ws, sm, dyn, out, res, status, delta);
 }
 
 __global__ void __launch_bounds__(BT, 1)
-    k_batch(const ArenaDesc* __restrict__ descs, const Job* __restrict__ jobs, uint32_t njobs,
+    k_batch(const ArenaDesc* __restrict__ descs, const Job* __restrict__ jobs, uint32_t count,
             const uint64_t* __restrict__ arena_off, const uint2* __restrict__ arena_adj,
             const uint32_t* __restrict__ arena_row, Workspace* __restrict__ wss, uint32_t* __restrict__ queue,
             JobOut* __restrict__ outs) {
@@ -464,11 +485,16 @@ __global__ void __launch_bounds__(BT, 1)
     for (;;) {
         if (threadIdx.x == 0) sm.job = atomicAdd(queue, 1u);
         __syncthreads();
-        const uint32_t jid = sm.job;
+        const uint32_t j = sm.job;
         __syncthreads();
-        if (jid >= njobs) break;
-        const Job job = jobs[jid];
+        if (j >= count) break;
+        const Job job = jobs[j];
+        const uint64_t t0 = global_ns();
         run_job(job, descs[job.graph], arena_off, arena_adj, arena_row, ws, sm, dyn, &outs[job.out]);
+        if (threadIdx.x == 0) {
+            outs[job.out].t_start = t0;
+            outs[job.out].t_end = global_ns();
+        }
     }
 }
 
@@ -570,6 +596,7 @@ struct cldiam_arena {
     uint64_t off_cap = 0, adj_cap = 0, off_used = 0, adj_used = 0;
     void* ws = nullptr;  // cached per-CTA workspaces
     size_t ws_bytes = 0;
+    std::vector<double> last_start, last_end;  // per-job device times of the last batch (seconds)
 };
 
 namespace cld {
@@ -681,6 +708,15 @@ cldiam_status arena_graph(cldiam_arena* a, uint32_t id, cldiam_graph** out) {
 
 uint32_t arena_count(const cldiam_arena* a) { return (uint32_t)a->graphs.size(); }
 cudaStream_t arena_stream(const cldiam_arena* a) { return a->stream; }
+cldiam_status arena_job_times(const cldiam_arena* a, uint32_t count, double* start_s, double* end_s) {
+    if (!a || (count && (!start_s || !end_s))) return fail(CLDIAM_ERR_INVALID_ARG, "NULL argument");
+    if (count > a->last_start.size()) return fail(CLDIAM_ERR_INVALID_ARG, "count exceeds the last batch");
+    for (uint32_t i = 0; i < count; ++i) {
+        start_s[i] = a->last_start[i];
+        end_s[i] = a->last_end[i];
+    }
+    return CLDIAM_OK;
+}
 uint64_t arena_entries(const cldiam_arena* a, const uint32_t* ids, uint32_t count) {
     uint64_t e = 0;
     for (uint32_t i = 0; i < count; ++i)
@@ -731,6 +767,17 @@ static cldiam_status make_workspaces(uint32_t nmax, int ctas, cudaStream_t s, vo
     return CLDIAM_OK;
 }
 
+struct CudaEvent {
+    cudaEvent_t e = nullptr;
+    cldiam_status create() {
+        CLD_CUDA(cudaEventCreate(&e));
+        return CLDIAM_OK;
+    }
+    ~CudaEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+};
+
 static size_t batch_dyn_smem() {
     // shared Floyd-Warshall matrix, or the quotient SSSP's k x 8 distances and two words of change bits per node
     return std::max<size_t>((size_t)kSmemFwK * kSmemFwK * 4, (size_t)kDenseCap * (8 * 4 + 8));
@@ -759,7 +806,6 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     const cudaStream_t s = a->stream;
     const uint32_t fw_k = tuning_for_batch(arena_entries(a, ids, count)).batch_fw_k;
     std::vector<Job> jobs(count);
-    uint32_t nmax = 1;
     for (uint32_t i = 0; i < count; ++i) {
         if (ids[i] >= a->graphs.size()) return fail(CLDIAM_ERR_INVALID_ARG, "graph id out of range");
         if (!(tau[i] > 0.0) || !std::isfinite(tau[i])) return fail(CLDIAM_ERR_INVALID_ARG, "tau must be positive");
@@ -776,42 +822,115 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         jobs[i].step_cap = opts.step_cap;
         jobs[i].cumulative = opts.contract_mode == CLDIAM_CONTRACT_CUMULATIVE ? 1u : 0u;
         jobs[i].fw_k = fw_k;
-        nmax = std::max(nmax, view.n);
     }
     // largest graphs first: the work queue then balances the tail
     std::stable_sort(jobs.begin(), jobs.end(), [&](const Job& x, const Job& y) {
         return a->graphs[x.graph].nnz + a->graphs[x.graph].n > a->graphs[y.graph].nnz + a->graphs[y.graph].n;
     });
     const int nsm = num_sms();
-    std::vector<Workspace> wsh;
-    CLD_TRY(make_workspaces(nmax, nsm, s, &a->ws, &a->ws_bytes, &wsh));
-    DBuf<ArenaDesc> ddesc;
-    DBuf<Job> djobs;
-    DBuf<Workspace> dws;
-    DBuf<uint32_t> queue;
-    DBuf<JobOut> douts;
-    CLD_TRY(ddesc.alloc(a->graphs.size(), s));
-    CLD_TRY(djobs.alloc(count, s));
-    CLD_TRY(dws.alloc(nsm, s));
-    CLD_TRY(queue.alloc(1, s));
-    CLD_TRY(douts.alloc(count, s));
-    CLD_CUDA(cudaMemcpyAsync(ddesc.get(), a->graphs.data(), a->graphs.size() * sizeof(ArenaDesc),
-                             cudaMemcpyHostToDevice, s));
-    CLD_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), count * sizeof(Job), cudaMemcpyHostToDevice, s));
-    CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
-    CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
-    const size_t dyn = batch_dyn_smem();
-    static std::atomic<bool> attr[64];
-    CLD_TRY(set_dyn_smem(k_batch, attr));
-    CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), count, a->off, a->adj, a->row, dws.get(),
-                                                   queue.get(), douts.get()));
-    CLD_LAUNCH_CHECK();
+    // The launch ends with its largest graph on one CTA, or with the even split of all work over the CTAs,
+    // whichever is later.  The k largest graphs can instead run first on the one-graph path, each with the
+    // whole device at a fixed cost per graph; k is chosen to minimise the estimated makespan
+    // (batch_split = 2; 1 keeps every graph in the launch).  Work = adjacency entries + nodes.
+    const uint32_t split = tuning_for_batch(arena_entries(a, ids, count)).batch_split;
+    std::vector<double> cost(count);
+    double rest = 0.0;
+    for (uint32_t j = 0; j < count; ++j) {
+        cost[j] = (double)(a->graphs[jobs[j].graph].nnz + a->graphs[jobs[j].graph].n);
+        rest += cost[j];
+    }
+    uint32_t nbig = 0;  // jobs[0 .. nbig) take the one-graph path (largest first, so a prefix)
+    if (split == 2) {
+        const auto launch_s = [&](uint32_t k, double rest_work) {
+            return k < count ? std::max(cost[k] * kCtaSecPerUnit, rest_work * kCtaSecPerUnit / nsm) : 0.0;
+        };
+        double plain_s = 0.0, best = launch_s(0, rest);
+        for (uint32_t k = 1; k <= count && a->graphs[jobs[k - 1].graph].nnz >= kSplitMinEntries; ++k) {
+            plain_s += kPlainSecPerGraph + cost[k - 1] * kPlainSecPerUnit;
+            rest -= cost[k - 1];
+            const double t = plain_s + launch_s(k, rest);
+            if (t < best) {
+                best = t;
+                nbig = k;
+            }
+        }
+    }
+    a->last_start.assign(count, 0.0);
+    a->last_end.assign(count, 0.0);
     std::vector<JobOut> ho(count);
-    CLD_CUDA(cudaMemcpyAsync(ho.data(), douts.get(), count * sizeof(JobOut), cudaMemcpyDeviceToHost, s));
-    CLD_CUDA(cudaStreamSynchronize(s));
+    for (auto& h : ho) h.status = kJobOk;
+    double big_s = 0.0;  // device time of the one-graph runs, the offset of the launch's job times
+    std::vector<cldiam_status> big_st(count, CLDIAM_OK);
+    if (nbig > 0) {
+        CudaEvent e0, e1;
+        CLD_TRY(e0.create());
+        CLD_TRY(e1.create());
+        for (uint32_t j = 0; j < nbig; ++j) {
+            const uint32_t i = jobs[j].out;
+            cldiam_graph view;
+            arena_view(a, ids[i], &view);
+            CLD_TRY(view.host.alloc(256));
+            CLD_CUDA(cudaEventRecord(e0.e, s));
+            cldiam_clustering* c = nullptr;
+            cldiam_quotient* q = nullptr;
+            cldiam_status st = cluster(&view, tau[i], seed[i], &opts, &c);
+            if (st == CLDIAM_OK) st = quotient(c, &q);
+            if (st == CLDIAM_OK) st = cldiam_estimate(q, &ho[i].r);
+            free_quotient(q);
+            free_clustering(c);
+            CLD_CUDA(cudaEventRecord(e1.e, s));
+            CLD_CUDA(cudaEventSynchronize(e1.e));
+            float ms = 0.f;
+            CLD_CUDA(cudaEventElapsedTime(&ms, e0.e, e1.e));
+            a->last_start[i] = big_s;
+            big_s += ms * 1e-3;
+            a->last_end[i] = big_s;
+            big_st[i] = st;
+        }
+    }
+    const uint32_t nrest = count - nbig;
+    if (nrest > 0) {
+        uint32_t nmax_rest = 1;
+        for (uint32_t j = nbig; j < count; ++j) nmax_rest = std::max(nmax_rest, a->graphs[jobs[j].graph].n);
+        std::vector<Workspace> wsh;
+        CLD_TRY(make_workspaces(nmax_rest, nsm, s, &a->ws, &a->ws_bytes, &wsh));
+        DBuf<ArenaDesc> ddesc;
+        DBuf<Job> djobs;
+        DBuf<Workspace> dws;
+        DBuf<uint32_t> queue;
+        DBuf<JobOut> douts;
+        CLD_TRY(ddesc.alloc(a->graphs.size(), s));
+        CLD_TRY(djobs.alloc(nrest, s));
+        CLD_TRY(dws.alloc(nsm, s));
+        CLD_TRY(queue.alloc(1, s));
+        CLD_TRY(douts.alloc(count, s));
+        CLD_CUDA(cudaMemcpyAsync(ddesc.get(), a->graphs.data(), a->graphs.size() * sizeof(ArenaDesc),
+                                 cudaMemcpyHostToDevice, s));
+        CLD_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data() + nbig, nrest * sizeof(Job), cudaMemcpyHostToDevice, s));
+        CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
+        CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
+        const size_t dyn = batch_dyn_smem();
+        static std::atomic<bool> attr[64];
+        CLD_TRY(set_dyn_smem(k_batch, attr));
+        CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), nrest, a->off, a->adj, a->row, dws.get(),
+                                                       queue.get(), douts.get()));
+        CLD_LAUNCH_CHECK();
+        std::vector<JobOut> hl(count);
+        CLD_CUDA(cudaMemcpyAsync(hl.data(), douts.get(), count * sizeof(JobOut), cudaMemcpyDeviceToHost, s));
+        CLD_CUDA(cudaStreamSynchronize(s));
+        // per-job device times of the launch, relative to its first job's start, after the one-graph runs
+        uint64_t t0 = ~0ull;
+        for (uint32_t j = nbig; j < count; ++j) t0 = std::min(t0, hl[jobs[j].out].t_start);
+        for (uint32_t j = nbig; j < count; ++j) {
+            const uint32_t i = jobs[j].out;
+            ho[i] = hl[i];
+            a->last_start[i] = big_s + (double)(hl[i].t_start - t0) * 1e-9;
+            a->last_end[i] = big_s + (double)(hl[i].t_end - t0) * 1e-9;
+        }
+    }
     cldiam_status first_err = CLDIAM_OK;
     for (uint32_t i = 0; i < count; ++i) {
-        cldiam_status st = CLDIAM_OK;
+        cldiam_status st = big_st[i];
         if (ho[i].status == kJobNeedsPlain) {
             // quotient larger than the dense capacity: finish this graph with the one-graph path
             cldiam_graph view;
@@ -947,6 +1066,9 @@ static void big_lane(cldiam_server* sv) {
 }
 
 cldiam_status server_free(cldiam_server* sv);
+
+// Servers alive in this process: while one is, its persistent kernel may hold SMs, so CLUSTER keeps its
+// host-driven stage loop (a cooperative launch would wait for every SM).
 
 cldiam_status server_create(cldiam_arena* a, const cldiam_server_opts* o, cldiam_server** out) {
     if (!a || !out) return fail(CLDIAM_ERR_INVALID_ARG, "NULL arena or out");

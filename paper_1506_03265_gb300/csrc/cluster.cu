@@ -1,9 +1,11 @@
 // CLUSTER(G, tau) of Algorithm 1 on the GPU, one graph per launch: each
 // phase body of cluster_dev.cuh runs as its own grid kernel and the host
 // drives the stage / step / doubling control flow from small counter reads.
+
 #include <atomic>
 #include <cmath>
 #include <vector>
+
 
 #include "cluster_dev.cuh"
 #include "internal.cuh"
@@ -101,26 +103,33 @@ __global__ void k_assign_cid(uint32_t n, const uint32_t* __restrict__ center, co
 // entry (an unfrozen node that reads the candidates of its contracted
 // neighbours, kPullTag | v) reduces its candidates over its lanes first, so
 // it lowers its own key once per group segment.  No block barrier.
-__global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fbase,
-                                                const unsigned long long* __restrict__ fkey,
-                                                const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
-                                                uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
-                                                const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
-                                                unsigned long long* __restrict__ key, uint32_t delta,
-                                                uint32_t* __restrict__ stamp, uint32_t stepid,
-                                                uint32_t* __restrict__ next, Counters* ctr) {
-    __shared__ uint32_t spre[PT / 32][QC + 1];  // first positions of the entries after the chunk's first
-    __shared__ uint32_t sbase[PT / 32][QC + 2];
-    __shared__ unsigned long long skey[PT / 32][QC + 2];
-    __shared__ uint32_t sbuf[PT / 32][PNB];
+struct PushSmem {
+    uint32_t spre[PT / 32][QC + 1];  // first positions of the entries after the chunk's first
+    uint32_t sbase[PT / 32][QC + 2];
+    unsigned long long skey[PT / 32][QC + 2];
+    uint32_t sbuf[PT / 32][PNB];
+};
+
+__device__ __forceinline__ void dev_push(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
+                                         const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
+                                         uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
+                                         const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
+                                         unsigned long long* __restrict__ key, uint32_t delta,
+                                         uint32_t* __restrict__ stamp, uint32_t stepid,
+                                         uint32_t* __restrict__ next, Counters* ctr, PushSmem& smp, uint32_t br,
+                                         uint32_t nb) {
+    auto& spre = smp.spre;
+    auto& sbase = smp.sbase;
+    auto& skey = smp.skey;
+    auto& sbuf = smp.sbuf;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     const unsigned le_mask = 0xffffffffu >> (31u - lane);
     WarpNext wn{sbuf[warp], 0};
     unsigned long long newly = 0;
     const uint32_t nq = (uint32_t)(((uint64_t)E + QC - 1) / QC);
-    const uint32_t nwarps = gridDim.x * (PT / 32);
-    for (uint32_t q = blockIdx.x * (PT / 32) + warp; q < nq; q += nwarps) {
+    const uint32_t nwarps = nb * (PT / 32);
+    for (uint32_t q = br * (PT / 32) + warp; q < nq; q += nwarps) {
         const uint32_t p0 = q * QC, e1 = min(E, p0 + QC);
         // entry i0 holds p0; entries i0 + 1 .. il start inside (p0, p0 + QC] (at most QC of them)
         const uint32_t i0 = __ldcg(&cfirst[q]);
@@ -189,7 +198,8 @@ __global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fba
             bool first = false;
             if (nk != kInfKey) {
                 // the target's key and stamp in one round trip, through L1 (a stale line only lets an
-                // extra candidate through: the atomics decide); most candidates lose to the current key
+                // extra candidate through: keys only fall within a launch, and the atomics decide); most
+                // candidates lose to the current key
                 const unsigned long long cur = ld_keep_u64(&key[target], pol_keep);
                 const uint32_t stp = ld_keep_u32(&stamp[target], pol_keep);
                 if (nk < cur) {
@@ -209,6 +219,19 @@ __global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fba
     warp_add_u64(&ctr->newly_covered, newly);
 }
 
+__global__ void __launch_bounds__(PT, 6) k_push(const uint32_t* __restrict__ fbase,
+                                                const unsigned long long* __restrict__ fkey,
+                                                const uint32_t* __restrict__ fpre, const uint32_t* __restrict__ cfirst,
+                                                uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
+                                                const uint32_t* __restrict__ center, const uint32_t* __restrict__ Dcum,
+                                                unsigned long long* __restrict__ key, uint32_t delta,
+                                                uint32_t* __restrict__ stamp, uint32_t stepid,
+                                                uint32_t* __restrict__ next, Counters* ctr) {
+    __shared__ PushSmem smp;
+    dev_push(fbase, fkey, fpre, cfirst, nf, E, adj, center, Dcum, key, delta, stamp, stepid, next, ctr, smp,
+                    blockIdx.x, gridDim.x);
+}
+
 // crow[q] = the row that holds CSR position q * PW (every row has >= 1 entry)
 __global__ void k_pull_rows(uint32_t n, const uint64_t* __restrict__ off, uint32_t* __restrict__ crow) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
@@ -217,34 +240,41 @@ __global__ void k_pull_rows(uint32_t n, const uint64_t* __restrict__ off, uint32
     }
 }
 
-__global__ void __launch_bounds__(PT, 6) k_pull(uint32_t n, uint32_t nnz, uint32_t nq, const uint32_t* __restrict__ crow,
-                                             const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
-                                             const uint32_t* __restrict__ center_cum,
-                                             const unsigned long long* __restrict__ keyS,
-                                             unsigned long long* __restrict__ key, uint32_t delta,
-                                             uint32_t* __restrict__ stamp, uint32_t stepid,
-                                             uint32_t* __restrict__ next, Counters* ctr) {
-    __shared__ uint32_t sst[PT / 32][PW + 1];              // starts of the rows after the chunk's first row
-    __shared__ unsigned long long sks[PT / 32][PW + 2];    // snapshot keys of the chunk's rows
-    __shared__ uint32_t sbuf[PT / 32][PNB];                // changed rows waiting for the next list
+struct PullSmem {
+    uint32_t sst[PT / 32][PW + 1];            // starts of the rows after the chunk's first row
+    unsigned long long sks[PT / 32][PW + 2];  // snapshot keys of the chunk's rows
+    uint32_t sbuf[PT / 32][PNB];              // changed rows waiting for the next list
+};
+
+__device__ __forceinline__ void dev_pull(uint32_t n, uint32_t nnz, uint32_t nq, const uint32_t* __restrict__ crow,
+                                         const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
+                                         const uint32_t* __restrict__ center_cum,
+                                         const unsigned long long* __restrict__ keyS,
+                                         unsigned long long* __restrict__ key, uint32_t delta,
+                                         uint32_t* __restrict__ stamp, uint32_t stepid,
+                                         uint32_t* __restrict__ next, Counters* ctr, PullSmem& smq, uint32_t br,
+                                         uint32_t nb) {
+    auto& sst = smq.sst;
+    auto& sks = smq.sks;
+    auto& sbuf = smq.sbuf;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     uint32_t* st = sst[warp];
     WarpNext wn{sbuf[warp], 0};
     unsigned long long newly = 0;
-    const uint32_t nwarps = gridDim.x * (PT / 32);
+    const uint32_t nwarps = nb * (PT / 32);
     const unsigned le_mask = 0xffffffffu >> (31u - lane);  // lanes <= this one
     // lower row r to v if v undercuts its start-of-step key ks; true for the one lowering that is r's first
     const auto lower_row = [&](uint32_t r, unsigned long long v, unsigned long long ks) -> bool {
         if (!(v < ks)) return false;
-        if (center_cum && __ldg(&center_cum[r]) != kNone) return false;  // a contracted row keeps its key
+        if (center_cum && __ldg(&center_cum[r]) != kNone) return false;  // contracted: keeps its key
         // exactly one lowering of r finds its start-of-step key: that one is the first change
         if (atom_min_keep_u64(&key[r], v, pol_keep) != ks) return false;
         stamp[r] = stepid;  // r has been lowered (a later pushed step reads it)
         newly += ks == kInfKey ? 1 : 0;
         return true;
     };
-    for (uint32_t q = blockIdx.x * (PT / 32) + warp; q < nq; q += nwarps) {
+    for (uint32_t q = br * (PT / 32) + warp; q < nq; q += nwarps) {
         const uint32_t p0 = q * PW;
         uint2 ed[PWG];
 #pragma unroll
@@ -315,6 +345,18 @@ __global__ void __launch_bounds__(PT, 6) k_pull(uint32_t n, uint32_t nnz, uint32
     warp_add_u64(&ctr->newly_covered, newly);
 }
 
+__global__ void __launch_bounds__(PT, 6) k_pull(uint32_t n, uint32_t nnz, uint32_t nq, const uint32_t* __restrict__ crow,
+                                             const uint64_t* __restrict__ off, const uint2* __restrict__ adj,
+                                             const uint32_t* __restrict__ center_cum,
+                                             const unsigned long long* __restrict__ keyS,
+                                             unsigned long long* __restrict__ key, uint32_t delta,
+                                             uint32_t* __restrict__ stamp, uint32_t stepid,
+                                             uint32_t* __restrict__ next, Counters* ctr) {
+    __shared__ PullSmem smq;
+    dev_pull(n, nnz, nq, crow, off, adj, center_cum, keyS, key, delta, stamp, stepid, next, ctr, smq,
+                    blockIdx.x, gridDim.x);
+}
+
 // node state before the first stage: no center, D = R = 0, no stamp, no key
 __global__ void k_cluster_init(uint32_t n, uint32_t* __restrict__ center, uint32_t* __restrict__ D,
                                uint32_t* __restrict__ R, uint32_t* __restrict__ stamp,
@@ -363,7 +405,7 @@ cldiam_status relabel_clusters(cldiam_graph* g, const uint32_t* center, uint32_t
 
 void free_clustering(cldiam_clustering* c) {
     if (!c) return;
-    cudaStream_t s = c->g ? c->g->stream : nullptr;
+    cudaStream_t s = c->stream;
     dfree(c->center, s);
     dfree(c->D, s);
     dfree(c->cid, s);
@@ -391,6 +433,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     ClusterOwner owner(new cldiam_clustering());
     cldiam_clustering* cl = owner.c;
     cl->g = g;
+    cl->stream = g->stream;
     cl->max_fw_k = opts.max_fw_k ? opts.max_fw_k : 8192u;
     cl->quotient_mode = opts.quotient_mode;
 
@@ -500,118 +543,127 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
         return CLDIAM_OK;
     };
 
-    for (;;) {
-        uint64_t thr = 0;
-        if (!stage_threshold(U, tau, L, &thr)) break;  // outer while test of Algorithm 1, center draw threshold
-        if (stage > kMaxStages) return fail(CLDIAM_ERR_DIVERGED, "CLUSTER exceeded its stage limit");
-
-        // selection + reset, then the stage's first frontier
-        CLD_TRY(zero_field(offsetof(Counters, selected), 8));
-        CLD_K(K_SELECT, s, k_select<<<gb, 256, 0, s>>>(n, center.get(), key.get(), seed, stage, thr, ctr.get(),
-                                                        keyS.get()));
-        CLD_LAUNCH_CHECK();
-        CLD_TRY(rebuild());
-        CLD_TRY(sync_counters());
-        uint64_t covered = hc->selected;
-        nf = (uint32_t)(hc->front >> 32);
-        E = (uint32_t)hc->front;
-        st.centers_drawn += hc->selected;
-
+    {
         for (;;) {
-            uint32_t updated, growth_steps = 0;
-            do {
-                ++growth_steps;
-                ++stepid;
-                updated = 0;
-                if (nf > 0) {
-                    CLD_TRY(zero_field(offsetof(Counters, newly_covered), 24));  // newly_covered, front, nnext
-                    // the dense form reads the whole adjacency: worth it when the relaxers hold a large share
-                    const bool dense = pull_dense && (double)E >= (double)tun.pull_ratio * (double)g->nnz;
-                    if (dense) {
-                        CLD_K(K_PULL, s, k_pull<<<pull_grid, PT, 0, s>>>(n, (uint32_t)g->nnz, pull_chunks, crow.get(),
-                                                                          g->off, g->adj,
-                                                                          cumulative ? center.get() : nullptr, keyS.get(),
-                                                                          key.get(), delta, stamp.get(), stepid,
-                                                                          next.get(), ctr.get()));
-                    } else {
-                        const uint64_t warps = ((uint64_t)E + QC - 1) / QC;
-                        const unsigned rg = (unsigned)std::min<uint64_t>((warps + PT / 32 - 1) / (PT / 32), push_grid);
-                        CLD_K(K_RELAX, s, k_push<<<rg, PT, 0, s>>>(fv, fk, fp, cf, nf, E, g->adj, center.get(),
-                                                                    cumulative ? D.get() : nullptr, key.get(), delta,
-                                                                    stamp.get(), stepid, next.get(), ctr.get()));
-                    }
-                    CLD_LAUNCH_CHECK();
-                    CLD_K(K_SNAPSHOT, s, k_snapshot<<<max_relax_grid, 256, 0, s>>>(next.get(), key.get(), g->off, delta,
-                                                                                 fv2, fk2, fp2, cf2, ctr.get(),
-                                                                                 keyS.get()));
-                    CLD_LAUNCH_CHECK();
-                    CLD_TRY(sync_counters());
-                    updated = hc->nnext;
-                    covered += hc->newly_covered;
-                    st.edges_scanned += E;
-                    if (dense) {
-                        // algorithmic bytes of a dense step: per adjacency entry the (col, w) pair (8 B) and
-                        // the neighbour's snapshot key (8 B); per row its start and snapshot key (16 B); per
-                        // changed node its key, stamp and list slot (16 B)
-                        prof_add_bytes(K_PULL, 16.0 * (double)g->nnz + 16.0 * n + 16.0 * updated);
-                    } else {
-                        // algorithmic bytes of a pushed step: per frontier entry its slot (4 + 8 + 4 B)
-                        // and row start (8 B); per adjacency entry the (col, w) pair (8 B) and the target's
-                        // key (8 B); per changed node its key, stamp and list slot (16 B)
-                        prof_add_bytes(K_RELAX, 24.0 * nf + 16.0 * (double)E + 16.0 * updated);
-                    }
-                    prof_add_bytes(K_SNAPSHOT, 4.0 * updated + 16.0 * updated + 16.0 * updated + 16.0 * (hc->front >> 32));
-                    std::swap(fv, fv2);
-                    std::swap(fp, fp2);
-                    std::swap(fk, fk2);
-                    std::swap(cf, cf2);
-                    nf = (uint32_t)(hc->front >> 32);
-                    E = (uint32_t)hc->front;
-                }
-                st.steps++;
-                st.node_updates += updated;
-            } while (updated != 0 && 2 * covered < U && (step_cap == 0 || growth_steps < step_cap));
-            if (2 * covered >= U) break;
-            bool growable = false;
-            if (delta < kDeltaMax && g->connected) {
-                // connected graph: some covered or frozen node touches an uncovered one iff any exists
-                growable = covered > 0 || U < n;
-            } else if (delta < kDeltaMax && g->nnz) {
-                CLD_TRY(zero_field(offsetof(Counters, growable), 4));
-                CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz,
-                                                                                         key.get(), ctr.get()));
-                CLD_LAUNCH_CHECK();
-                CLD_TRY(sync_counters());
-                growable = hc->growable != 0;
-            }
-            if (!growable) {
-                st.guard_exits++;
-                break;
-            }
-            delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
-            st.doublings++;
+            uint64_t thr = 0;
+            if (!stage_threshold(U, tau, L, &thr)) break;  // outer while test of Algorithm 1, center draw threshold
+            if (stage > kMaxStages) return fail(CLDIAM_ERR_DIVERGED, "CLUSTER exceeded its stage limit");
+
+            // selection + reset, then the stage's first frontier
+            CLD_TRY(zero_field(offsetof(Counters, selected), 8));
+            CLD_TRY(zero_field(offsetof(Counters, unfrozen), 8));
+            CLD_K(K_SELECT, s, k_select<<<gb, 256, 0, s>>>(n, center.get(), key.get(), seed, stage, thr, ctr.get(),
+                                                            keyS.get()));
+            CLD_LAUNCH_CHECK();
             CLD_TRY(rebuild());
             CLD_TRY(sync_counters());
+            if (hc->unfrozen != U) {
+                char buf[200];
+                snprintf(buf, sizeof buf, "the draw of stage %u saw %llu unfrozen nodes, the loop tracked %llu",
+                         stage, (unsigned long long)hc->unfrozen, (unsigned long long)U);
+                return fail(CLDIAM_ERR_DIVERGED, buf);
+            }
+            uint64_t covered = hc->selected;
             nf = (uint32_t)(hc->front >> 32);
             E = (uint32_t)hc->front;
-        }
+            st.centers_drawn += hc->selected;
 
-        // assign and contract
-        CLD_TRY(zero_field(offsetof(Counters, frozen), 16));  // frozen + frozen_deg
-        CLD_K(K_FINALIZE, s, k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), cumulative ? nullptr : R.get(),
-                                                             D.get(), ctr.get()));
-        CLD_K(K_FINALIZE, s, k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), g->off,
-                                                                  ctr.get(), keyS.get(), cumulative));
+            for (;;) {
+                uint32_t updated, growth_steps = 0;
+                do {
+                    ++growth_steps;
+                    ++stepid;
+                    updated = 0;
+                    if (nf > 0) {
+                        CLD_TRY(zero_field(offsetof(Counters, newly_covered), 24));  // newly_covered, front, nnext
+                        // the dense form reads the whole adjacency: worth it when the relaxers hold a large share
+                        const bool dense = pull_dense && (double)E >= (double)tun.pull_ratio * (double)g->nnz;
+                        if (dense) {
+                            CLD_K(K_PULL, s, k_pull<<<pull_grid, PT, 0, s>>>(n, (uint32_t)g->nnz, pull_chunks, crow.get(),
+                                                                              g->off, g->adj,
+                                                                              cumulative ? center.get() : nullptr, keyS.get(),
+                                                                              key.get(), delta, stamp.get(), stepid,
+                                                                              next.get(), ctr.get()));
+                        } else {
+                            const uint64_t warps = ((uint64_t)E + QC - 1) / QC;
+                            const unsigned rg = (unsigned)std::min<uint64_t>((warps + PT / 32 - 1) / (PT / 32), push_grid);
+                            CLD_K(K_RELAX, s, k_push<<<rg, PT, 0, s>>>(fv, fk, fp, cf, nf, E, g->adj, center.get(),
+                                                                        cumulative ? D.get() : nullptr, key.get(), delta,
+                                                                        stamp.get(), stepid, next.get(), ctr.get()));
+                        }
+                        CLD_LAUNCH_CHECK();
+                        CLD_K(K_SNAPSHOT, s, k_snapshot<<<max_relax_grid, 256, 0, s>>>(next.get(), key.get(), g->off, delta,
+                                                                                     fv2, fk2, fp2, cf2, ctr.get(),
+                                                                                     keyS.get()));
+                        CLD_LAUNCH_CHECK();
+                        CLD_TRY(sync_counters());
+                        updated = hc->nnext;
+                        covered += hc->newly_covered;
+                        st.edges_scanned += E;
+                        if (dense) {
+                            // algorithmic bytes of a dense step: per adjacency entry the (col, w) pair (8 B) and
+                            // the neighbour's snapshot key (8 B); per row its start and snapshot key (16 B); per
+                            // changed node its key, stamp and list slot (16 B)
+                            prof_add_bytes(K_PULL, 16.0 * (double)g->nnz + 16.0 * n + 16.0 * updated);
+                        } else {
+                            // algorithmic bytes of a pushed step: per frontier entry its slot (4 + 8 + 4 B)
+                            // and row start (8 B); per adjacency entry the (col, w) pair (8 B) and the target's
+                            // key (8 B); per changed node its key, stamp and list slot (16 B)
+                            prof_add_bytes(K_RELAX, 24.0 * nf + 16.0 * (double)E + 16.0 * updated);
+                        }
+                        prof_add_bytes(K_SNAPSHOT, 4.0 * updated + 16.0 * updated + 16.0 * updated + 16.0 * (hc->front >> 32));
+                        std::swap(fv, fv2);
+                        std::swap(fp, fp2);
+                        std::swap(fk, fk2);
+                        std::swap(cf, cf2);
+                        nf = (uint32_t)(hc->front >> 32);
+                        E = (uint32_t)hc->front;
+                    }
+                    st.steps++;
+                    st.node_updates += updated;
+                } while (updated != 0 && 2 * covered < U && (step_cap == 0 || growth_steps < step_cap));
+                if (2 * covered >= U) break;
+                bool growable = false;
+                if (delta < kDeltaMax && g->connected) {
+                    // connected graph: some covered or frozen node touches an uncovered one iff any exists
+                    growable = covered > 0 || U < n;
+                } else if (delta < kDeltaMax && g->nnz) {
+                    CLD_TRY(zero_field(offsetof(Counters, growable), 4));
+                    CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz,
+                                                                                             key.get(), ctr.get()));
+                    CLD_LAUNCH_CHECK();
+                    CLD_TRY(sync_counters());
+                    growable = hc->growable != 0;
+                }
+                if (!growable) {
+                    st.guard_exits++;
+                    break;
+                }
+                delta = (delta > kDeltaMax / 2) ? kDeltaMax : 2 * delta;
+                st.doublings++;
+                CLD_TRY(rebuild());
+                CLD_TRY(sync_counters());
+                nf = (uint32_t)(hc->front >> 32);
+                E = (uint32_t)hc->front;
+            }
+
+            // assign and contract
+            CLD_TRY(zero_field(offsetof(Counters, frozen), 16));  // frozen + frozen_deg
+            CLD_K(K_FINALIZE, s, k_finalize_d<<<gb, 256, 0, s>>>(n, key.get(), center.get(), cumulative ? nullptr : R.get(),
+                                                                 D.get(), ctr.get()));
+            CLD_K(K_FINALIZE, s, k_finalize_freeze<<<gb, 256, 0, s>>>(n, key.get(), center.get(), R.get(), D.get(), g->off,
+                                                                      ctr.get(), keyS.get(), cumulative));
+            CLD_LAUNCH_CHECK();
+            CLD_TRY(sync_counters());
+            if (hc->overflow) return fail(CLDIAM_ERR_OVERFLOW, "a cluster distance bound reached 2^32 - 1");
+            U -= hc->frozen;
+            frozen_deg += hc->frozen_deg;
+            st.stages++;
+            ++stage;
+        }
+        CLD_K(K_FINALIZE, s, k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get()));
         CLD_LAUNCH_CHECK();
-        CLD_TRY(sync_counters());
-        if (hc->overflow) return fail(CLDIAM_ERR_OVERFLOW, "a cluster distance bound reached 2^32 - 1");
-        U -= hc->frozen;
-        frozen_deg += hc->frozen_deg;
-        st.stages++;
-        ++stage;
     }
-    CLD_K(K_FINALIZE, s, k_singletons<<<gb, 256, 0, s>>>(n, center.get(), D.get()));
-    CLD_LAUNCH_CHECK();
 
     CLD_TRY(relabel_clusters(g, center.get(), cid.get(), &st.k));
     prof_flush();

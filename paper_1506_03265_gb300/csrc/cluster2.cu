@@ -260,6 +260,7 @@ cldiam_status cluster2(cldiam_graph* g, double tau, uint64_t seed, const cldiam_
     Owner owner(new cldiam_clustering());
     cldiam_clustering* cl = owner.c;
     cl->g = g;
+    cl->stream = g->stream;
     cl->max_fw_k = first->max_fw_k;
     cl->quotient_mode = first->quotient_mode;
     DBuf<uint32_t> center, D, cid, gv, stamp, frA, frB;

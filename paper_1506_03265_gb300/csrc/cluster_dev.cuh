@@ -49,6 +49,7 @@ struct Counters {
     // others
     uint32_t growable;                 // some covered/frozen node touches an uncovered one
     uint32_t overflow;                 // a D_v reached 2^32 - 1
+    unsigned long long unfrozen;       // unfrozen nodes the stage's draw saw (checks the tracked |U|)
 };
 static_assert(offsetof(Counters, pad) + 4 - offsetof(Counters, newly_covered) == 24,
               "the per-step counters form one block");
@@ -163,7 +164,7 @@ __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restric
                                            unsigned long long* __restrict__ key, uint64_t seed, uint32_t stage,
                                            uint64_t thr, Counters* ctr, uint32_t br, uint32_t nb,
                                            unsigned long long* __restrict__ keyS = nullptr) {
-    unsigned long long cnt = 0;
+    unsigned long long cnt = 0, unfrozen = 0;
     for (uint32_t base = br * blockDim.x; base < n; base += nb * blockDim.x) {
         const uint32_t v = base + threadIdx.x;
         if (v < n && __ldcg(&center[v]) == kNone) {
@@ -172,9 +173,11 @@ __device__ __forceinline__ void dev_select(uint32_t n, const uint32_t* __restric
             key[v] = sel ? (unsigned long long)v : kInfKey;
             if (keyS) keyS[v] = sel ? (unsigned long long)v : kInfKey;
             cnt += sel ? 1 : 0;
+            ++unfrozen;
         }
     }
     warp_add_u64(&ctr->selected, cnt);
+    warp_add_u64(&ctr->unfrozen, unfrozen);
 }
 
 // a4: list every relaxer with its current key: unfrozen nodes with d < Delta
@@ -288,8 +291,10 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // next list) and "newly covered" (a node that was never lowered before had
 // no key: centers and frozen nodes cannot be lowered).  Changed nodes gather
 // in a per-warp shared buffer that is appended to the next list with one
-// atomic per U x 32 or more nodes.
-template <int U>
+// atomic per U x 32 or more nodes.  L2STAGE: the frontier entries are staged
+// with L2 loads instead of cp.async through L1 (several CTAs of one job write
+// the frontier, and none of them ends its kernel between steps).
+template <int U, bool L2STAGE = false>
 __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, const unsigned long long* __restrict__ fkey,
                                           const uint32_t* __restrict__ fpre,
                                           uint32_t nf, uint32_t E, const uint2* __restrict__ adj,
@@ -322,9 +327,15 @@ __device__ __forceinline__ void dev_relax(const uint32_t* __restrict__ fbase, co
     };
     const auto stage = [&](uint32_t b, uint32_t i0, uint32_t cnt) {
         for (uint32_t j = tid; j < cnt; j += nt) {
-            cp_async_4(&sm.pre[b][j], &fpre[i0 + j]);
-            cp_async_4(&sm.base[b][j], &fbase[i0 + j]);
-            cp_async_8(&sm.key[b][j], &fkey[i0 + j]);
+            if constexpr (L2STAGE) {
+                sm.pre[b][j] = __ldcg(&fpre[i0 + j]);
+                sm.base[b][j] = __ldcg(&fbase[i0 + j]);
+                sm.key[b][j] = __ldcg(&fkey[i0 + j]);
+            } else {
+                cp_async_4(&sm.pre[b][j], &fpre[i0 + j]);
+                cp_async_4(&sm.base[b][j], &fbase[i0 + j]);
+                cp_async_8(&sm.key[b][j], &fkey[i0 + j]);
+            }
         }
     };
     uint32_t chunk = br;  // chunks br, br + nb, ...

@@ -233,6 +233,24 @@ __device__ T block_reduce(T v, Op op, T identity) {
     return v;  // valid in thread 0
 }
 
+// ---------------------------------------------------------------- timers and acquire loads
+// nanoseconds of the GPU's global timer (bounds every wait on another CTA)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // ---------------------------------------------------------------- L2 eviction priorities
 // A graph sweep streams adjacency that is read once per step; the node state
 // it looks up (keys, stamps) is far smaller and reused by every entry.  The
@@ -254,6 +272,21 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2* p, uint64_t pol) {
     asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
                  : "=r"(r.x), "=r"(r.y)
                  : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, uint64_t pol) {
+    uint32_t r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint64_t ld_stream_u64(const uint64_t* p, uint64_t pol) {
+    uint64_t r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_nc_keep_u32(const uint32_t* p, uint64_t pol) {
+    uint32_t r;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
 }
 // read-only for the whole kernel (a snapshot): may be cached in L1

@@ -409,22 +409,29 @@ __global__ void k_lcc_offsets_lists(const uint32_t* __restrict__ excl, const uin
 // The LCC's CSR straight from the two orders of the distinct edges: an edge (a, b) of the kept component
 // goes to row newid[a] after its lower entries (from U) and to row newid[b] (from T); new ids are
 // monotone, so rows stay sorted.  Weight statistics as k_lcc_copy (each undirected edge once: from U).
-// A position past the output (inconsistent input) is recorded in *err and the write skipped.
-__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info, uint64_t cap,
-                               uint32_t* __restrict__ nrow, uint2* __restrict__ nadj,
-                               unsigned long long* __restrict__ wsum, uint32_t* __restrict__ wmin,
-                               uint32_t* __restrict__ err) {
+// A position past the output (inconsistent input) is recorded in *err and the write skipped.  The row's
+// own record (info, 16 B) is read in runs (U is sorted on a, T on b); the far end's new id comes from
+// the 4-byte newid array (evict-last: it stays in L2 while the two edge lists stream through, evict-first).
+__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info,
+                               const uint32_t* __restrict__ newid, uint64_t cap, uint32_t* __restrict__ nrow,
+                               uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
+                               uint32_t* __restrict__ wmin, uint32_t* __restrict__ err) {
     const uint32_t wmask = g.wb >= 32 ? 0xFFFFFFFFu : ((1u << g.wb) - 1u);
+    const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     unsigned long long sum = 0;
     uint32_t mn = 0xFFFFFFFFu;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
-        const uint64_t u = g.U[i], t = g.T[i];
+        const uint64_t u = ld_stream_u64(g.U + i, pol_stream), t = ld_stream_u64(g.T + i, pol_stream);
         const uint32_t a = (uint32_t)(u >> g.ash), b = (uint32_t)(u >> g.wb) & g.cmask, w = (uint32_t)u & wmask;
-        const uint4 ia = info[a];
+        const uint32_t ta = (uint32_t)(t >> g.ash), tb = (uint32_t)(t >> g.wb) & g.cmask;
+        const uint4 ia = info[a], ib = info[tb];
+        // far ends (a kept row's neighbours are kept: their new ids are valid)
+        const uint32_t nb_ = ia.x != 0xFFFFFFFFu ? ld_nc_keep_u32(newid + b, pol_keep) : 0u;
+        const uint32_t na_ = ib.x != 0xFFFFFFFFu ? ld_nc_keep_u32(newid + ta, pol_keep) : 0u;
         if (ia.x != 0xFFFFFFFFu) {  // kept (then b is kept too)
             const uint32_t pos = ia.y + i;
             if (pos < cap) {
-                nadj[pos] = make_uint2(info[b].x, w);
+                nadj[pos] = make_uint2(nb_, w);
                 nrow[pos] = ia.x;
             } else {
                 atomicExch(err, 1u);
@@ -432,12 +439,10 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__
             sum += w;
             mn = w < mn ? w : mn;
         }
-        const uint32_t ta = (uint32_t)(t >> g.ash), tb = (uint32_t)(t >> g.wb) & g.cmask;
-        const uint4 ib = info[tb];
         if (ib.x != 0xFFFFFFFFu) {
             const uint32_t pos = ib.z + i;
             if (pos < cap) {
-                nadj[pos] = make_uint2(info[ta].x, (uint32_t)t & wmask);
+                nadj[pos] = make_uint2(na_, (uint32_t)t & wmask);
                 nrow[pos] = ib.x;
             } else {
                 atomicExch(err, 1u);
@@ -778,9 +783,10 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                 degx.get(), scal.get() + 4, scal.get() + 5, orig.get(), la, noff.get(), info.get()));
             CLD_LAUNCH_CHECK();
             if (mu > 0) {
-                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, info.get(), nnz ? nnz : 1,
-                                                                                nrow.get(), nadj.get(), wsum.get(),
-                                                                                scal.get() + 6, scal.get() + 8));
+                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, info.get(), newid.get(),
+                                                                                nnz ? nnz : 1, nrow.get(), nadj.get(),
+                                                                                wsum.get(), scal.get() + 6,
+                                                                                scal.get() + 8));
                 CLD_LAUNCH_CHECK();
             }
         } else {

@@ -23,6 +23,7 @@ struct cldiam_graph {
 
 struct cldiam_clustering {
     cldiam_graph* g = nullptr;
+    cudaStream_t stream = nullptr;  // the graph's stream, kept so that freeing needs no live graph
     uint32_t* center = nullptr;  // [n] center node id
     uint32_t* D = nullptr;       // [n] upper bound on dist_G(center, v)
     uint32_t* cid = nullptr;     // [n] cluster id (rank of the center id)
@@ -98,6 +99,8 @@ cldiam_status server_replay(cldiam_server* sv, const uint32_t* ids, const double
                             double* elapsed);
 uint64_t arena_device_bytes(const cldiam_arena* a);
 cudaStream_t arena_stream(const cldiam_arena* a);
+
+cldiam_status arena_job_times(const cldiam_arena* a, uint32_t count, double* start_s, double* end_s);
 // adjacency entries of the listed graphs (ids out of range count 0)
 uint64_t arena_entries(const cldiam_arena* a, const uint32_t* ids, uint32_t count);
 

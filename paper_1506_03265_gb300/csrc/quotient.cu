@@ -62,26 +62,44 @@ __global__ void k_q_emit(const uint32_t* __restrict__ row, const uint2* __restri
 // atomicMin (it stays in L2), then read the rows out in column order.  The quotient is symmetric
 // (an edge's weight D_u + w + D_v does not depend on its direction), so each undirected edge is
 // folded once, from its u < v entry, into the upper triangle, which is then mirrored.
-__global__ void k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj, uint64_t nnz,
-                               const uint2* __restrict__ cd, uint32_t k, uint32_t* __restrict__ M,
-                               uint32_t* __restrict__ overflow) {
+constexpr int QE_U = 4;  // entries per thread per sweep, loads issued together
+__global__ void __launch_bounds__(256) k_q_dense_emit(const uint32_t* __restrict__ row, const uint2* __restrict__ adj,
+                                                      uint64_t nnz, const uint2* __restrict__ cd, uint32_t k,
+                                                      uint32_t* __restrict__ M, uint32_t* __restrict__ overflow) {
+    // the CSR streams through once (evict-first, no L1); (cid, D) and the matrix are reused (evict-last)
+    const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     bool ovf = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = row[i];
-        const uint2 e = adj[i];
-        if (u >= e.x) continue;
-        const uint2 pu = cd[u], pv = cd[e.x];
-        const uint32_t a = pu.x, b = pv.x;
-        if (a == b) continue;
-        uint64_t s = (uint64_t)pu.y + e.y + pv.y;
-        if (s >= 0xFFFFFFFFull) {
-            ovf = true;
-            s = 0xFFFFFFFEull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * QE_U;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x * QE_U + threadIdx.x; base < nnz; base += stride) {
+        uint32_t u[QE_U];
+        uint2 e[QE_U];
+#pragma unroll
+        for (int j = 0; j < QE_U; ++j) {
+            const uint64_t i = base + (uint64_t)j * blockDim.x;
+            u[j] = i < nnz ? ld_stream_u32(row + i, pol_stream) : 0u;
+            e[j] = i < nnz ? ld_stream_u2(adj + i, pol_stream) : make_uint2(0u, 0u);
         }
-        uint32_t* m = &M[(size_t)min(a, b) * k + max(a, b)];
-        // entries only decrease, so a stale copy in this SM's L1 is never below the current value: reading
-        // through L1 can let a useless atomicMin through but never hold back one that lowers the entry
-        if ((uint32_t)s < __ldca(m)) atomicMin(m, (uint32_t)s);
+        unsigned long long pu[QE_U], pv[QE_U];
+#pragma unroll
+        for (int j = 0; j < QE_U; ++j) {
+            const bool take = u[j] < e[j].x;  // each undirected edge once (padding has u = e.x = 0)
+            pu[j] = take ? ld_nc_keep_u64(reinterpret_cast<const unsigned long long*>(cd) + u[j], pol_keep) : 0ull;
+            pv[j] = take ? ld_nc_keep_u64(reinterpret_cast<const unsigned long long*>(cd) + e[j].x, pol_keep) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < QE_U; ++j) {
+            const uint32_t a = (uint32_t)pu[j], b = (uint32_t)pv[j];
+            if (!(u[j] < e[j].x) || a == b) continue;
+            uint64_t s = (pu[j] >> 32) + e[j].y + (pv[j] >> 32);
+            if (s >= 0xFFFFFFFFull) {
+                ovf = true;
+                s = 0xFFFFFFFEull;
+            }
+            uint32_t* m = &M[(size_t)min(a, b) * k + max(a, b)];
+            // entries only decrease, so a stale copy in this SM's L1 is never below the current value: reading
+            // through L1 can let a useless atomicMin through but never hold back one that lowers the entry
+            if ((uint32_t)s < __ldca(m)) atomicMin(m, (uint32_t)s);
+        }
     }
     if (__any_sync(0xffffffffu, ovf) && lane_id() == 0) atomicExch(overflow, 1u);
 }
@@ -155,8 +173,8 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
         DBuf<uint2> cd;
         CLD_TRY(cd.alloc(g->n, s));
         CLD_K(K_QUOTIENT, s, k_q_pack_cd<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, c->cid, c->D, cd.get()));
-        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, cd.get(), k,
-                                                                                M.get(), scal.get()));
+        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for((g->nnz + QE_U - 1) / QE_U, 256), 256, 0, s>>>(
+                                 g->row, g->adj, g->nnz, cd.get(), k, M.get(), scal.get()));
         CLD_LAUNCH_CHECK();
     }
     {

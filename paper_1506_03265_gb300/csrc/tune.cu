@@ -52,6 +52,7 @@ void merge_unset(cldiam_tuning& into, const cldiam_tuning& from) {
     if (into.apsp_fw_density == 0) into.apsp_fw_density = from.apsp_fw_density;
     if (into.batch_fw_k == 0) into.batch_fw_k = from.batch_fw_k;
     if (into.sssp_delta_scale == 0.f) into.sssp_delta_scale = from.sssp_delta_scale;
+    if (into.batch_split == 0) into.batch_split = from.batch_split;
 }
 
 // Candidate values of each knob (bit i of a knob mask = knob i).
@@ -68,6 +69,7 @@ const std::vector<Knob>& knob_table() {
         {"apsp_fw_density", {4, 8, 16}},
         {"batch_fw_k", {64, 128, 200}},
         {"sssp_delta_scale", {1, 2, 4, 8}},
+        {"batch_split", {1, 2}},
     };
     return t;
 }
@@ -80,7 +82,8 @@ double knob_get(const cldiam_tuning& t, size_t i) {
         case 3: return t.apsp_sources_per_cta;
         case 4: return t.apsp_fw_density;
         case 5: return t.batch_fw_k;
-        default: return t.sssp_delta_scale;
+        case 6: return t.sssp_delta_scale;
+        default: return t.batch_split;
     }
 }
 void knob_set(cldiam_tuning& t, size_t i, double v) {
@@ -91,7 +94,8 @@ void knob_set(cldiam_tuning& t, size_t i, double v) {
         case 3: t.apsp_sources_per_cta = (uint32_t)v; break;
         case 4: t.apsp_fw_density = (uint32_t)v; break;
         case 5: t.batch_fw_k = (uint32_t)v; break;
-        default: t.sssp_delta_scale = (float)v; break;
+        case 6: t.sssp_delta_scale = (float)v; break;
+        default: t.batch_split = (uint32_t)v; break;
     }
 }
 
@@ -110,6 +114,7 @@ cldiam_tuning tuning_defaults_filled(const cldiam_tuning& t) {
     if (r.apsp_fw_density == 0) r.apsp_fw_density = 8;
     if (r.batch_fw_k == 0) r.batch_fw_k = 200;
     if (r.sssp_delta_scale == 0.f) r.sssp_delta_scale = 1.f;
+    if (r.batch_split == 0) r.batch_split = 2;
     return r;
 }
 
@@ -124,6 +129,7 @@ cldiam_status tuning_check(const cldiam_tuning& t) {
     if (t.batch_fw_k > 200) return fail(CLDIAM_ERR_INVALID_ARG, "batch_fw_k > 200");
     if (!(t.sssp_delta_scale == 0.f || t.sssp_delta_scale >= 1.f) || !(t.sssp_delta_scale < 1e9f))
         return fail(CLDIAM_ERR_INVALID_ARG, "sssp_delta_scale must be 0 or in [1, 1e9)");
+    if (t.batch_split > 2) return fail(CLDIAM_ERR_INVALID_ARG, "batch_split must be 0, 1 or 2");
     for (uint32_t r : t.reserved)
         if (r) return fail(CLDIAM_ERR_INVALID_ARG, "reserved tuning fields must be 0");
     return CLDIAM_OK;
@@ -167,7 +173,9 @@ cldiam_status search(const cldiam_tuning& start, uint32_t mask, cldiam_tune_meas
     double cur_t = 0.0;
     uint64_t ref = 0;
     CLD_TRY(fn(&cur, user, &cur_t, &ref));
-    for (size_t i = 0; i < table.size(); ++i) {
+    static const size_t order[] = {0, 1, 2, 3, 4, 5, 6, 7};
+    static_assert(sizeof(order) / sizeof(order[0]) == 8, "one entry per knob");
+    for (size_t i : order) {
         if (!(mask & (1u << i))) continue;
         const float at_start = (float)knob_get(cur, i);  // measured already (as part of cur)
         for (double v : table[i].values) {
@@ -328,7 +336,7 @@ void cache_put(int device, uint32_t cls, const cldiam_tuning& t, uint32_t mask) 
 }
 
 constexpr uint32_t kGraphKnobs = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3) | (1u << 4);
-constexpr uint32_t kBatchKnobs = 1u << 5;
+constexpr uint32_t kBatchKnobs = (1u << 7) | (1u << 5);
 constexpr uint32_t kSsspKnobs = 1u << 6;
 
 cldiam_tuning start_point() {
@@ -419,14 +427,15 @@ cldiam_status cldiam_tuning_cache_load(const char* path) {
         if (line[0] == '#' || line[0] == '\n') continue;
         int dev = 0;
         unsigned cls = 0;
-        double v[7];
-        if (sscanf(line, "%d %u %lf %lf %lf %lf %lf %lf %lf", &dev, &cls, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
-                   &v[6]) != 9) {
+        double v[8];
+        if (sscanf(line, "%d %u %lf %lf %lf %lf %lf %lf %lf %lf", &dev, &cls, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                   &v[6], &v[7]) != 10) {
             st = fail(CLDIAM_ERR_INVALID_ARG, "malformed tuning cache line");
             break;
         }
         cldiam_tuning t{};
-        for (size_t i = 0; i < 7; ++i) knob_set(t, i, v[i]);
+        static_assert(sizeof(v) / sizeof(v[0]) == 8, "one column per knob");
+        for (size_t i = 0; i < 8; ++i) knob_set(t, i, v[i]);
         st = tuning_check(t);
         if (st == CLDIAM_OK) rows.push_back({{dev, cls}, t});
     }

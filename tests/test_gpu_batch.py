@@ -99,3 +99,59 @@ def test_budget_admission(cd):
     with pytest.raises(cd.CldiamError) as ei:
         arena.add(e.src, e.dst, e.w, e.n)
     assert ei.value.status == -2
+
+
+@pytest.fixture(scope="module")
+def split_arena(cd):
+    """Graphs large enough to outweigh the per-CTA average of a small batch (they run on the one-graph
+    path first), a large disconnected one (no LCC), and small ones (the persistent launch)."""
+    arena = cd.arena_create()
+    big = [inputs.rmat(16, 16, 1000, 21), inputs.grid(400, 1000, 22), inputs.road_mesh(512, 1000, 23)]
+    rng = np.random.default_rng(24)
+    n = 200_000
+    disc = inputs.EdgeList(n, rng.integers(0, n, 160_000).astype(np.uint32),
+                           rng.integers(0, n, 160_000).astype(np.uint32),
+                           rng.integers(1, 1000, 160_000).astype(np.uint32))
+    small = [inputs.rmat(10, 8, 1000, 25), inputs.grid(30, 1000, 26)]
+    graphs = [(arena.add(e.src, e.dst, e.w, e.n), e) for e in big + small]
+    graphs.append((arena.add(disc.src, disc.dst, disc.w, disc.n, lcc=False), disc))
+    return arena, graphs
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_split_batches_match_one_graph_path(cd, split_arena, split):
+    arena, graphs = split_arena
+    ids = [gid for gid, _ in graphs] + [graphs[0][0]]
+    taus = [tau_for(arena.graph(gid).n) for gid in ids]
+    taus[-1] *= 30  # R-MAT 16 with k ~ 2,000: above the kernel's dense quotient capacity when in the launch
+    seeds = [40 + i for i in range(len(ids))]
+    cd.tuning_set(batch_split=split)
+    try:
+        for mode, cap in ((cd.CONTRACT_RESET, 0), (cd.CONTRACT_CUMULATIVE, 3)):
+            res, st = arena.run(ids, taus, seeds, contract_mode=mode, step_cap=cap)
+            assert all(x == 0 for x in st)
+            for gid, tau, seed, r in zip(ids, taus, seeds, res):
+                c = cd.cluster(arena.graph(gid), tau, seed, contract_mode=mode, step_cap=cap)
+                ref = cd.estimate(cd.quotient_build(c))
+                assert {f: r[f] for f in FIELDS} == {f: ref[f] for f in FIELDS}, (gid, mode)
+            start, end = arena.job_times(len(ids))
+            assert np.all(end >= start) and start.min() == 0.0
+    finally:
+        cd.tuning_set()
+
+
+def test_split_batch_matches_oracle(cd, split_arena):
+    arena, graphs = split_arena
+    ids = [gid for gid, _ in graphs]
+    taus = [tau_for(arena.graph(gid).n) for gid in ids]
+    seeds = [70 + i for i in range(len(ids))]
+    res, st = arena.run(ids, taus, seeds)
+    assert all(x == 0 for x in st)
+    for (gid, e), tau, seed, r in zip(graphs, taus, seeds, res):
+        if gid == graphs[-1][0]:  # no LCC: the oracle's CSR without it
+            og = oracle.build_csr(e.n, e.src, e.dst, e.w, lcc=False)
+            ores, ocl, oq = oracle.cldiam(og, tau, seed)
+            assert (r["k"], r["phi_gc"], r["phi_approx"], r["stages"]) == (ores.k, ores.phi_gc, ores.phi_approx,
+                                                                           ocl.stats["stages"])
+        else:
+            assert {f: r[f] for f in ORACLE_FIELDS} == oracle_result(e, tau, seed), (gid, e.n)

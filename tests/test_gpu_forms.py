@@ -14,7 +14,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-FORMS = {"push": -1.0, "pull": 1e-9}  # pull_ratio: never dense / dense at every step
+# pull_ratio -1: never dense, 1e-9: dense at every step, default: switching by the relaxers' share
+FORMS = {"push": {"pull_ratio": -1.0}, "pull": {"pull_ratio": 1e-9}, "mixed": {}}
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +67,7 @@ def check(cd, e, tau, seed, mode=0, cap=0, d0_mode=0):
 @pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("gi", range(len(GRAPHS)))
 def test_forms_match_oracle(cd, form, gi):
-    cd.tuning_set(pull_ratio=FORMS[form])
+    cd.tuning_set(**FORMS[form])
     e = GRAPHS[gi]
     cd.profile_reset()
     for tau, seed in ((0.3, 1), (2.0, 7)):
@@ -75,14 +76,14 @@ def test_forms_match_oracle(cd, form, gi):
     prof = cd.profile_get()
     if form == "pull":
         assert prof["relax_pull"]["launches"] > 0 and prof["relax"]["launches"] == 0
-    else:
+    elif form == "push":
         assert prof["relax_pull"]["launches"] == 0
 
 
 @pytest.mark.parametrize("form", list(FORMS))
 @pytest.mark.parametrize("mode,cap", [(1, 0), (0, 1), (1, 2), (0, 3)])
 def test_forms_options(cd, form, mode, cap):
-    cd.tuning_set(pull_ratio=FORMS[form])
+    cd.tuning_set(**FORMS[form])
     for e in (GRAPHS[1], GRAPHS[4], GRAPHS[6]):
         check(cd, e, 0.4, 5, mode=mode, cap=cap)
 
@@ -116,3 +117,48 @@ def test_pull_needs_every_row_to_have_an_entry(cd):
     center, D, _ = c.copy()
     assert np.array_equal(center, ocl.center) and np.array_equal(D.astype(np.uint64), ocl.D)
     assert cd.profile_get()["relax_pull"]["launches"] == 0
+    cd.tuning_set()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_disconnected_graphs(cd, seed):
+    # no LCC: stages that draw no center in a component end at the fixed-point guard
+    rng = np.random.default_rng(200 + seed)
+    n = 300
+    src = rng.integers(0, n, 200).astype(np.uint32)
+    dst = rng.integers(0, n, 200).astype(np.uint32)
+    w = rng.integers(1, 50, 200).astype(np.uint32)
+    g = cd.build_csr(src, dst, w, n, lcc=False)
+    og = oracle.build_csr(n, src, dst, w, lcc=False)
+    for ratio in (-1.0, 1e-9):
+        cd.tuning_set(pull_ratio=ratio)
+        c = cd.cluster(g, 0.2, seed)
+        ocl = oracle.cluster(og, 0.2, seed, oracle.delta0(og))
+        center, D, _ = c.copy()
+        assert np.array_equal(center, ocl.center) and np.array_equal(D.astype(np.uint64), ocl.D)
+        info = c.info()
+        for f in ("stages", "steps", "doublings", "delta_end", "guard_exits", "node_updates", "centers_drawn"):
+            assert info[f] == ocl.stats[f], f
+    cd.tuning_set()
+
+
+@pytest.mark.parametrize("which", ["road_mesh_2048", "rmat_16"])
+def test_repeated_runs_give_the_same_integers(cd, which):
+    # every call is deterministic: repeated runs in both growing-step forms give the same centers, D and counters
+    e = inputs.road_mesh(2048, 1000, 3) if which == "road_mesh_2048" else inputs.rmat(16, 16, 1000, 8)
+    g = cd.build_csr(e.src, e.dst, e.w, e.n)
+    tau = 3.0 if which == "road_mesh_2048" else 1.5
+    fields = ("stages", "steps", "doublings", "delta_end", "guard_exits", "node_updates", "centers_drawn")
+    ref = cd.cluster(g, tau, 3)
+    rc, rD, _ = ref.copy()
+    rinfo = {f: ref.info()[f] for f in fields}
+    try:
+        for ratio in (-1.0, 0.3, 1e-9):
+            cd.tuning_set(pull_ratio=ratio)
+            for it in range(8):
+                c = cd.cluster(g, tau, 3)
+                center, D, _ = c.copy()
+                assert np.array_equal(center, rc) and np.array_equal(D, rD), (ratio, it)
+                assert {f: c.info()[f] for f in fields} == rinfo, (ratio, it)
+    finally:
+        cd.tuning_set()

@@ -16,9 +16,11 @@ CANDIDATES = {  # the library's fixed candidate lists, restated for the syntheti
     "apsp_fw_density": [4, 8, 16],
     "batch_fw_k": [64, 128, 200],
     "sssp_delta_scale": [1, 2, 4, 8],
+    "batch_split": [1, 2],
 }
 DEFAULTS = {"pull_ratio": 0.3, "relax_ctas_per_sm": 0, "dense_quotient_k": 4096, "apsp_sources_per_cta": 0,
-            "apsp_fw_density": 8, "batch_fw_k": 200, "sssp_delta_scale": 1.0}
+            "apsp_fw_density": 8, "batch_fw_k": 200, "sssp_delta_scale": 1.0,
+            "batch_split": 2}
 
 
 @pytest.fixture(autouse=True)
@@ -137,7 +139,7 @@ def test_cache_save_and_load(tmp_path):
     with pytest.raises(cd.CldiamError):
         cd.tuning_cache_load(bad)
     with open(bad, "w") as f:
-        f.write("0 3 0.5 0 4096 3 8 200 1\n")  # apsp_sources_per_cta = 3 is out of range
+        f.write("0 3 0.5 0 4096 3 8 200 1 2\n")  # apsp_sources_per_cta = 3 is out of range
     with pytest.raises(cd.CldiamError):
         cd.tuning_cache_load(bad)
     with pytest.raises(cd.CldiamError):
@@ -146,7 +148,8 @@ def test_cache_save_and_load(tmp_path):
 
 @pytest.mark.parametrize("knobs", [{"relax_ctas_per_sm": 65}, {"dense_quotient_k": 70000},
                                    {"apsp_sources_per_cta": 2}, {"batch_fw_k": 201},
-                                   {"sssp_delta_scale": 0.5}, {"pull_ratio": float("nan")}])
+                                   {"sssp_delta_scale": 0.5}, {"pull_ratio": float("nan")},
+                                   {"batch_split": 3}])
 def test_tuning_set_rejects_out_of_range(knobs):
     with pytest.raises(cd.CldiamError) as ei:
         cd.tuning_set(**knobs)
