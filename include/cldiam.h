@@ -289,10 +289,10 @@ cldiam_status cldiam_run(const uint32_t* src, const uint32_t* dst, const uint32_
  * cluster): graphs are packed into one device-resident CSR arena and a batch
  * of (graph, tau, seed) jobs runs the whole method -- CLUSTER (Algorithm 1),
  * the weighted quotient graph and Phi_approx (Section 4) -- in one persistent
- * launch, one graph per CTA at a time, largest graphs first.  A graph that
- * alone outweighs the batch's per-CTA average would hold its CTA past the
- * end of an even split: such graphs run first on the one-graph path with the
- * whole device (cldiam_tuning.batch_split).  Every result is
+ * launch, one graph per CTA at a time, largest graphs first.  The launch
+ * ends with its largest graph on one CTA or with the even split of all work,
+ * whichever is later; the largest graphs may therefore run first on the
+ * one-graph path with the whole device (cldiam_tuning.batch_split).  Every result is
  * identical to cldiam_cluster + cldiam_quotient_build + cldiam_estimate on the
  * same graph, tau and seed with the same options.
  */
@@ -376,11 +376,11 @@ typedef struct {
                                       Floyd-Warshall in shared memory; 0 = 200                     */
     float sssp_delta_scale;        /* Delta-stepping with delta = 0: Delta = this x the average
                                       weight (>= 1); 0 = 1                                          */
-    uint32_t batch_split;          /* many-graph form: 2 = a graph whose work (entries + nodes)
-                                      exceeds the batch's per-CTA average (and that has at least
-                                      2^16 entries) runs first on the one-graph path with the whole
-                                      device, the rest in the persistent launch; 1 = every graph in
-                                      the launch; 0 = 2                                             */
+    uint32_t batch_split;          /* many-graph form: 2 = the k largest graphs (each with at least
+                                      2^16 entries) run first on the one-graph path with the whole
+                                      device, k chosen by a makespan model (one CTA's rate in the
+                                      launch against a fixed cost per graph on the one-graph path);
+                                      1 = every graph in the persistent launch; 0 = 2              */
     uint32_t reserved[8];          /* must be 0                                                     */
 } cldiam_tuning;
 
