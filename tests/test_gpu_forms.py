@@ -74,10 +74,11 @@ def test_forms_match_oracle(cd, form, gi):
         check(cd, e, tau, seed)
     check(cd, e, 0.5, 3, d0_mode=1)  # Delta from the minimum weight: many doublings
     prof = cd.profile_get()
+    # queued steps launch both forms and the one not taken returns at once: the work shows in the bytes
     if form == "pull":
-        assert prof["relax_pull"]["launches"] > 0 and prof["relax"]["launches"] == 0
+        assert prof["relax_pull"]["bytes"] > 0 and prof["relax"]["bytes"] == 0
     elif form == "push":
-        assert prof["relax_pull"]["launches"] == 0
+        assert prof["relax_pull"]["launches"] == 0 and prof["relax"]["bytes"] > 0
 
 
 @pytest.mark.parametrize("form", list(FORMS))
@@ -116,7 +117,7 @@ def test_pull_needs_every_row_to_have_an_entry(cd):
     ocl = oracle.cluster(og, 0.2, 1, oracle.delta0(og))
     center, D, _ = c.copy()
     assert np.array_equal(center, ocl.center) and np.array_equal(D.astype(np.uint64), ocl.D)
-    assert cd.profile_get()["relax_pull"]["launches"] == 0
+    assert cd.profile_get()["relax_pull"]["bytes"] == 0
     cd.tuning_set()
 
 
