@@ -367,7 +367,8 @@ cldiam_status unique_min_sorted_u32(const uint32_t* keys, const uint32_t* vals, 
 // number.  With hist2 (ceil(vb / 8) x 256 words, zeroed) the counting pass also adds up the 8-bit digits
 // of every distinct item's b (bits [wb, wb + vb)), pass by pass: the histograms of a following sort on b.
 cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64_t* out, uint32_t* total_dev,
-                               cudaStream_t s, uint32_t* hist2 = nullptr);
+                               cudaStream_t s, uint32_t* hist2 = nullptr, uint32_t* ustart = nullptr,
+                               uint32_t* uend = nullptr);
 
 // CSR offsets off[0..n] of entries whose (sorted) row ids are row[0..nnz):
 // off[u] = index of the first entry with row >= u.  No atomics, no scan.

@@ -103,13 +103,12 @@ __global__ void k_emit_canon(const uint32_t* __restrict__ src, const uint32_t* _
 
 // Distinct edges in two orders: U by (a, b) and T by (b, a) (a < b).  Row x of the symmetric CSR is its
 // lower entries (the a of T's run b = x, ascending) followed by its upper entries (the b of U's run
-// a = x, ascending).  Run boundaries give each row's two counts.
+// a = x, ascending).  Run boundaries give each row's two counts: U's are written by the de-duplication
+// that produces U, T's here.
 // (also the directed entry count 2 mu into *nnz)
-__global__ void k_canon_runs(const uint64_t* __restrict__ U, const uint64_t* __restrict__ T, uint32_t mu, int vb,
-                             int wb, uint32_t* __restrict__ ustart, uint32_t* __restrict__ uend,
+__global__ void k_canon_runs(const uint64_t* __restrict__ T, uint32_t mu, int vb, int wb,
                              uint32_t* __restrict__ tstart, uint32_t* __restrict__ tend, uint32_t* __restrict__ nnz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *nnz = 2 * mu;
-    const int ash = 64 - vb;
     const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
     constexpr uint32_t kNo = 0xFFFFFFFFu;  // no neighbour (ids are below n <= 2^32 - 1)
     const unsigned l = lane_id();
@@ -118,21 +117,11 @@ __global__ void k_canon_runs(const uint64_t* __restrict__ U, const uint64_t* __r
     for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < mu; i0 += stride) {
         const uint32_t i = i0 + l;
         const bool ok = i < mu;
-        const uint32_t a = ok ? (uint32_t)(U[i] >> ash) : kNo;
         const uint32_t b = ok ? (uint32_t)(T[i] >> wb) & cmask : kNo;
-        uint32_t ap = __shfl_up_sync(0xffffffffu, a, 1), an = __shfl_down_sync(0xffffffffu, a, 1);
         uint32_t bp = __shfl_up_sync(0xffffffffu, b, 1), bn = __shfl_down_sync(0xffffffffu, b, 1);
-        if (l == 0) {
-            ap = ok && i > 0 ? (uint32_t)(U[i - 1] >> ash) : kNo;
-            bp = ok && i > 0 ? (uint32_t)(T[i - 1] >> wb) & cmask : kNo;
-        }
-        if (l == 31) {
-            an = i + 1 < mu ? (uint32_t)(U[i + 1] >> ash) : kNo;
-            bn = i + 1 < mu ? (uint32_t)(T[i + 1] >> wb) & cmask : kNo;
-        }
+        if (l == 0) bp = ok && i > 0 ? (uint32_t)(T[i - 1] >> wb) & cmask : kNo;
+        if (l == 31) bn = i + 1 < mu ? (uint32_t)(T[i + 1] >> wb) & cmask : kNo;
         if (!ok) continue;
-        if (ap != a) ustart[a] = i;
-        if (an != a) uend[a] = i + 1;
         if (bp != b) tstart[b] = i;
         if (bn != b) tend[b] = i + 1;
     }
@@ -609,15 +598,17 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             const int npass2 = (vb + 7) / 8;
             CLD_TRY(hist2.alloc((size_t)npass2 * 256, s));
             CLD_CUDA(cudaMemsetAsync(hist2.get(), 0, (size_t)npass2 * 256 * 4, s));
-            CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s, hist2.get()));
+            // every row's run bounds in both orders; the de-duplication writes the first order's
+            CLD_TRY(runs.alloc(4 * (size_t)n, s));
+            CLD_CUDA(cudaMemsetAsync(runs.get(), 0, 4 * (size_t)n * 4, s));
+            CLD_TRY(unique_items_u64(alt ? items2.get() : items.get(), m, vb, uniq.get(), scal.get() + 1, s, hist2.get(),
+                                     runs.get(), runs.get() + n));
             CLD_CUDA(cudaMemcpyAsync(hbad + 1, scal.get() + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             CLD_CUDA(cudaStreamSynchronize(s));
             mu = hbad[1];  // distinct undirected edges
             bool alt2 = false;
             CLD_TRY(radix_sort_keys_u64(items.get(), items2.get(), mu, wb, vb, &alt2, s, scal.get() + 8, uniq.get(),
                                         hist2.get()));
-            CLD_TRY(runs.alloc(4 * (size_t)n, s));
-            CLD_CUDA(cudaMemsetAsync(runs.get(), 0, 4 * (size_t)n * 4, s));
             la.U = uniq.get();
             la.T = alt2 ? items2.get() : items.get();
             la.ustart = runs.get();
@@ -629,9 +620,8 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             la.cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
             uint32_t* r0 = runs.get();
             if (mu > 0) {
-                CLD_K(K_CSR, s, k_canon_runs<<<grid_for(mu, 256), 256, 0, s>>>(la.U, la.T, mu, vb, wb, r0, r0 + n,
-                                                                              r0 + 2 * (size_t)n, r0 + 3 * (size_t)n,
-                                                                              scal.get() + 1));
+                CLD_K(K_CSR, s, k_canon_runs<<<grid_for(mu, 256), 256, 0, s>>>(la.T, mu, vb, wb, r0 + 2 * (size_t)n,
+                                                                              r0 + 3 * (size_t)n, scal.get() + 1));
                 CLD_LAUNCH_CHECK();
             }
             if (!lcc) {

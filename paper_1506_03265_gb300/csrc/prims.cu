@@ -894,7 +894,8 @@ __global__ void __launch_bounds__(UP_THREADS) k_unique_packed_count(const uint64
 // a block barrier, and the tile's last run is followed into later tiles by one warp.
 __global__ void __launch_bounds__(UP_THREADS, 4)
     k_unique_items(const uint64_t* __restrict__ items, uint32_t cnt, int vb, unsigned long long* __restrict__ out,
-                   uint32_t* __restrict__ total, const uint32_t* __restrict__ first) {
+                   uint32_t* __restrict__ total, const uint32_t* __restrict__ first, uint32_t* __restrict__ ustart,
+                   uint32_t* __restrict__ uend) {
     __shared__ uint32_t s_woff[UP_WARPS];
     __shared__ uint32_t s_first, s_count;
     const unsigned tid = threadIdx.x, w = tid >> 5, l = lane_id();
@@ -915,12 +916,14 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
     if (l == 0 && wstart < rem && tbase + wstart > 0) carry = it[(int64_t)wstart - 1];
     uint32_t head = 0, run = 0;
     uint32_t ex_pk[UP_ITEMS / 4];
+    uint32_t newrow = 0;  // bit i: item i heads a run whose row (the a bits) differs from the previous item's
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i) {
         const uint64_t rot = __shfl_sync(0xffffffffu, x[i], (l + 31) & 31);
         const uint64_t prev = l == 0 ? carry : rot;
         carry = rot;
         const bool f = up_head(prev, x[i], same_lim, valid_lim);
+        if (f && (prev >= valid_lim || (prev ^ x[i]) >> (wb + vb) != 0)) newrow |= 1u << i;
         const unsigned bal = __ballot_sync(0xffffffffu, f);
         const uint32_t ex = run + (uint32_t)__popc(bal & lanemask_lt());
         run += (uint32_t)__popc(bal);
@@ -946,7 +949,22 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
     const uint32_t woff = s_woff[w], tfirst = s_first;
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i)
-        if ((head >> i) & 1u) out[woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu)] = x[i];
+        if ((head >> i) & 1u) {
+            const uint32_t r = woff + ((ex_pk[i / 4] >> (8 * (i % 4))) & 0xFFu);
+            out[r] = x[i];
+            // run bounds of the rows: a distinct edge whose row differs from the previous one's starts its
+            // row's run and ends the previous row's (the last row's end is set after the pass)
+            if (ustart && ((newrow >> i) & 1u)) {
+                ustart[(uint32_t)(x[i] >> (wb + vb))] = r;
+                if (r > 0) {
+                    // the previous distinct edge is any item before this one in the run order: the item at
+                    // position (tile start + this item's position) - 1 of the sorted input
+                    const uint32_t li = wstart + (uint32_t)i * 32 + l;
+                    const uint64_t pv = items[tbase + li - 1];
+                    uend[(uint32_t)(pv >> (wb + vb))] = r;
+                }
+            }
+        }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < UP_ITEMS; ++i) {
@@ -973,8 +991,15 @@ __global__ void __launch_bounds__(UP_THREADS, 4)
     }
 }
 
+// the last row's run ends at the number of distinct edges
+__global__ void k_last_uend(const uint64_t* __restrict__ out, const uint32_t* __restrict__ total, int shift,
+                            uint32_t* __restrict__ uend) {
+    const uint32_t t = *total;
+    if (t > 0) uend[(uint32_t)(out[t - 1] >> shift)] = t;
+}
+
 cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64_t* out, uint32_t* total_dev,
-                               cudaStream_t s, uint32_t* hist2) {
+                               cudaStream_t s, uint32_t* hist2, uint32_t* ustart, uint32_t* uend) {
     if (cnt == 0) {
         CLD_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
         return CLDIAM_OK;
@@ -992,7 +1017,8 @@ cldiam_status unique_items_u64(const uint64_t* items, size_t cnt, int vb, uint64
     CLD_TRY(scan_exclusive_u32(heads.get(), first.get(), ntiles, nullptr, s));
     CLD_K(K_CSR, s, k_unique_items<<<ntiles, UP_THREADS, 0, s>>>(items, (uint32_t)cnt, vb,
                                                                  reinterpret_cast<unsigned long long*>(out), total_dev,
-                                                                 first.get()));
+                                                                 first.get(), ustart, uend));
+    if (ustart) CLD_K(K_CSR, s, k_last_uend<<<1, 1, 0, s>>>(out, total_dev, 64 - vb, uend));
     CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
