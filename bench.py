@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--plain-sample-every", type=int, default=10)
     ap.add_argument("--no-delta0-experiment", action="store_true", help="skip the initial-Delta experiment")
     ap.add_argument("--no-cluster2", action="store_true", help="skip the CLUSTER2 (Algorithm 2) leg")
+    ap.add_argument("--no-tuned-cluster", action="store_true",
+                    help="skip the autotuned CLUSTER + quotient + estimate leg on the headline graph")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run one pipeline pass on the workload and exit (for ncu captures)")
     ap.add_argument("--profile-sssp", action="store_true",
@@ -451,7 +453,39 @@ def roofline_of(prof, classes, peak, peaks, workload, tkey=None):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
 
 
-def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None):
+def tuned_cluster_leg(cd, g, tau, seed, stream, reps=5):
+    """CLUSTER + quotient + estimate on a built CSR with the library's default knobs, then after
+    cldiam_autotune_graph picked and cached knobs for this size class; same results required."""
+    import torch
+    cd.profile_set_timing([])
+
+    def timed():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        r = None
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            r = cd.estimate(cd.quotient_build(cd.cluster(g, tau, seed)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    cd.tuning_cache_clear()
+    timed()  # warm-up
+    ms_def, r_def = timed()
+    best = cd.autotune_graph(g, tau, seed, reps=2)
+    ms_tuned, r_tuned = timed()
+    cd.tuning_cache_clear()
+    keys = ("pull_ratio", "relax_ctas_per_sm", "dense_quotient_k", "apsp_sources_per_cta", "apsp_fw_density")
+    return {"default_ms": round(ms_def, 3), "tuned_ms": round(ms_tuned, 3),
+            "knobs": {k: (round(best[k], 3) if isinstance(best[k], float) else best[k]) for k in keys},
+            "identical": bool(r_def == r_tuned),
+            "what": ("CLUSTER + quotient + estimate on the built CSR (CUDA events, mean of 5 runs) with the default "
+                     "knobs, then with the knobs cldiam_autotune_graph picked and cached for this size class")}
+
+
+def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None, tune=False):
     """Time `steps` whole CL-DIAM passes (CSR build .. estimate) on one workload with its edge list resident
     in HBM; check the first pass against the oracle's stored result."""
     import torch
@@ -569,9 +603,14 @@ def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None)
         "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
         "gpu_launches": sum(v["launches"] for v in prof.values()),
+        "tuned_cluster": None,
         "wall": (t_wall0, t_wall1),
         "in_bytes": 12 * e.m, "nnz": nnz,
     }
+    if tune:
+        g = cd.build_csr(src_d, dst_d, w_d, e.n, lcc=True, stream=stream)
+        out["tuned_cluster"] = tuned_cluster_leg(cd, g, wl.tau, wl.seed, stream)
+        del g
     return out, (e, src_d, dst_d, w_d, r)
 
 
@@ -596,7 +635,8 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     sampler.wait_first()
-    head, (e, src_d, dst_d, w_d, r) = measure_workload(cd, args.workload, args.steps, args.warmup, stream, dist, local)
+    head, (e, src_d, dst_d, w_d, r) = measure_workload(cd, args.workload, args.steps, args.warmup, stream, dist, local,
+                                                       tune=not args.no_tuned_cluster)
     t_wall0, t_wall1 = head.pop("wall")
     clocks = sampler.summary(t_wall0, t_wall1)
     in_bytes = head.pop("in_bytes")
@@ -679,6 +719,7 @@ def run_gpu(args):
         "e2e": e2e,
         "roofline": head["roofline"],
         "relax_roofline": head["relax_roofline"],
+        "tuned_cluster": head["tuned_cluster"],
         "kernel_shares": head["kernel_shares"],
         "kernel_ms_per_step": head["kernel_ms_per_step"],
         "clocks": clocks,
@@ -699,7 +740,7 @@ def run_gpu(args):
             res.pop("in_bytes"); res.pop("nnz")
             res["clocks"] = sm.summary(w0, w1)
             sm.stop()
-            for k in ("kernel_shares",):
+            for k in ("kernel_shares", "tuned_cluster"):
                 res.pop(k)
             sec[name] = res
             torch.cuda.empty_cache()
