@@ -662,7 +662,11 @@ cldiam_status arena_add(cldiam_arena* a, const uint32_t* src, const uint32_t* ds
     CLD_CUDA(cudaMemcpyAsync(a->off + a->off_used, g->off, (g->n + 1) * 8, cudaMemcpyDeviceToDevice, a->stream));
     if (g->nnz) {
         CLD_CUDA(cudaMemcpyAsync(a->adj + a->adj_used, g->adj, g->nnz * 8, cudaMemcpyDeviceToDevice, a->stream));
-        CLD_CUDA(cudaMemcpyAsync(a->row + a->adj_used, g->row, g->nnz * 4, cudaMemcpyDeviceToDevice, a->stream));
+        if (g->row) {
+            CLD_CUDA(cudaMemcpyAsync(a->row + a->adj_used, g->row, g->nnz * 4, cudaMemcpyDeviceToDevice, a->stream));
+        } else {
+            CLD_TRY(fill_rows(g->off, g->n, a->row + a->adj_used, a->stream));
+        }
     }
     ArenaDesc dsc{};
     dsc.off_base = a->off_used;

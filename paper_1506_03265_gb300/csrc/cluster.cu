@@ -532,6 +532,7 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
     const unsigned pull_grid =
         (unsigned)std::min<uint64_t>((uint64_t)num_sms() * pull_ctas, (pull_chunks + PT / 32 - 1) / (PT / 32));
     uint32_t nf = 0, E = 0;
+    DBuf<uint32_t> rows_built;  // COO rows for the guard's edge scan when the graph keeps none
 
     // list every relaxer (stage start, or after Delta doubled)
     auto rebuild = [&]() -> cldiam_status {
@@ -629,7 +630,12 @@ cldiam_status cluster(cldiam_graph* g, double tau, uint64_t seed, const cldiam_o
                     growable = covered > 0 || U < n;
                 } else if (delta < kDeltaMax && g->nnz) {
                     CLD_TRY(zero_field(offsetof(Counters, growable), 4));
-                    CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz,
+                    if (!g->row && !rows_built.get()) {  // (graphs without a row array are connected LCCs)
+                        CLD_TRY(rows_built.alloc(g->nnz, s));
+                        CLD_TRY(fill_rows(g->off, n, rows_built.get(), s));
+                    }
+                    const uint32_t* rows = g->row ? g->row : rows_built.get();
+                    CLD_K(K_GROWABLE, s, k_growable<<<grid_for(g->nnz, 256), 256, 0, s>>>(rows, g->adj, g->nnz,
                                                                                              key.get(), ctr.get()));
                     CLD_LAUNCH_CHECK();
                     CLD_TRY(sync_counters());

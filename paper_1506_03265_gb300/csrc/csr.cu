@@ -421,7 +421,7 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__
             const uint32_t pos = ia.y + i;
             if (pos < cap) {
                 nadj[pos] = make_uint2(nb_, w);
-                nrow[pos] = ia.x;
+                if (nrow) nrow[pos] = ia.x;
             } else {
                 atomicExch(err, 1u);
             }
@@ -432,7 +432,7 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__
             const uint32_t pos = ib.z + i;
             if (pos < cap) {
                 nadj[pos] = make_uint2(na_, (uint32_t)t & wmask);
-                nrow[pos] = ib.x;
+                if (nrow) nrow[pos] = ib.x;
             } else {
                 atomicExch(err, 1u);
             }
@@ -763,7 +763,9 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         DBuf<uint32_t> nrow;
         CLD_TRY(noff.alloc((size_t)n + 1, s));
         CLD_TRY(nadj.alloc(nnz ? nnz : 1, s));
-        CLD_TRY(nrow.alloc(nnz ? nnz : 1, s));
+        // the row of every entry (COO form) is written only by the (key, weight) copy; a CSR assembled from the
+        // lists leaves it out (its users build it from the offsets when they need it: fill_rows)
+        if (!packed) CLD_TRY(nrow.alloc(nnz ? nnz : 1, s));
         if (packed) {
             // the LCC's CSR straight from the lists: the whole graph's CSR is never built
             DBuf<uint4> info;
@@ -774,7 +776,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             CLD_LAUNCH_CHECK();
             if (mu > 0) {
                 CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, info.get(), newid.get(),
-                                                                                nnz ? nnz : 1, nrow.get(), nadj.get(),
+                                                                                nnz ? nnz : 1, nullptr, nadj.get(),
                                                                                 wsum.get(), scal.get() + 6,
                                                                                 scal.get() + 8));
                 CLD_LAUNCH_CHECK();
@@ -835,6 +837,34 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
     g->wmin = hbad[6];
     g->max_deg = hbad[7];
     *out = owner.release();
+    return CLDIAM_OK;
+}
+
+// row[p] = v for every position p of row v (an empty row writes nothing): a lane per row writes a short row
+// itself; the rows of more than 32 entries in a warp are written by the whole warp, one after another
+__global__ void k_fill_rows(const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ row) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint32_t v = base + lane;
+        const uint64_t o0 = v < n ? off[v] : 0, o1 = v < n ? off[v + 1] : 0;
+        const bool big = o1 - o0 > 32;
+        if (!big)
+            for (uint64_t p = o0; p < o1; ++p) row[p] = v;
+        unsigned bigs = __ballot_sync(0xffffffffu, big);
+        while (bigs) {
+            const uint32_t src = (uint32_t)__ffs(bigs) - 1;
+            const uint64_t b0 = __shfl_sync(0xffffffffu, o0, src), b1 = __shfl_sync(0xffffffffu, o1, src);
+            for (uint64_t p = b0 + lane; p < b1; p += 32) row[p] = base + src;
+            bigs &= bigs - 1;
+        }
+    }
+}
+
+cldiam_status fill_rows(const uint64_t* off, uint32_t n, uint32_t* row, cudaStream_t s) {
+    if (n == 0) return CLDIAM_OK;
+    CLD_K(K_CSR, s, k_fill_rows<<<grid_for(n, 256), 256, 0, s>>>(off, n, row));
+    CLD_LAUNCH_CHECK();
     return CLDIAM_OK;
 }
 

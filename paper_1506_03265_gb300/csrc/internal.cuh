@@ -11,7 +11,8 @@ struct cldiam_graph {
     uint64_t nnz = 0;            // directed entries = 2 x undirected edges
     uint64_t* off = nullptr;     // [n+1]
     uint2* adj = nullptr;        // [nnz] (col, w), rows sorted by col
-    uint32_t* row = nullptr;     // [nnz] row of each entry (COO view for edge-parallel passes)
+    uint32_t* row = nullptr;     // [nnz] row of each entry (COO view), or null: a CSR assembled from the
+                                 // sorted edge lists has none (fill_rows builds it from off when needed)
     uint32_t* orig = nullptr;    // [n] original id
     uint64_t wsum_upper = 0;     // sum of weights over u < v entries
     uint32_t wmin = 0;
@@ -103,6 +104,9 @@ cudaStream_t arena_stream(const cldiam_arena* a);
 cldiam_status arena_job_times(const cldiam_arena* a, uint32_t count, double* start_s, double* end_s);
 // adjacency entries of the listed graphs (ids out of range count 0)
 uint64_t arena_entries(const cldiam_arena* a, const uint32_t* ids, uint32_t count);
+
+// row[p] = v for every CSR position p of row v (a graph assembled from the sorted lists keeps no row array)
+cldiam_status fill_rows(const uint64_t* off, uint32_t n, uint32_t* row, cudaStream_t s);
 
 cldiam_status sssp_delta(cldiam_graph* g, uint32_t source, uint32_t delta, uint32_t* dist_out, uint64_t* ecc,
                          uint64_t* rounds, uint64_t* scanned);

@@ -9,6 +9,7 @@
 // (row, col).  While k is small enough for a dense k x k matrix to stay in
 // L2, the pairs are instead folded into that matrix with atomicMin and read
 // out row by row, which gives the same sorted CSR.
+#include "cluster_dev.cuh"
 #include "internal.cuh"
 #include "prof.cuh"
 
@@ -104,6 +105,77 @@ __global__ void __launch_bounds__(256) k_q_dense_emit(const uint32_t* __restrict
     if (__any_sync(0xffffffffu, ovf) && lane_id() == 0) atomicExch(overflow, 1u);
 }
 
+// The same folds for a CSR without a row array (every row has an entry: the LCC): each warp takes QW
+// consecutive positions, finds the row holding its first from the chunk table (qrow: the row holding
+// position QW * q) and the rows that start inside from the offsets, and gives every position its row with
+// one OR-reduction of start bits per 32 positions.  The adjacency loads of a chunk are issued first.
+constexpr int QW = 128;  // positions per warp chunk
+__global__ void k_q_rows(uint32_t n, const uint64_t* __restrict__ off, uint32_t* __restrict__ qrow) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint64_t o0 = off[v], o1 = off[v + 1];
+        for (uint64_t q = (o0 + QW - 1) / QW; q * QW < o1; ++q) qrow[q] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_q_dense_emit_chunks(uint32_t n, uint32_t nnz, uint32_t nq,
+                                                             const uint32_t* __restrict__ qrow,
+                                                             const uint64_t* __restrict__ off,
+                                                             const uint2* __restrict__ adj, const uint2* __restrict__ cd,
+                                                             uint32_t k, uint32_t* __restrict__ M,
+                                                             uint32_t* __restrict__ overflow) {
+    __shared__ uint32_t sst[8][QW + 1];
+    const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned le_mask = 0xffffffffu >> (31u - lane);  // lanes <= this one
+    const uint32_t nwarps = gridDim.x * 8;
+    bool ovf = false;
+    for (uint32_t q = blockIdx.x * 8 + warp; q < nq; q += nwarps) {
+        const uint32_t p0 = q * QW;
+        uint2 e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t p = p0 + 32u * u + lane;
+            e[u] = p < nnz ? ld_stream_u2(adj + p, pol_stream) : make_uint2(0u, 0u);
+        }
+        // row B0 holds p0; rows B0 + 1 .. B1 start inside (p0, p0 + QW] (at most QW of them)
+        const uint32_t B0 = __ldg(&qrow[q]);
+        const uint32_t B1 = q + 1 < nq ? __ldg(&qrow[q + 1]) : n - 1;
+        const uint32_t nr = min(B1 - B0, (uint32_t)QW);
+        __syncwarp();  // the previous chunk's starts have been read
+        for (uint32_t j = lane; j < nr; j += 32) sst[warp][j] = (uint32_t)__ldg(&off[B0 + 1 + j]);
+        __syncwarp();
+        uint32_t own[4];
+        {
+            uint32_t B = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) B += (uint32_t)__popc(group_starts(sst[warp] + B, nr - B, p0 + 32u * u, B, lane,
+                                                                         le_mask, &own[u]));
+        }
+        unsigned long long pu[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t r = B0 + own[u];
+            const bool take = p0 + 32u * u + lane < nnz && r < e[u].x;  // each undirected edge once
+            pu[u] = take ? ld_nc_keep_u64(reinterpret_cast<const unsigned long long*>(cd) + r, pol_keep) : 0ull;
+            pv[u] = take ? ld_nc_keep_u64(reinterpret_cast<const unsigned long long*>(cd) + e[u].x, pol_keep) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t r = B0 + own[u];
+            const uint32_t a = (uint32_t)pu[u], b = (uint32_t)pv[u];
+            if (!(p0 + 32u * u + lane < nnz && r < e[u].x) || a == b) continue;
+            uint64_t sw = (pu[u] >> 32) + e[u].y + (pv[u] >> 32);
+            if (sw >= 0xFFFFFFFFull) {
+                ovf = true;
+                sw = 0xFFFFFFFEull;
+            }
+            uint32_t* m = &M[(size_t)min(a, b) * k + max(a, b)];
+            if ((uint32_t)sw < __ldca(m)) atomicMin(m, (uint32_t)sw);
+        }
+    }
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicExch(overflow, 1u);
+}
+
 // lower triangle := transpose of the upper one, through 32 x 32 shared-memory tiles
 __global__ void k_q_dense_mirror(uint32_t* __restrict__ M, uint32_t k) {
     __shared__ uint32_t t[32][33];
@@ -173,8 +245,20 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
         DBuf<uint2> cd;
         CLD_TRY(cd.alloc(g->n, s));
         CLD_K(K_QUOTIENT, s, k_q_pack_cd<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, c->cid, c->D, cd.get()));
-        CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for((g->nnz + QE_U - 1) / QE_U, 256), 256, 0, s>>>(
-                                 g->row, g->adj, g->nnz, cd.get(), k, M.get(), scal.get()));
+        if (g->row) {
+            CLD_K(K_QUOTIENT, s, k_q_dense_emit<<<grid_for((g->nnz + QE_U - 1) / QE_U, 256), 256, 0, s>>>(
+                                     g->row, g->adj, g->nnz, cd.get(), k, M.get(), scal.get()));
+        } else {
+            // no row array: an assembled LCC, where every row has an entry (positions fit 32 bits)
+            if (g->nnz >= 0xFFFFFFFFull) return fail(CLDIAM_ERR_UNSUPPORTED, "2^32 or more CSR entries");
+            const uint32_t nqc = (uint32_t)((g->nnz + QW - 1) / QW);
+            DBuf<uint32_t> qrow;
+            CLD_TRY(qrow.alloc(nqc, s));
+            CLD_K(K_QUOTIENT, s, k_q_rows<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, g->off, qrow.get()));
+            CLD_K(K_QUOTIENT, s, k_q_dense_emit_chunks<<<grid_for((size_t)nqc * 32, 256), 256, 0, s>>>(
+                                     g->n, (uint32_t)g->nnz, nqc, qrow.get(), g->off, g->adj, cd.get(), k, M.get(),
+                                     scal.get()));
+        }
         CLD_LAUNCH_CHECK();
     }
     {
@@ -198,9 +282,10 @@ cldiam_status build_quotient_dense(const cldiam_clustering* c, cldiam_quotient* 
                                                                                     w.get()));
     CLD_K(K_QUOTIENT, s, k_q_widen<<<grid_for((size_t)k + 1, 256), 256, 0, s>>>(start.get(), k, nq, off.get()));
     CLD_LAUNCH_CHECK();
-    // algorithmic bytes: each CSR entry's row and (col, w); for half of them two cluster ids and two
-    // D values; the matrix mirrored and read twice
-    prof_add_bytes(K_QUOTIENT, (double)g->nnz * 20.0 + (double)k * k * 12.0);
+    // algorithmic bytes: each CSR entry's (col, w) and, with a row array, its row (else the offsets of the
+    // chunks' rows); for half of the entries two cluster ids and two D values; the matrix mirrored and read twice
+    prof_add_bytes(K_QUOTIENT, (double)g->nnz * (g->row ? 20.0 : 16.0) + (g->row ? 0.0 : 8.0 * g->n) +
+                                   (double)k * k * 12.0);
     CLD_CUDA(cudaStreamSynchronize(s));
     q->k = k;
     q->nnz = nq;
@@ -227,7 +312,14 @@ cldiam_status build_quotient(const cldiam_clustering* c, cldiam_quotient* q) {
         DBuf<uint2> cd;
         CLD_TRY(cd.alloc(g->n, s));
         CLD_K(K_QUOTIENT, s, k_q_pack_cd<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, c->cid, c->D, cd.get()));
-        CLD_K(K_QUOTIENT, s, k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(g->row, g->adj, g->nnz, cd.get(), k,
+        DBuf<uint32_t> rows;  // the COO rows, built from the offsets when the graph keeps none
+        const uint32_t* row = g->row;
+        if (!row) {
+            CLD_TRY(rows.alloc(g->nnz, s));
+            CLD_TRY(fill_rows(g->off, g->n, rows.get(), s));
+            row = rows.get();
+        }
+        CLD_K(K_QUOTIENT, s, k_q_emit<K><<<grid_for(g->nnz, 256), 256, 0, s>>>(row, g->adj, g->nnz, cd.get(), k,
                                                                               keys.get(), vals.get(), scal.get(),
                                                                               scal.get() + 1));
         CLD_LAUNCH_CHECK();
