@@ -111,19 +111,34 @@ __global__ void k_canon_runs(const uint64_t* __restrict__ T, uint32_t mu, int vb
     if (blockIdx.x == 0 && threadIdx.x == 0) *nnz = 2 * mu;
     const uint32_t cmask = vb >= 32 ? 0xFFFFFFFFu : ((1u << vb) - 1u);
     constexpr uint32_t kNo = 0xFFFFFFFFu;  // no neighbour (ids are below n <= 2^32 - 1)
+    constexpr int CU = 4;                  // 32-entry chunks per warp and iteration, loaded together
     const unsigned l = lane_id();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    // warp-uniform trip count; neighbours' row ids come by shuffle, the warp's two edge lanes load theirs
-    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < mu; i0 += stride) {
-        const uint32_t i = i0 + l;
-        const bool ok = i < mu;
-        const uint32_t b = ok ? (uint32_t)(T[i] >> wb) & cmask : kNo;
-        uint32_t bp = __shfl_up_sync(0xffffffffu, b, 1), bn = __shfl_down_sync(0xffffffffu, b, 1);
-        if (l == 0) bp = ok && i > 0 ? (uint32_t)(T[i - 1] >> wb) & cmask : kNo;
-        if (l == 31) bn = i + 1 < mu ? (uint32_t)(T[i + 1] >> wb) & cmask : kNo;
-        if (!ok) continue;
-        if (bp != b) tstart[b] = i;
-        if (bn != b) tend[b] = i + 1;
+    const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x * CU;
+    // warp-uniform trip count; a warp takes CU * 32 consecutive entries, neighbours' row ids come by
+    // shuffle (across chunks through lanes 31 and 0), the two ends of the span are loaded
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * CU; i0 < mu; i0 += wstride) {
+        uint32_t b[CU];
+#pragma unroll
+        for (int k = 0; k < CU; ++k) {
+            const uint64_t i = i0 + 32 * k + l;
+            b[k] = i < mu ? (uint32_t)(T[i] >> wb) & cmask : kNo;
+        }
+        uint32_t before = kNo, after = kNo;
+        if (l == 0 && i0 > 0) before = (uint32_t)(T[i0 - 1] >> wb) & cmask;
+        if (l == 31 && i0 + 32 * CU < mu) after = (uint32_t)(T[i0 + 32 * CU] >> wb) & cmask;
+#pragma unroll
+        for (int k = 0; k < CU; ++k) {
+            const uint64_t i = i0 + 32 * k + l;
+            uint32_t bp = __shfl_up_sync(0xffffffffu, b[k], 1), bn = __shfl_down_sync(0xffffffffu, b[k], 1);
+            const uint32_t prev_last = __shfl_sync(0xffffffffu, k > 0 ? b[k > 0 ? k - 1 : 0] : before, k > 0 ? 31 : 0);
+            const uint32_t next_first = __shfl_sync(0xffffffffu, k < CU - 1 ? b[k < CU - 1 ? k + 1 : k] : after,
+                                                    k < CU - 1 ? 0 : 31);
+            if (l == 0) bp = prev_last;
+            if (l == 31) bn = next_first;
+            if (i >= mu) continue;
+            if (bp != b[k]) tstart[b[k]] = (uint32_t)i;
+            if (bn != b[k]) tend[b[k]] = (uint32_t)i + 1;
+        }
     }
 }
 
@@ -401,7 +416,7 @@ __global__ void k_lcc_offsets_lists(const uint32_t* __restrict__ excl, const uin
 // A position past the output (inconsistent input) is recorded in *err and the write skipped.  The row's
 // own record (info, 16 B) is read in runs (U is sorted on a, T on b); the far end's new id comes from
 // the 4-byte newid array (evict-last: it stays in L2 while the two edge lists stream through, evict-first).
-__global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info,
+__global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info,
                                const uint32_t* __restrict__ newid, uint64_t cap, uint32_t* __restrict__ nrow,
                                uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
                                uint32_t* __restrict__ wmin, uint32_t* __restrict__ err) {
@@ -409,32 +424,62 @@ __global__ void k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__
     const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     unsigned long long sum = 0;
     uint32_t mn = 0xFFFFFFFFu;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += gridDim.x * blockDim.x) {
-        const uint64_t u = ld_stream_u64(g.U + i, pol_stream), t = ld_stream_u64(g.T + i, pol_stream);
-        const uint32_t a = (uint32_t)(u >> g.ash), b = (uint32_t)(u >> g.wb) & g.cmask, w = (uint32_t)u & wmask;
-        const uint32_t ta = (uint32_t)(t >> g.ash), tb = (uint32_t)(t >> g.wb) & g.cmask;
-        const uint4 ia = info[a], ib = info[tb];
-        // far ends (a kept row's neighbours are kept: their new ids are valid)
-        const uint32_t nb_ = ia.x != 0xFFFFFFFFu ? ld_nc_keep_u32(newid + b, pol_keep) : 0u;
-        const uint32_t na_ = ib.x != 0xFFFFFFFFu ? ld_nc_keep_u32(newid + ta, pol_keep) : 0u;
-        if (ia.x != 0xFFFFFFFFu) {  // kept (then b is kept too)
-            const uint32_t pos = ia.y + i;
-            if (pos < cap) {
-                nadj[pos] = make_uint2(nb_, w);
-                if (nrow) nrow[pos] = ia.x;
-            } else {
-                atomicExch(err, 1u);
-            }
-            sum += w;
-            mn = w < mn ? w : mn;
+    // AU entries per thread and iteration: the loads of each level (edge words, row records, far-end ids)
+    // are issued for all of them before the next level, so the dependent gathers overlap
+    constexpr int AU = 4;
+    constexpr uint32_t kDrop = 0xFFFFFFFFu;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < mu; base += stride * AU) {
+        uint64_t u[AU], t[AU];
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+            const uint64_t i = base + k * stride;
+            u[k] = i < mu ? ld_stream_u64(g.U + i, pol_stream) : 0ull;
+            t[k] = i < mu ? ld_stream_u64(g.T + i, pol_stream) : 0ull;
         }
-        if (ib.x != 0xFFFFFFFFu) {
-            const uint32_t pos = ib.z + i;
-            if (pos < cap) {
-                nadj[pos] = make_uint2(na_, (uint32_t)t & wmask);
-                if (nrow) nrow[pos] = ib.x;
-            } else {
-                atomicExch(err, 1u);
+        uint32_t ix[AU], iy[AU], jx[AU], jz[AU];
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+            ix[k] = jx[k] = kDrop;
+            iy[k] = jz[k] = 0;
+            if (base + k * stride < mu) {
+                const uint4 ia = info[(uint32_t)(u[k] >> g.ash)], ib = info[(uint32_t)(t[k] >> g.wb) & g.cmask];
+                ix[k] = ia.x;
+                iy[k] = ia.y;
+                jx[k] = ib.x;
+                jz[k] = ib.z;
+            }
+        }
+        // far ends (a kept row's neighbours are kept: their new ids are valid)
+        uint32_t nb[AU], na[AU];
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+            nb[k] = ix[k] != kDrop ? ld_nc_keep_u32(newid + ((uint32_t)(u[k] >> g.wb) & g.cmask), pol_keep) : 0u;
+            na[k] = jx[k] != kDrop ? ld_nc_keep_u32(newid + (uint32_t)(t[k] >> g.ash), pol_keep) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+            const uint32_t i = (uint32_t)(base + k * stride);  // < mu when the row is kept
+            if (ix[k] != kDrop) {  // kept (then b is kept too)
+                const uint32_t w = (uint32_t)u[k] & wmask;
+                const uint32_t pos = iy[k] + i;
+                if (pos < cap) {
+                    nadj[pos] = make_uint2(nb[k], w);
+                    if (nrow) nrow[pos] = ix[k];
+                } else {
+                    atomicExch(err, 1u);
+                }
+                sum += w;
+                mn = w < mn ? w : mn;
+            }
+            if (jx[k] != kDrop) {
+                const uint32_t pos = jz[k] + i;
+                if (pos < cap) {
+                    nadj[pos] = make_uint2(na[k], (uint32_t)t[k] & wmask);
+                    if (nrow) nrow[pos] = jx[k];
+                } else {
+                    atomicExch(err, 1u);
+                }
             }
         }
     }
@@ -775,7 +820,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
                                 degx.get(), scal.get() + 4, scal.get() + 5, orig.get(), la, noff.get(), info.get()));
             CLD_LAUNCH_CHECK();
             if (mu > 0) {
-                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256), 256, 0, s>>>(la, mu, info.get(), newid.get(),
+                CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256, 4), 256, 0, s>>>(la, mu, info.get(), newid.get(),
                                                                                 nnz ? nnz : 1, nullptr, nadj.get(),
                                                                                 wsum.get(), scal.get() + 6,
                                                                                 scal.get() + 8));
