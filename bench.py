@@ -425,8 +425,11 @@ def load_peaks():
     return json.load(open(pk)) if os.path.exists(pk) else {}
 
 
-def stored_traffic(workload, cls):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary, while its source is unchanged."""
+def stored_traffic(workload, cls, alg_bytes_per_launch=None):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, while its source is unchanged:
+    either captured on the workload itself, or (a workload too large to capture under the size rule)
+    captured on a smaller one above the L2 size and scaled by the algorithmic bytes per launch, i.e. by the
+    units a launch processes."""
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tpath):
         return None
@@ -435,7 +438,13 @@ def stored_traffic(workload, cls):
         return None
     src = os.path.join(ROOT, ent.get("source_file", ""))
     same = os.path.isfile(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == ent.get("source_sha256")
-    return ent.get("dram_bytes_per_launch") if same else None
+    if not same:
+        return None
+    if "dram_bytes_per_launch" in ent:
+        return ent["dram_bytes_per_launch"]
+    if "dram_per_alg_byte" in ent and alg_bytes_per_launch:
+        return round(ent["dram_per_alg_byte"] * alg_bytes_per_launch)
+    return None
 
 
 def roofline_of(prof, classes, peak, peaks, workload, tkey=None):
@@ -447,10 +456,19 @@ def roofline_of(prof, classes, peak, peaks, workload, tkey=None):
     achieved = b / (ms * 1e-3) / 1e9 if ms > 0 else None
     return {"bound": "hbm", "kernel": "+".join(classes), "achieved": round(achieved, 1) if achieved else None,
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-            "traffic": stored_traffic(workload, tkey or classes[0]), "launches": launches,
+            "traffic": stored_traffic(workload, tkey or classes[0], b / max(1, launches)), "launches": launches,
             "alg_bytes_per_launch": round(b / max(1, launches)),
             "avg_launch_us": round(1e3 * ms / max(1, launches), 2),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+
+
+def combined_traffic(roof):
+    """Traffic per launch of several kernel classes together: the forms' values weighed by their launches
+    (null unless every form that launched has one)."""
+    forms = [f for f in roof["forms"].values() if f["launches"]]
+    if forms and all(f["traffic"] is not None for f in forms):
+        roof["traffic"] = round(sum(f["traffic"] * f["launches"] for f in forms) / sum(f["launches"] for f in forms))
+    return roof
 
 
 def tuned_cluster_leg(cd, g, tau, seed, stream, reps=5):
@@ -581,10 +599,11 @@ def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None,
                        "gteps_excluding_csr_build": round(ws * m_lcc / (ms_rest * 1e-3) / 1e9, 4),
                        "what": "m_LCC / time of CLUSTER + quotient + estimate on a built CSR (the same timed steps)"},
         "roofline": roofline_of(prof, [dominant], peak, peaks, name),
-        "relax_roofline": dict(
+        "relax_roofline": combined_traffic(dict(
             roofline_of(prof, list(RELAX_CLASSES), peak, peaks, name, tkey="relax_steps"),
-            traffic_note=("per form below (ncu, one launch, R-MAT 20 only); no full-size capture of R-MAT 24 "
-                          "(multi-metric captures stay at R-MAT 20 or smaller)"),
+            traffic_note=("per form below: DRAM bytes per algorithmic byte from one-kernel ncu captures on R-MAT 22 "
+                          "(inputs above the L2 size, a few GB on the device), times this workload's algorithmic "
+                          "bytes per launch; the combined value weighs the forms by their launches"),
             what=("both forms of the Delta-growing step (pushed relax and dense relax_pull) over the timed "
                   "steps: algorithmic bytes = 16 B per adjacency entry a launch reads + per-entry/row/changed-"
                   "node terms (DESIGN.md section 6) / CUDA-event time"),
@@ -594,12 +613,12 @@ def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None,
                        "frac": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9 / peak, 4) if prof[c]["ms"]
                        else None,
                        "alg_bytes_per_launch": round(prof[c]["bytes"] / max(1, prof[c]["launches"])),
-                       "traffic": stored_traffic(name, c)}
+                       "traffic": stored_traffic(name, c, prof[c]["bytes"] / max(1, prof[c]["launches"]))}
                    for c in RELAX_CLASSES},
             edges_scanned_per_step=scanned,
             scanned_16B_gbs=round(16.0 * scanned / (relax_ms * 1e-3) / 1e9, 1) if relax_ms else None,
             scanned_16B_frac=round(16.0 * scanned / (relax_ms * 1e-3) / 1e9 / peak, 4) if relax_ms else None,
-            relax_gteps=round(scanned / (relax_ms * 1e-3) / 1e9, 3) if relax_ms else None),
+            relax_gteps=round(scanned / (relax_ms * 1e-3) / 1e9, 3) if relax_ms else None)),
         "kernel_shares": {k: round(v / tot, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
         "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda x: -x[1])},
         "gpu_launches": sum(v["launches"] for v in prof.values()),
@@ -780,9 +799,13 @@ def profile_pass(args):
     wl = WORKLOADS[args.workload]
     e = wl.make()
     ts = [torch.from_numpy(a.view(np.int32)).cuda() for a in (e.src, e.dst, e.w)]
+    cd.profile_reset()
     g = cd.build_csr(ts[0], ts[1], ts[2], e.n, lcc=True)
     r = cd.estimate(cd.quotient_build(cd.cluster(g, wl.tau, wl.seed)))
-    print(json.dumps({"workload": args.workload, "k": r["k"], "phi_approx": r["phi_approx"]}))
+    # launches and algorithmic bytes per kernel class of this pass: the denominators of the DRAM captures
+    prof = {c: {"launches": v["launches"], "bytes": v["bytes"]} for c, v in cd.profile_get().items() if v["launches"]}
+    print(json.dumps({"workload": args.workload, "k": r["k"], "phi_approx": r["phi_approx"], "m": int(e.src.size),
+                      "nnz_lcc": g.nnz, "n_lcc": g.n, "classes": prof}))
 
 
 def profile_other(args):
