@@ -30,16 +30,24 @@ namespace cld {
 
 namespace {
 
-constexpr int BT = 1024;              // threads per CTA
+// many-graph CTAs resident per SM.  One 1,024-thread CTA per SM: two 512-thread CTAs per SM (shared-memory
+// carveout at its maximum, Floyd-Warshall cut-over 128) gave 16 % more aggregate work per second on the
+// 2,000-graph mixture but 1.6x the time per large graph on one CTA, and its 111 R-MAT 16 graphs set the
+// tail (17.4k against 25.4k graphs/s)
+constexpr int kBatchCtasPerSm = 1;
+constexpr int BT = 1024 / kBatchCtasPerSm;  // threads per CTA
+constexpr int kRelaxU = 1024 / BT;          // positions per thread of a growing-step chunk (1,024 per chunk)
 constexpr uint32_t kDenseCap = 1024;  // largest quotient deduplicated in the dense matrix
 constexpr uint64_t kSplitMinEntries = 1u << 16;  // graphs below this many entries always stay in the launch
 // makespan model of the many-graph split (GB300): seconds per unit of work (entry or node) on one 1,024-thread
 // CTA of the launch, and a graph's cost on the one-graph path (a fixed part for its launches and counter
 // reads, and a per-unit part with the whole device)
-constexpr double kCtaSecPerUnit = 37e-9;
+constexpr double kCtaSecPerUnit = kBatchCtasPerSm == 1 ? 37e-9 : 63e-9;
 constexpr double kPlainSecPerGraph = 1.5e-3;
 constexpr double kPlainSecPerUnit = 0.05e-9;
-constexpr uint32_t kSmemFwK = 200;    // quotients up to this size are closed by Floyd-Warshall in shared memory
+// quotients up to this size are closed by Floyd-Warshall in shared memory (the k x k matrix, next to the
+// static shared memory, must fit kBatchCtasPerSm times per SM)
+constexpr uint32_t kSmemFwK = kBatchCtasPerSm == 1 ? 200 : 128;
 constexpr uint32_t kJobOk = 0, kJobNeedsPlain = 1, kJobOverflow = 2, kJobDiverged = 3, kJobTimeout = 4;
 
 struct ArenaDesc {  // one graph of the arena (device copy)
@@ -97,8 +105,10 @@ __device__ __forceinline__ uint32_t relax_min_u32(uint32_t c, uint32_t a, uint32
     return (carry | !finite) ? c : (s < c ? s : c);
 }
 
+// every thread gets op over the block's values; ident is op's identity (it fills the lanes past the
+// block's warp count)
 template <class T, class Op>
-__device__ __forceinline__ T block_all_reduce(T v, Op op, T* red) {
+__device__ __forceinline__ T block_all_reduce(T v, Op op, T ident, T* red) {
     v = op(v, __shfl_xor_sync(0xffffffffu, v, 16));
     v = op(v, __shfl_xor_sync(0xffffffffu, v, 8));
     v = op(v, __shfl_xor_sync(0xffffffffu, v, 4));
@@ -108,7 +118,7 @@ __device__ __forceinline__ T block_all_reduce(T v, Op op, T* red) {
     if (l == 0) red[w] = v;
     __syncthreads();
     if (w == 0) {
-        T x = l < nw ? red[l] : red[0];
+        T x = l < nw ? red[l] : ident;
         x = op(x, __shfl_xor_sync(0xffffffffu, x, 16));
         x = op(x, __shfl_xor_sync(0xffffffffu, x, 8));
         x = op(x, __shfl_xor_sync(0xffffffffu, x, 4));
@@ -124,7 +134,7 @@ __device__ __forceinline__ T block_all_reduce(T v, Op op, T* red) {
 
 struct BatchSmem {
     RelaxSmem relax;
-    uint32_t relax_next[relax_nbuf_words<1>(32)];  // 1024 threads
+    uint32_t relax_next[relax_nbuf_words<kRelaxU>(BT / 32)];
     unsigned long long scratch[33];
     unsigned long long red64[33];
     uint32_t red32[33];
@@ -136,7 +146,7 @@ struct BatchSmem {
 // cid[v] = rank of v's center among all centers (block-wide scan); returns k
 __device__ uint32_t block_relabel(uint32_t n, const uint32_t* __restrict__ center, uint32_t* __restrict__ rank,
                                   uint32_t* __restrict__ cid, BatchSmem& sm) {
-    const unsigned w = threadIdx.x >> 5, l = lane_id();
+    const unsigned w = threadIdx.x >> 5, l = lane_id(), nw = blockDim.x >> 5;
     uint32_t running = 0;
     for (uint32_t base = 0; base < n; base += blockDim.x) {
         const uint32_t v = base + threadIdx.x;
@@ -145,7 +155,7 @@ __device__ uint32_t block_relabel(uint32_t n, const uint32_t* __restrict__ cente
         if (l == 0) sm.woff[w] = (uint32_t)__popc(bal);
         __syncthreads();
         if (w == 0) {
-            const uint32_t c = sm.woff[l];
+            const uint32_t c = l < nw ? sm.woff[l] : 0u;  // lanes past the warp count add nothing
             const uint32_t incl = warp_incl_scan(c);
             sm.woff[l] = incl - c;
             if (l == 31) sm.woff[32] = incl;
@@ -266,7 +276,7 @@ __device__ uint32_t block_quotient_diameter(uint32_t k, uint32_t* __restrict__ M
         }
     }
     __syncthreads();
-    return block_all_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+    return block_all_reduce(best, [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u, sm.red32);
 }
 
 // One job: CLUSTER + quotient + Phi(G_C) of one arena graph by this CTA; thread 0 stores the result.
@@ -289,7 +299,7 @@ __device__ void finish_job(const Job& job, const ArenaDesc& d, const uint64_t* _
                 uint32_t m = 0;
                 for (uint32_t v = tid; v < n; v += BT) m = max(m, __ldcg(&ws.D[v]));
                 return m;
-            }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, sm.red32);
+            }(), [](uint32_t a, uint32_t b) { return a > b ? a : b; }, 0u, sm.red32);
         res.radius = rmax;
         if (k > kDenseCap) {
             status = kJobNeedsPlain;
@@ -319,12 +329,12 @@ __device__ void finish_job(const Job& job, const ArenaDesc& d, const uint64_t* _
                     for (uint32_t i = tid; i < k * k; i += BT) c += (i / k != i % k && __ldcg(&M[i]) != kNone);
                     return c;
                 }(),
-                [](unsigned long long a, unsigned long long b) { return a + b; }, sm.red64);
+                [](unsigned long long a, unsigned long long b) { return a + b; }, 0ull, sm.red64);
             res.quotient_edges = qe;
             bool ovf2 = false;
             const uint32_t phi = block_quotient_diameter(k, M, ws, dyn, sm, ovf2, job.fw_k);
             const uint32_t any_ovf = block_all_reduce((uint32_t)(ovf || ovf2),
-                                                      [](uint32_t a, uint32_t b) { return a | b; }, sm.red32);
+                                                      [](uint32_t a, uint32_t b) { return a | b; }, 0u, sm.red32);
             if (any_ovf) status = kJobOverflow;
             res.phi_gc = phi;
             res.phi_approx = (uint64_t)phi + 2ull * rmax;
@@ -404,7 +414,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
                         ctr->nnext = 0;
                     }
                     __syncthreads();
-                    dev_relax<1>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nf, E, adj, ws.center,
+                    dev_relax<kRelaxU>(ws.fbase[cur], ws.fkey[cur], ws.fpre[cur], nf, E, adj, ws.center,
                                  job.cumulative ? ws.D : nullptr, ws.key,
                                  delta, ws.stamp, stepid, ws.next, ctr, sm.relax, sm.relax_next, 0, 1);
                     __syncthreads();
@@ -474,7 +484,7 @@ __device__ void run_job(const Job& job, const ArenaDesc& d, const uint64_t* __re
     finish_job(job, d, off, adj, row, ws, sm, dyn, out, res, status, delta);
 }
 
-__global__ void __launch_bounds__(BT, 1)
+__global__ void __launch_bounds__(BT, kBatchCtasPerSm)
     k_batch(const ArenaDesc* __restrict__ descs, const Job* __restrict__ jobs, uint32_t count,
             const uint64_t* __restrict__ arena_off, const uint2* __restrict__ arena_adj,
             const uint32_t* __restrict__ arena_row, Workspace* __restrict__ wss, uint32_t* __restrict__ queue,
@@ -520,7 +530,7 @@ __device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
 // it finishes its previous one, so requests that arrive while others run join
 // immediately.  Waiting for work is bounded by idle_cycles; the host
 // relaunches the kernel when a request arrives after the CTAs left.
-__global__ void __launch_bounds__(BT, 1)
+__global__ void __launch_bounds__(BT, kBatchCtasPerSm)
     k_serve(const ArenaDesc* __restrict__ descs, const uint64_t* __restrict__ arena_off,
             const uint2* __restrict__ arena_adj, const uint32_t* __restrict__ arena_row,
             Workspace* __restrict__ wss, const Job* ring, ServeCtl* ctl, uint32_t* head, JobOut* outs,
@@ -793,8 +803,21 @@ static cldiam_status set_dyn_smem(Kern k, std::atomic<bool>* done_flags) {
     CLD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !done_flags[dev]) {
         CLD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_dyn_smem()));
+        if (kBatchCtasPerSm > 1)  // room for several CTAs' shared memory on one SM
+            CLD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
         if (dev >= 0 && dev < 64) done_flags[dev] = true;
     }
+    return CLDIAM_OK;
+}
+
+// CTAs of a persistent many-graph kernel resident on one SM: kBatchCtasPerSm when they fit, else what does
+template <class Kern>
+static cldiam_status resident_per_sm(Kern k, std::atomic<bool>* done_flags, int* out) {
+    CLD_TRY(set_dyn_smem(k, done_flags));
+    int nb = 0;
+    CLD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, BT, batch_dyn_smem()));
+    *out = std::max(1, std::min(nb, kBatchCtasPerSm));
     return CLDIAM_OK;
 }
 
@@ -831,7 +854,10 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
     std::stable_sort(jobs.begin(), jobs.end(), [&](const Job& x, const Job& y) {
         return a->graphs[x.graph].nnz + a->graphs[x.graph].n > a->graphs[y.graph].nnz + a->graphs[y.graph].n;
     });
-    const int nsm = num_sms();
+    static std::atomic<bool> attr[64];
+    int cps = 1;
+    CLD_TRY(resident_per_sm(k_batch, attr, &cps));
+    const int nsm = num_sms() * cps;  // CTAs of the launch
     // The launch ends with its largest graph on one CTA, or with the even split of all work over the CTAs,
     // whichever is later.  The k largest graphs can instead run first on the one-graph path, each with the
     // whole device at a fixed cost per graph; k is chosen to minimise the estimated makespan
@@ -914,8 +940,6 @@ cldiam_status batch_run(cldiam_arena* a, const uint32_t* ids, const double* tau,
         CLD_CUDA(cudaMemcpyAsync(dws.get(), wsh.data(), nsm * sizeof(Workspace), cudaMemcpyHostToDevice, s));
         CLD_CUDA(cudaMemsetAsync(queue.get(), 0, 4, s));
         const size_t dyn = batch_dyn_smem();
-        static std::atomic<bool> attr[64];
-        CLD_TRY(set_dyn_smem(k_batch, attr));
         CLD_K(K_MISC, s, k_batch<<<nsm, BT, dyn, s>>>(ddesc.get(), djobs.get(), nrest, a->off, a->adj, a->row, dws.get(),
                                                        queue.get(), douts.get()));
         CLD_LAUNCH_CHECK();
@@ -1005,9 +1029,10 @@ struct cldiam_server {
 
 namespace cld {
 
+static std::atomic<bool> g_serve_attr[64];
+
 static cldiam_status server_launch(cldiam_server* sv) {
-    static std::atomic<bool> attr[64];
-    CLD_TRY(set_dyn_smem(k_serve, attr));
+    CLD_TRY(set_dyn_smem(k_serve, g_serve_attr));
     sv->ctl->idle = 0;
     CLD_K(K_MISC, sv->kstream,
           k_serve<<<sv->ctas, BT, batch_dyn_smem(), sv->kstream>>>(sv->descs, sv->arena->off, sv->arena->adj,
@@ -1083,7 +1108,12 @@ cldiam_status server_create(cldiam_arena* a, const cldiam_server_opts* o, cldiam
     sv->arena = a;
     CLD_CUDA(cudaGetDevice(&sv->device));
     const int nsm = num_sms();
-    sv->ctas = opts.ctas ? std::min<uint32_t>(opts.ctas, nsm) : (uint32_t)std::max(1, nsm - 24);
+    int cps = 1;
+    if (cldiam_status st = resident_per_sm(k_serve, g_serve_attr, &cps); st != CLDIAM_OK) {
+        delete sv;
+        return st;
+    }
+    sv->ctas = opts.ctas ? std::min<uint32_t>(opts.ctas, (uint32_t)(nsm * cps)) : (uint32_t)(std::max(1, nsm - 24) * cps);
     sv->cap = opts.capacity ? opts.capacity : (1u << 20);
     sv->big_nodes = opts.big_nodes ? opts.big_nodes : (1u << 19);
     sv->budget = opts.hbm_budget_bytes;
