@@ -417,9 +417,9 @@ __global__ void k_lcc_offsets_lists(const uint32_t* __restrict__ excl, const uin
 // own record (info, 16 B) is read in runs (U is sorted on a, T on b); the far end's new id comes from
 // the 4-byte newid array (evict-last: it stays in L2 while the two edge lists stream through, evict-first).
 __global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu, const uint4* __restrict__ info,
-                               const uint32_t* __restrict__ newid, uint64_t cap, uint32_t* __restrict__ nrow,
-                               uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
-                               uint32_t* __restrict__ wmin, uint32_t* __restrict__ err) {
+                                                         const uint32_t* __restrict__ newid, uint64_t cap,
+                                                         uint2* __restrict__ nadj, unsigned long long* __restrict__ wsum,
+                                                         uint32_t* __restrict__ wmin, uint32_t* __restrict__ err) {
     const uint32_t wmask = g.wb >= 32 ? 0xFFFFFFFFu : ((1u << g.wb) - 1u);
     const uint64_t pol_stream = l2_evict_first_policy(), pol_keep = l2_evict_last_policy();
     unsigned long long sum = 0;
@@ -465,7 +465,6 @@ __global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu,
                 const uint32_t pos = iy[k] + i;
                 if (pos < cap) {
                     nadj[pos] = make_uint2(nb[k], w);
-                    if (nrow) nrow[pos] = ix[k];
                 } else {
                     atomicExch(err, 1u);
                 }
@@ -476,7 +475,6 @@ __global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu,
                 const uint32_t pos = jz[k] + i;
                 if (pos < cap) {
                     nadj[pos] = make_uint2(na[k], (uint32_t)t[k] & wmask);
-                    if (nrow) nrow[pos] = jx[k];
                 } else {
                     atomicExch(err, 1u);
                 }
@@ -821,7 +819,7 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
             CLD_LAUNCH_CHECK();
             if (mu > 0) {
                 CLD_K(K_CSR, s, k_lcc_assemble<<<grid_for(mu, 256, 4), 256, 0, s>>>(la, mu, info.get(), newid.get(),
-                                                                                nnz ? nnz : 1, nullptr, nadj.get(),
+                                                                                nnz ? nnz : 1, nadj.get(),
                                                                                 wsum.get(), scal.get() + 6,
                                                                                 scal.get() + 8));
                 CLD_LAUNCH_CHECK();
