@@ -606,7 +606,7 @@ def measure_workload(cd, name, steps, warmup, stream, dist, local, sampler=None,
                           "bytes per launch; the combined value weighs the forms by their launches"),
             what=("both forms of the Delta-growing step (pushed relax and dense relax_pull) over the timed "
                   "steps: algorithmic bytes = 16 B per adjacency entry a launch reads + per-entry/row/changed-"
-                  "node terms (DESIGN.md section 6) / CUDA-event time"),
+                  "node terms, as the library counts them per launch / CUDA-event time"),
             ms_per_step=round(relax_ms, 4),
             forms={c: {"launches": prof[c]["launches"], "ms": round(prof[c]["ms"] / steps, 4),
                        "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] * 1e-3) / 1e9, 1) if prof[c]["ms"] else None,
