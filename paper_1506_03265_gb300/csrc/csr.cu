@@ -437,30 +437,31 @@ __global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu,
             u[k] = i < mu ? ld_stream_u64(g.U + i, pol_stream) : 0ull;
             t[k] = i < mu ? ld_stream_u64(g.T + i, pol_stream) : 0ull;
         }
-        uint32_t ix[AU], iy[AU], jx[AU], jz[AU];
+        // position shifts of the kept rows' entries, and which rows are kept (bit k: the edge's row in U,
+        // bit AU + k: its row in T)
+        uint32_t iy[AU], jz[AU], kept = 0;
 #pragma unroll
         for (int k = 0; k < AU; ++k) {
-            ix[k] = jx[k] = kDrop;
             iy[k] = jz[k] = 0;
             if (base + k * stride < mu) {
                 const uint4 ia = info[(uint32_t)(u[k] >> g.ash)], ib = info[(uint32_t)(t[k] >> g.wb) & g.cmask];
-                ix[k] = ia.x;
                 iy[k] = ia.y;
-                jx[k] = ib.x;
                 jz[k] = ib.z;
+                kept |= (ia.x != kDrop ? 1u : 0u) << k;
+                kept |= (ib.x != kDrop ? 1u : 0u) << (AU + k);
             }
         }
         // far ends (a kept row's neighbours are kept: their new ids are valid)
         uint32_t nb[AU], na[AU];
 #pragma unroll
         for (int k = 0; k < AU; ++k) {
-            nb[k] = ix[k] != kDrop ? ld_nc_keep_u32(newid + ((uint32_t)(u[k] >> g.wb) & g.cmask), pol_keep) : 0u;
-            na[k] = jx[k] != kDrop ? ld_nc_keep_u32(newid + (uint32_t)(t[k] >> g.ash), pol_keep) : 0u;
+            nb[k] = (kept >> k) & 1u ? ld_nc_keep_u32(newid + ((uint32_t)(u[k] >> g.wb) & g.cmask), pol_keep) : 0u;
+            na[k] = (kept >> (AU + k)) & 1u ? ld_nc_keep_u32(newid + (uint32_t)(t[k] >> g.ash), pol_keep) : 0u;
         }
 #pragma unroll
         for (int k = 0; k < AU; ++k) {
             const uint32_t i = (uint32_t)(base + k * stride);  // < mu when the row is kept
-            if (ix[k] != kDrop) {  // kept (then b is kept too)
+            if ((kept >> k) & 1u) {  // kept (then b is kept too)
                 const uint32_t w = (uint32_t)u[k] & wmask;
                 const uint32_t pos = iy[k] + i;
                 if (pos < cap) {
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(256, 4) k_lcc_assemble(ListAdj g, uint32_t mu,
                 sum += w;
                 mn = w < mn ? w : mn;
             }
-            if (jx[k] != kDrop) {
+            if ((kept >> (AU + k)) & 1u) {
                 const uint32_t pos = jz[k] + i;
                 if (pos < cap) {
                     nadj[pos] = make_uint2(na[k], (uint32_t)t[k] & wmask);
