@@ -123,8 +123,9 @@ cldiam_status cldiam_version(int32_t* major, int32_t* minor);
 /*
  * Build the device CSR of an undirected weighted graph (Section 2 graph model).
  *  src, dst, w : m edges (host or device arrays); node ids < n, weights >= 1.
- *               Pinned host arrays are read in place by the device (no staging
- *               copy); other host arrays are copied to the device first.
+ *               Host arrays are copied to the device first, on the call's
+ *               stream (from pinned memory by the copy engine, which leaves
+ *               the SMs to work queued on other streams meanwhile).
  *  Self-loops are dropped; parallel edges merge to their minimum weight; the
  *  result is symmetric with rows sorted by column.  With CLDIAM_CSR_LCC only
  *  the largest connected component is kept (ties: the component holding the

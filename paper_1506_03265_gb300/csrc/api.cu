@@ -33,21 +33,13 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-cldiam_status to_device(const void* src, size_t bytes, cudaStream_t s, void** dev, bool* owned, bool read_once) {
+cldiam_status to_device(const void* src, size_t bytes, cudaStream_t s, void** dev, bool* owned) {
     *owned = false;
     *dev = nullptr;
     if (bytes == 0 || !src) return CLDIAM_OK;
     if (is_device_ptr(src)) {
         *dev = const_cast<void*>(src);
         return CLDIAM_OK;
-    }
-    if (read_once) {  // pinned host memory mapped into the device's address space: read it in place
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
-            *dev = a.devicePointer;
-            return CLDIAM_OK;
-        }
-        cudaGetLastError();
     }
     CLD_TRY(dmalloc(dev, bytes, s));
     *owned = true;

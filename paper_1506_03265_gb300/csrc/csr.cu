@@ -568,12 +568,14 @@ cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t
         void** p; bool* o; cudaStream_t s;
         ~InFree() { if (*o) dfree(*p, s); }
     };
-    // the edge arrays are read once (by the emission kernel): pinned host arrays are read in place
-    CLD_TRY(to_device(src, m * 4, s, &dsrc, &osrc, true));
+    // host edge arrays are copied to the device by the copy engine (cudaMemcpyAsync on the call's stream),
+    // not read in place by the emission kernel: the copy then occupies no SM, so another call's kernels can
+    // run on the whole device while this call's edge list crosses the host link
+    CLD_TRY(to_device(src, m * 4, s, &dsrc, &osrc));
     InFree f1{&dsrc, &osrc, s};
-    CLD_TRY(to_device(dst, m * 4, s, &ddst, &odst, true));
+    CLD_TRY(to_device(dst, m * 4, s, &ddst, &odst));
     InFree f2{&ddst, &odst, s};
-    CLD_TRY(to_device(w, m * 4, s, &dw, &ow, true));
+    CLD_TRY(to_device(w, m * 4, s, &dw, &ow));
     InFree f3{&dw, &ow, s};
 
     // items: packed words when the weight fits in the bits the two ids leave, else (key, weight) pairs

@@ -48,13 +48,10 @@ struct cldiam_quotient {
 namespace cld {
 
 cudaStream_t resolve_stream(void* user_stream);
-// Copy `bytes` from a host-or-device pointer into a fresh device buffer unless
-// it already is device memory (then *dev = src, *owned = false).
-// Device-visible copy of a caller array: device pointers are used as they are; with
-// read_once, pinned host memory is read in place by the kernel (over the host link, no
-// staging copy); other host memory is copied into a new device buffer (*owned = true).
-cldiam_status to_device(const void* src, size_t bytes, cudaStream_t s, void** dev, bool* owned,
-                        bool read_once = false);
+// Device copy of a caller array: device pointers are used as they are (*dev = src, *owned = false); host
+// memory is copied into a new device buffer by cudaMemcpyAsync on `s` (*owned = true): from pinned memory
+// that is the copy engine, which leaves the SMs to other work while the data crosses the host link.
+cldiam_status to_device(const void* src, size_t bytes, cudaStream_t s, void** dev, bool* owned);
 bool is_device_ptr(const void* p);
 
 cldiam_status build_csr(const uint32_t* src, const uint32_t* dst, const uint32_t* w, uint64_t m, uint32_t n,
