@@ -36,7 +36,9 @@
  *    The quotient diameter is exact whenever every quotient distance is
  *    below 2^31 - 1; beyond that, a candidate path sum that reaches 2^32 - 1
  *    is reported as CLDIAM_ERR_OVERFLOW even if the shortest distances fit.
- *  - Threads: one handle must not be used by two threads at once.
+ *  - Threads: one handle must not be used by two threads at once.  Calls on
+ *    different handles (and cldiam_run) may run at once from several threads,
+ *    each on its own stream; they give the results they give alone.
  */
 #ifndef CLDIAM_H
 #define CLDIAM_H
