@@ -119,7 +119,6 @@ int num_sms() {
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
-static_assert(SCAN_THREADS == 1024, "the tile scan's second level reads one warp sum per lane of warp 0");
 
 template <class T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_reduce(const T* __restrict__ in, size_t n, T* __restrict__ partial) {
